@@ -1,0 +1,217 @@
+/*
+ * hodlr2d.h -- C ABI of the GB300 (sm_103a) HODLR2D library.
+ *
+ * HODLR2D ("HODLR2D: A new class of hierarchical matrices", arXiv 2204.05536)
+ * represents the dense N x N matrix A_ij = phi(|x_i - x_j|) of a 2D point set
+ * on a balanced quadtree (Sec. 4):
+ *   - at every level l = 1..kappa, the interaction of a box C with each box of
+ *     its interaction list I_C (Def. ic, Eq. ilist: clan members that share
+ *     only a vertex with C or are well separated from it) is a low-rank block
+ *     U V^T obtained by ACA at tolerance eps (Alg. 1);
+ *   - at the leaf level the self block and the edge-sharing blocks (Def. ec)
+ *     stay dense (Remark in Sec. 4.1); they are evaluated from the kernel when
+ *     the product runs, not stored;
+ *   - the product b = K psi follows Alg. 2.
+ *
+ * Conventions (all entry points):
+ *   - Return HODLR2D_OK (0) or a negative HODLR2D_ERR_* code; hodlr2d_strerror
+ *     names it.  No entry point aborts, traps or prints.
+ *   - Pointers marked "host or device" may be either; the library asks the
+ *     CUDA runtime which one it was given.  Device pointers must be on the
+ *     handle's device.
+ *   - Matrices of right-hand sides are n x nrhs, column-major (column c starts
+ *     at c * n), in the caller's point order.
+ *   - A handle owns all of its device memory.  A handle is not thread-safe;
+ *     separate handles may run concurrently on separate streams.
+ *   - Work is queued on the handle's stream (hodlr2d_set_stream, default: the
+ *     legacy default stream).  Calls that return host-visible results
+ *     synchronise that stream before returning.
+ */
+#ifndef HODLR2D_H
+#define HODLR2D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----- error codes ----- */
+#define HODLR2D_OK 0
+#define HODLR2D_ERR_ARG (-1)     /* invalid argument (null, size, NaN, ...)       */
+#define HODLR2D_ERR_OOM (-2)     /* device or host allocation failed             */
+#define HODLR2D_ERR_CUDA (-3)    /* a CUDA runtime call failed                   */
+#define HODLR2D_ERR_NOCONV (-4)  /* an iteration did not reach its tolerance     */
+#define HODLR2D_ERR_TIMEOUT (-5) /* a bounded device-side wait gave up           */
+#define HODLR2D_ERR_DEPTH (-6)   /* no depth <= 14 meets the leaf rule           */
+#define HODLR2D_ERR_STATE (-7)   /* handle not ready (e.g. no factors yet)       */
+
+/* ----- kernel functions ----- */
+typedef enum {
+  HODLR2D_IMQ = 0,   /* 1 / sqrt(r^2 + a^2)                                      */
+  HODLR2D_MQ = 1,    /* sqrt(r^2 + a^2)                                          */
+  HODLR2D_LOG = 2,   /* log r                     (Sec. 3, zero diagonal)        */
+  HODLR2D_INV_R = 3, /* 1 / r                     (Eq. 1byr, zero diagonal)      */
+  HODLR2D_PHI1 = 4,  /* log r / log a (r >= a), (r log r - 1)/(a log a - 1) else */
+  HODLR2D_PHI2 = 5   /* a / r (r >= a), r / a else            (Sec. 5.2, Eq. ker) */
+} hodlr2d_kernel_kind;
+
+typedef struct {
+  int kind;          /* hodlr2d_kernel_kind                                    */
+  double a;          /* shape parameter of IMQ, MQ, PHI1, PHI2                 */
+  int diag_mode;     /* 0: A_ii = phi(0) (IMQ 1/a, MQ a, PHI1 -1/(a log a - 1),
+                        PHI2 0; LOG and INV_R 0); 1: A_ii = diag_value
+                        (beta of Eq. ker, or a panel self-term)                */
+  double diag_value;
+} hodlr2d_kernel;
+
+/* ----- arithmetic of the product ----- */
+typedef enum {
+  /* factors stored in IEEE binary64, products and sums in binary64 */
+  HODLR2D_MODE_F64 = 0,
+  /* factors stored as unevaluated float pairs hi + lo (8 bytes, ~48-bit
+     significand), products and sums in float-float arithmetic (Dekker 1971
+     products, Knuth two-sum); the near field in the same arithmetic */
+  HODLR2D_MODE_DF32 = 1,
+  /* factors stored in binary32, binary32 products and sums */
+  HODLR2D_MODE_F32 = 2,
+  /* factors stored in bfloat16, binary32 products and sums */
+  HODLR2D_MODE_BF16 = 3
+} hodlr2d_mode;
+
+/* ----- build options ----- */
+typedef struct {
+  double root[3];  /* {x0, y0, w}: the root box [x0,x0+w] x [y0,y0+w].  w <= 0:
+                      the bounding square of the points (centred on their
+                      bounding box) -- the default.                            */
+  int levels;      /* < 0 (default): kappa = smallest depth whose leaves all
+                      hold <= leaf_size points (Alg. 1); >= 0: force kappa.    */
+  int compress;    /* 1 (default): run ACA; 0: tree and lists only, factors
+                      come from hodlr2d_import_factors.                        */
+  int max_rank;    /* ACA rank cap per block (default 256).  A block that hits
+                      the cap before eps is counted in stats.unconverged.      */
+  int mode;        /* hodlr2d_mode used by hodlr2d_matvec (default F64).      */
+} hodlr2d_opts;
+
+typedef struct hodlr2d* hodlr2d_t;
+
+/* Fill *opts with the defaults listed above. */
+void hodlr2d_default_opts(hodlr2d_opts* opts);
+
+/* InitializeHODLR2D (Alg. 1): quadtree, edge and interaction lists (Defs. ec,
+ * ic), ACA of every admissible pair at tolerance eps.
+ *   points:    N x 2 row-major {x_i, y_i}, host or device; copied.
+ *   n:         N >= 1.
+ *   kernel:    entry rule; a > 0 where the kind uses it.
+ *   leaf_size: N_max >= 1 of Alg. 1.
+ *   eps:       ACA tolerance, 0 < eps < 1.
+ *   out:       receives the handle (unchanged on error).
+ * The kernels are radial, so A(Y,X) = A(X,Y)^T: each unordered admissible
+ * pair is compressed once (rows: the box with the smaller Morton key) and
+ * serves both directions.  Errors: ARG, OOM, CUDA, DEPTH. */
+int hodlr2d_build(const double* points, int64_t n, hodlr2d_kernel kernel,
+                  int leaf_size, double eps, hodlr2d_t* out);
+
+/* As hodlr2d_build with options (opts may be NULL for the defaults). */
+int hodlr2d_build_ex(const double* points, int64_t n, hodlr2d_kernel kernel,
+                     int leaf_size, double eps, const hodlr2d_opts* opts,
+                     hodlr2d_t* out);
+
+/* MatVec (Alg. 2): y = K_hat x in the handle's default mode.
+ *   x: n x nrhs column-major, host or device (read only).
+ *   y: n x nrhs column-major, host or device (overwritten).
+ *   nrhs >= 1.
+ * With device x and y the call is asynchronous on the handle's stream; with a
+ * host x or y it returns after y is written.  Errors: ARG, STATE, CUDA. */
+int hodlr2d_matvec(hodlr2d_t h, const double* x, double* y, int nrhs);
+
+/* As hodlr2d_matvec in an explicit hodlr2d_mode.  Modes other than F64 need a
+ * prior hodlr2d_prepare(h, mode) (else HODLR2D_ERR_STATE). */
+int hodlr2d_matvec_ex(hodlr2d_t h, const double* x, double* y, int nrhs, int mode);
+
+/* Make the factor copy that a mode reads (allocates device memory once; the
+ * F64 factors stay).  Errors: ARG, OOM, CUDA, STATE. */
+int hodlr2d_prepare(hodlr2d_t h, int mode);
+
+/* Restarted GMRES for A x = b with the HODLR2D product (Sec. 5.2, 5.3), all
+ * in FP64 on the GPU.  b, x: n vectors, host or device; x holds x0 on entry
+ * and the solution on return.  Stops at |b - A x| <= tol |b|.
+ * hodlr2d_gmres uses restart 50 and maxit = min(10 n, 100000) matvecs. */
+int hodlr2d_gmres(hodlr2d_t h, const double* b, double* x, double tol);
+
+/* As hodlr2d_gmres with explicit restart length, matvec cap, and outputs
+ * (iters: matvecs used, relres: final |b - A x| / |b|; either may be NULL).
+ * inner_mode: the hodlr2d_mode of the products inside each cycle; with a mode
+ * other than F64 the solver runs iterative refinement: residuals r = b - A x
+ * in F64, corrections solved with inner_mode.  Returns HODLR2D_ERR_NOCONV
+ * (with x and the outputs filled) when maxit is reached first. */
+int hodlr2d_gmres_ex(hodlr2d_t h, const double* b, double* x, double tol,
+                     int restart, int maxit, int inner_mode, int* iters,
+                     double* relres);
+
+/* ----- statistics (Sec. 5 notation: kappa, r_m, CR, memory, T_I) ----- */
+#define HODLR2D_MAX_LEVELS 15
+typedef struct {
+  int64_t n;
+  int kappa;
+  double root[3];
+  int64_t npairs;                            /* stored (unordered) pairs      */
+  int64_t pairs_per_level[HODLR2D_MAX_LEVELS];
+  int64_t values_per_level[HODLR2D_MAX_LEVELS]; /* sum (|X|+|Y|) k           */
+  int max_rank_per_level[HODLR2D_MAX_LEVELS];
+  int max_rank;                              /* r_m                           */
+  int64_t far_values;                        /* stored factor values          */
+  int64_t near_entries;                      /* dense leaf entries per product */
+  int64_t unconverged;                       /* pairs that hit max_rank       */
+  double compression_ratio;                  /* (far_values + near_entries)/N^2 */
+  double build_ms[4];                        /* tree, lists, ACA, pack        */
+  int64_t bytes_per_matvec[4];               /* algorithmic bytes, per mode   */
+} hodlr2d_stats;
+
+int hodlr2d_get_stats(hodlr2d_t h, hodlr2d_stats* s);
+
+/* ----- tracing: per-phase device time of the product -----
+ * Phases of one product: 0 gather x, 1 near field, 2 far-field projection,
+ * 3 projection sums, 4 far-field expansion, 5 combine and scatter y,
+ * 6 fused far field, 7 other.  While enabled, each phase's launches are
+ * bracketed by CUDA events on the handle's stream.  hodlr2d_profile(h, 1)
+ * resets and starts recording, (h, 0) stops.  hodlr2d_get_profile
+ * synchronises the stream and returns, per phase, the summed milliseconds,
+ * the number of kernel launches, and the algorithmic bytes one launch moves
+ * (arrays of HODLR2D_NPHASE entries; any may be NULL). */
+#define HODLR2D_NPHASE 8
+int hodlr2d_profile(hodlr2d_t h, int enable);
+int hodlr2d_get_profile(hodlr2d_t h, double* ms, int64_t* launches, int64_t* bytes);
+
+/* Queue the handle's work on a cudaStream_t (passed as void*). */
+int hodlr2d_set_stream(hodlr2d_t h, void* stream);
+
+/* ----- tree introspection (tests, tools) ----- */
+/* perm[i] = original index of the point at tree position i (Morton order of
+ * the leaves, ascending original index inside a leaf).  perm: n int64, host. */
+int hodlr2d_get_perm(hodlr2d_t h, int64_t* perm);
+/* Stored pairs: for pair p, info[6p..6p+5] = {level, ixX, iyX, ixY, iyY, rank}
+ * with X the row side.  Pass info = NULL to get the count in *npairs. */
+int hodlr2d_get_pairs(hodlr2d_t h, int64_t* npairs, int32_t* info);
+
+/* ----- factor exchange (checkpoint / resume, and tests) -----
+ * Flat layout shared by import and export: npairs pairs, each
+ *   info[6p..6p+5] = {level, ixX, iyX, ixY, iyY, rank},
+ *   values[offsets[p] .. offsets[p+1]) = U (|X| x rank) then V (|Y| x rank),
+ *   each column-major, rows ordered by ascending original point index.
+ * Import requires a handle built with the same points, kernel and tree and
+ * exactly its set of stored pairs (any order); all host pointers.
+ * Errors: ARG (pair set or sizes differ), OOM, CUDA. */
+int hodlr2d_import_factors(hodlr2d_t h, int64_t npairs, const int32_t* info,
+                           const int64_t* offsets, const double* values);
+/* Export: pass values = NULL to get *npairs and *nvalues only. */
+int hodlr2d_export_factors(hodlr2d_t h, int64_t* npairs, int64_t* nvalues,
+                           int32_t* info, int64_t* offsets, double* values);
+
+void hodlr2d_free(hodlr2d_t h);
+const char* hodlr2d_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HODLR2D_H */

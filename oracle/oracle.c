@@ -321,16 +321,24 @@ static int build_lists(orc_h2d* h) {
     const int64_t nb = nboxes(l);
     h->e_off[l] = (int64_t*)calloc((size_t)nb + 1, sizeof(int64_t));
     h->i_off[l] = (int64_t*)calloc((size_t)nb + 1, sizeof(int64_t));
-    h->e_lst[l] = (int64_t*)malloc((size_t)(4 * nb + 1) * sizeof(int64_t));
-    h->i_lst[l] = (int64_t*)malloc((size_t)(15 * nb + 1) * sizeof(int64_t));
-    h->i_pair[l] = (int64_t*)malloc((size_t)(15 * nb + 1) * sizeof(int64_t));
-    if (!h->e_off[l] || !h->i_off[l] || !h->e_lst[l] || !h->i_lst[l] || !h->i_pair[l])
-      return -2;
-    int64_t ne = 0, ni = 0;
+    /* list storage grows with the non-empty boxes (deep trees are sparse) */
+    int64_t cap = 64;
+    h->e_lst[l] = (int64_t*)malloc((size_t)cap * 4 * sizeof(int64_t));
+    h->i_lst[l] = (int64_t*)malloc((size_t)cap * 15 * sizeof(int64_t));
+    if (!h->e_off[l] || !h->i_off[l] || !h->e_lst[l] || !h->i_lst[l]) return -2;
+    int64_t ne = 0, ni = 0, nonempty = 0;
     for (int64_t b = 0; b < nb; ++b) {
       h->e_off[l][b] = ne;
       h->i_off[l][b] = ni;
       if (box_count(h, l, b) == 0) continue;
+      if (++nonempty > cap) {
+        cap *= 2;
+        int64_t* ne_ = (int64_t*)realloc(h->e_lst[l], (size_t)cap * 4 * sizeof(int64_t));
+        if (ne_) h->e_lst[l] = ne_;
+        int64_t* ni_ = (int64_t*)realloc(h->i_lst[l], (size_t)cap * 15 * sizeof(int64_t));
+        if (ni_) h->i_lst[l] = ni_;
+        if (!ne_ || !ni_) return -2;
+      }
       int32_t cx, cy;
       orc_paper_coords(l, b, &cx, &cy);
       /* E_C: same-level boxes sharing an edge with C (at most 4) */
@@ -361,6 +369,8 @@ static int build_lists(orc_h2d* h) {
     }
     h->e_off[l][nb] = ne;
     h->i_off[l][nb] = ni;
+    h->i_pair[l] = (int64_t*)malloc((size_t)(ni + 1) * sizeof(int64_t));
+    if (!h->i_pair[l]) return -2;
   }
   return 0;
 }

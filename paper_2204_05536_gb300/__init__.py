@@ -1,0 +1,227 @@
+"""GB300 (sm_103a) HODLR2D: quadtree, admissibility lists, batched ACA and
+the O(p N log N) matrix-vector product of "HODLR2D: A new class of
+hierarchical matrices" (arXiv 2204.05536), behind the C ABI of
+``include/hodlr2d.h``.
+
+This module marshals arguments only; every step runs in the CUDA library.
+Device buffers are torch CUDA tensors (float64); host arrays may be numpy.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import KINDS, MODES, HodlrError, check, load
+
+__all__ = ["HODLR2D", "kernel", "load", "HodlrError", "KINDS", "MODES"]
+
+
+def kernel(kind: str, a: float = 0.0, diag: float | None = None) -> _lib.Kernel:
+    """Kernel descriptor: kind in KINDS; diag=None keeps phi(0) (0 for log, 1/r)."""
+    return _lib.Kernel(KINDS[kind], float(a), 0 if diag is None else 1,
+                       0.0 if diag is None else float(diag))
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, keepalive) of a contiguous float64 torch tensor or numpy array."""
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float64:
+            raise TypeError("expected a float64 tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return C.c_void_p(x.data_ptr()), x
+    a = np.asarray(x)
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float64 array")
+    return C.c_void_p(a.ctypes.data), a
+
+
+def _colmajor(x, n):
+    """x (n,) or (n, nrhs) -> column-major buffer of the same kind, nrhs."""
+    if _is_torch(x):
+        if x.dim() == 1:
+            return x.contiguous(), 1
+        if x.shape[0] != n:
+            raise ValueError("x must have n rows")
+        return x.t().contiguous(), x.shape[1]
+    a = np.asarray(x, dtype=np.float64)
+    if a.ndim == 1:
+        return np.ascontiguousarray(a), 1
+    if a.shape[0] != n:
+        raise ValueError("x must have n rows")
+    return np.ascontiguousarray(a.T), a.shape[1]
+
+
+class HODLR2D:
+    """A built HODLR2D matrix on the current CUDA device (hodlr2d_build_ex)."""
+
+    def __init__(self, points, k: _lib.Kernel, leaf_size: int, eps: float, root=None,
+                 levels: int = -1, compress: bool = True, max_rank: int = 256,
+                 mode: str = "f64", stream=None):
+        lib = load()
+        self._lib = lib
+        opts = _lib.Opts()
+        lib.hodlr2d_default_opts(C.byref(opts))
+        if root is not None:
+            for i in range(3):
+                opts.root[i] = float(root[i])
+        opts.levels = int(levels)
+        opts.compress = int(bool(compress))
+        opts.max_rank = int(max_rank)
+        opts.mode = MODES[mode]
+        if _is_torch(points):
+            pts = points.contiguous()
+        else:
+            pts = np.ascontiguousarray(points, dtype=np.float64)
+        if pts.shape[-1] != 2 or len(pts.shape) != 2:
+            raise ValueError("points must be N x 2")
+        self.n = int(pts.shape[0])
+        p, keep = _ptr(pts)
+        h = C.c_void_p()
+        check(lib.hodlr2d_build_ex(p, self.n, k, int(leaf_size), float(eps), C.byref(opts),
+                                   C.byref(h)), "hodlr2d_build_ex")
+        self._h = h
+        self.kernel = k
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.hodlr2d_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- products -----------------------------------------------------------
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None (default)."""
+        s = 0 if stream is None else getattr(stream, "cuda_stream", stream)
+        check(self._lib.hodlr2d_set_stream(self._h, C.c_void_p(int(s))), "hodlr2d_set_stream")
+
+    def prepare(self, mode: str):
+        check(self._lib.hodlr2d_prepare(self._h, MODES[mode]), "hodlr2d_prepare")
+
+    def matvec(self, x, mode: str = "f64", out=None):
+        """y = K_hat x for x of shape (n,) or (n, nrhs).  torch CUDA tensors stay
+        on the device (asynchronous on the handle's stream); numpy arrays go
+        through host staging."""
+        xc, nrhs = _colmajor(x, self.n)
+        if out is None:
+            if _is_torch(xc):
+                import torch
+                yc = torch.empty_like(xc)
+            else:
+                yc = np.empty_like(xc)
+        else:
+            yc = out
+        px, kx = _ptr(xc)
+        py, ky = _ptr(yc)
+        check(self._lib.hodlr2d_matvec_ex(self._h, px, py, nrhs, MODES[mode]),
+              "hodlr2d_matvec_ex")
+        if out is not None:
+            return out
+        if nrhs == 1 and (x.dim() == 1 if _is_torch(x) else np.ndim(x) == 1):
+            return yc
+        return yc.t() if _is_torch(yc) else yc.T
+
+    def gmres(self, b, x0=None, tol: float = 1e-8, restart: int = 50, maxit: int | None = None,
+              inner_mode: str = "f64", raise_on_noconv: bool = False):
+        """Restarted GMRES for A x = b; returns (x, iters, relres, code)."""
+        if _is_torch(b):
+            import torch
+            x = torch.zeros_like(b) if x0 is None else x0.clone()
+        else:
+            x = np.zeros_like(np.asarray(b, dtype=np.float64)) if x0 is None else np.array(
+                x0, dtype=np.float64)
+        if maxit is None:
+            maxit = int(min(10 * self.n, 100000))
+        pb, kb = _ptr(b)
+        px, kx = _ptr(x)
+        it = C.c_int()
+        rr = C.c_double()
+        rc = self._lib.hodlr2d_gmres_ex(self._h, pb, px, float(tol), int(restart), int(maxit),
+                                        MODES[inner_mode], C.byref(it), C.byref(rr))
+        if rc not in (_lib.OK, _lib.ERR_NOCONV) or (raise_on_noconv and rc != _lib.OK):
+            check(rc, "hodlr2d_gmres_ex")
+        return x, it.value, rr.value, rc
+
+    # -- introspection --------------------------------------------------------
+    def stats(self) -> dict:
+        s = _lib.Stats()
+        check(self._lib.hodlr2d_get_stats(self._h, C.byref(s)), "hodlr2d_get_stats")
+        k = s.kappa
+        return {
+            "n": s.n, "kappa": k, "root": tuple(s.root), "npairs": s.npairs,
+            "pairs_per_level": list(s.pairs_per_level)[: k + 1],
+            "values_per_level": list(s.values_per_level)[: k + 1],
+            "max_rank_per_level": list(s.max_rank_per_level)[: k + 1],
+            "max_rank": s.max_rank, "far_values": s.far_values,
+            "near_entries": s.near_entries, "unconverged": s.unconverged,
+            "compression_ratio": s.compression_ratio, "build_ms": list(s.build_ms),
+            "bytes_per_matvec": dict(zip(MODES, list(s.bytes_per_matvec))),
+        }
+
+    def profile(self, enable: bool):
+        check(self._lib.hodlr2d_profile(self._h, int(bool(enable))), "hodlr2d_profile")
+
+    def get_profile(self) -> dict:
+        """Per phase: summed device ms, launches, algorithmic bytes per launch."""
+        ms = np.zeros(_lib.NPHASE)
+        nl = np.zeros(_lib.NPHASE, dtype=np.int64)
+        by = np.zeros(_lib.NPHASE, dtype=np.int64)
+        check(self._lib.hodlr2d_get_profile(self._h, C.c_void_p(ms.ctypes.data),
+                                            C.c_void_p(nl.ctypes.data),
+                                            C.c_void_p(by.ctypes.data)), "hodlr2d_get_profile")
+        return {name: {"ms": float(ms[i]), "launches": int(nl[i]), "bytes": int(by[i])}
+                for i, name in enumerate(_lib.PHASES)}
+
+    def perm(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.int64)
+        check(self._lib.hodlr2d_get_perm(self._h, C.c_void_p(out.ctypes.data)), "hodlr2d_get_perm")
+        return out
+
+    def pairs(self) -> np.ndarray:
+        """(npairs, 6) int32: level, ixX, iyX, ixY, iyY, rank."""
+        n = C.c_int64()
+        check(self._lib.hodlr2d_get_pairs(self._h, C.byref(n), None), "hodlr2d_get_pairs")
+        info = np.zeros((max(n.value, 1), 6), dtype=np.int32)
+        check(self._lib.hodlr2d_get_pairs(self._h, C.byref(n), C.c_void_p(info.ctypes.data)),
+              "hodlr2d_get_pairs")
+        return info[: n.value]
+
+    def import_factors(self, info, offsets, values):
+        info = np.ascontiguousarray(info, dtype=np.int32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        values = np.ascontiguousarray(values, dtype=np.float64)
+        check(self._lib.hodlr2d_import_factors(
+            self._h, int(info.shape[0]), C.c_void_p(info.ctypes.data),
+            C.c_void_p(offsets.ctypes.data), C.c_void_p(values.ctypes.data)),
+            "hodlr2d_import_factors")
+
+    def export_factors(self):
+        npairs, nvals = C.c_int64(), C.c_int64()
+        check(self._lib.hodlr2d_export_factors(self._h, C.byref(npairs), C.byref(nvals), None,
+                                               None, None), "hodlr2d_export_factors")
+        info = np.zeros((max(npairs.value, 1), 6), dtype=np.int32)
+        offs = np.zeros(npairs.value + 1, dtype=np.int64)
+        vals = np.zeros(max(nvals.value, 1))
+        check(self._lib.hodlr2d_export_factors(
+            self._h, C.byref(npairs), C.byref(nvals), C.c_void_p(info.ctypes.data),
+            C.c_void_p(offs.ctypes.data), C.c_void_p(vals.ctypes.data)), "hodlr2d_export_factors")
+        return info[: npairs.value], offs, vals[: nvals.value]

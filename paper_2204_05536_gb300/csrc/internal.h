@@ -1,0 +1,129 @@
+// Internal handle layout shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace h2d {
+
+// Stored factors of one level: pairs sorted by (row box, column box) in
+// Morton order; pair p's U (|X| x k, column-major) starts at foff[p] and its
+// V (|Y| x k, column-major) follows at foff[p] + |X| k.
+struct Level {
+  int l = 0;
+  int64_t npairs = 0;
+  int32_t* d_px = nullptr;       // row box (Morton id at level l)
+  int32_t* d_py = nullptr;       // column box
+  int32_t* d_rank = nullptr;     // k per pair
+  int64_t* d_foff = nullptr;     // npairs + 1 value offsets
+  int64_t* d_toff = nullptr;     // npairs + 1 offsets into the projection buffer
+  double* d_fac = nullptr;       // F64 factor values
+  void* d_fac_mode[4] = {nullptr, nullptr, nullptr, nullptr};  // per hodlr2d_mode copy
+  int64_t nvalues = 0;
+  int max_rank = 0;
+  // per box: entries (pair * 2 + side) of its interaction list, ascending
+  // partner; side 0 = the box is the row side (applies U), 1 = column (V)
+  int32_t* d_ent_off = nullptr;  // 4^l + 1
+  int32_t* d_ent = nullptr;
+  int64_t nent = 0;
+  std::vector<int32_t> h_rank;   // host copy of the ranks
+  std::vector<int64_t> h_foff;
+};
+
+// One unit of the projection pass: rows [r0, r0 + nr) of one factor matrix.
+struct ProjTask {
+  int32_t level;
+  int32_t side;   // 0: V of the pair against x_Y -> t1 ; 1: U against x_X -> t2
+  int64_t pair;
+  int32_t r0, nr;
+  int64_t out;    // offset of its k partial sums (per right-hand side)
+};
+
+// One unit of the expansion pass: rows [r0, r0 + nr) of one box.
+struct ExpTask {
+  int32_t level;
+  int32_t box;
+  int32_t r0, nr;
+};
+
+}  // namespace h2d
+
+struct hodlr2d {
+  int device = 0;
+  cudaStream_t stream = 0;
+  int64_t n = 0;
+  hodlr2d_kernel kern{};
+  h2d::KernelParams kp{};
+  int leaf_size = 0;
+  double eps = 0;
+  hodlr2d_opts opts{};
+  int kappa = 0;
+  double root[3] = {0, 0, 0};
+
+  // tree (device)
+  double* d_x = nullptr;      // coordinates in tree order
+  double* d_y = nullptr;
+  int64_t* d_perm = nullptr;  // tree position -> original index
+  int32_t* d_leaf_off = nullptr;  // 4^kappa + 1 leaf offsets (Morton order)
+  std::vector<int32_t> h_leaf_off;
+
+  h2d::Level lev[HODLR2D_MAX_LEVELS];
+  bool has_factors = false;
+  bool prepared[4] = {true, false, false, false};
+
+  // matvec plan
+  int64_t nproj = 0, nexp = 0;
+  h2d::ProjTask* d_proj = nullptr;
+  h2d::ExpTask* d_exp = nullptr;
+  int64_t proj_partials = 0;   // sum of k over projection tasks
+  int64_t t_total = 0;         // sum of 2 k over pairs
+  int64_t* d_tred = nullptr;   // per (pair, side): first task and task count
+  int64_t nt_sides = 0;
+
+  // matvec scratch, sized for scratch_nrhs right-hand sides
+  int scratch_nrhs = 0;
+  double* d_xt = nullptr;      // n x nrhs, tree order
+  double* d_yl = nullptr;      // (kappa + 1) x n x nrhs, per-level results
+  double* d_part = nullptr;    // proj_partials x nrhs
+  double* d_t = nullptr;       // t_total x nrhs
+  double* d_io = nullptr;      // staging for host x / y (n x nrhs each)
+
+  hodlr2d_stats st{};
+
+  // tracing (hodlr2d_profile)
+  struct ProfRec {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<ProfRec> prof;
+  double prof_ms[HODLR2D_NPHASE] = {};
+  int64_t prof_launches[HODLR2D_NPHASE] = {};
+  int64_t prof_bytes[HODLR2D_NPHASE] = {};
+};
+
+namespace h2d {
+// Brackets the launches of one phase with events while profiling is on.
+struct PhaseScope {
+  hodlr2d* h;
+  int phase;
+  int nlaunch;
+  cudaEvent_t a = nullptr, b = nullptr;
+  PhaseScope(hodlr2d* h_, int phase_, int nlaunch_, int64_t bytes) : h(h_), phase(phase_), nlaunch(nlaunch_) {
+    if (!h->prof_on) return;
+    h->prof_bytes[phase] = bytes;
+    if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+      cudaEventRecord(a, h->stream);
+  }
+  ~PhaseScope() {
+    if (!h->prof_on || !a || !b) return;
+    cudaEventRecord(b, h->stream);
+    h->prof.push_back({phase, a, b});
+    h->prof_launches[phase] += nlaunch;
+  }
+};
+}  // namespace h2d

@@ -1,0 +1,223 @@
+"""GPU path against the CPU oracle, through the C ABI (needs a GB300).
+
+P1  same factors: the GPU product on factors imported from the oracle equals
+    the oracle's Alg. 2 product to relative 2-norm <= 1e-12.
+P2  independent builds: identical tree, lists and pair set; ranks equal on
+    >= 99.9% of pairs; each block within 10 eps of the dense block; the GPU
+    product within 10 eps of the direct product.
+Plus determinism, edge cases (tiny, ragged, empty boxes, kappa = 0, deep
+trees), several right-hand sides, and argument errors.
+"""
+import numpy as np
+import pytest
+
+from paper_2204_05536_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def h2d():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2204_05536_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def both(h2d, oracle, pts, kind, a, leaf, eps, diag=None, root=None, levels=-1, compress=True):
+    g = h2d.HODLR2D(pts, h2d.kernel(kind, a, diag), leaf, eps, root=root, levels=levels,
+                    compress=compress)
+    o = oracle.Oracle(pts, oracle.kernel(kind, a, diag), leaf, eps, root=root, levels=levels)
+    return g, o
+
+
+CASES = [
+    # (name, n, kind, a, leaf, eps)
+    ("imq4096", 4096, "imq", 1 / 64, 64, 1e-10),
+    ("mq3000", 3000, "mq", 0.02, 40, 1e-8),
+    ("log2500", 2500, "log", 0.0, 32, 1e-10),
+    ("invr1800", 1800, "inv_r", 0.0, 16, 1e-9),
+    ("phi1_2000", 2000, "phi1", 0.001, 50, 1e-10),
+    ("phi2_2000", 2000, "phi2", 0.001, 50, 1e-10),
+]
+
+
+@pytest.mark.parametrize("name,n,kind,a,leaf,eps", CASES)
+def test_tree_lists_and_pairs_match_oracle(h2d, oracle, name, n, kind, a, leaf, eps):
+    pts = inputs.uniform(n, seed=0)
+    g, o = both(h2d, oracle, pts, kind, a, leaf, eps)
+    st = g.stats()
+    assert st["kappa"] == o.kappa
+    assert np.allclose(st["root"], o.root, rtol=0, atol=0)
+    # every leaf holds the same points, in ascending original index
+    perm = g.perm()
+    k = o.kappa
+    pos = 0
+    # tree order: leaves in Morton order; compare each leaf's point set
+    m = 2 ** k
+    for key in range(4 ** k):
+        ix = int(sum(((key >> (2 * s)) & 1) << s for s in range(k)))
+        iy = int(sum(((key >> (2 * s + 1)) & 1) << s for s in range(k)))
+        want = o.box_points(k, oracle.paper_index(k, ix, iy))
+        got = perm[pos: pos + len(want)]
+        np.testing.assert_array_equal(got, want)
+        pos += len(want)
+    assert pos == n
+    # same stored pairs (level, row box, column box)
+    gp = g.pairs()
+    op = np.array([[d["level"], *d["x"], *d["y"], d["rank"]] for d, _, _ in o.pairs()])
+    gs = sorted(map(tuple, gp[:, :5].tolist()))
+    os_ = sorted(map(tuple, op[:, :5].tolist()))
+    assert gs == os_
+    # ranks agree on >= 99.9% of pairs (near-ties in a pivot may flip)
+    rk_g = {tuple(r[:5]): r[5] for r in gp.tolist()}
+    same = sum(rk_g[tuple(r[:5])] == r[5] for r in op.tolist())
+    assert same >= 0.999 * len(op)
+    assert st["unconverged"] == 0
+
+
+@pytest.mark.parametrize("name,n,kind,a,leaf,eps", CASES)
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_p1_same_factors_matches_oracle_matvec(h2d, oracle, name, n, kind, a, leaf, eps, nrhs):
+    pts = inputs.uniform(n, seed=0)
+    o = oracle.Oracle(pts, oracle.kernel(kind, a), leaf, eps)
+    g = h2d.HODLR2D(pts, h2d.kernel(kind, a), leaf, eps, compress=False)
+    g.import_factors(*o.export_factors())
+    x = inputs.rhs(n, nrhs, seed=1)
+    y_o = o.matvec(x)
+    y_g = g.matvec(torch.from_numpy(np.ascontiguousarray(x)).cuda()).cpu().numpy()
+    assert rel(y_g, y_o) <= 1e-12
+    # host buffers through the same entry point
+    y_h = g.matvec(np.ascontiguousarray(x))
+    np.testing.assert_array_equal(y_h, y_g)
+
+
+@pytest.mark.parametrize("name,n,kind,a,leaf,eps", CASES)
+def test_p2_gpu_build_vs_direct(h2d, oracle, name, n, kind, a, leaf, eps):
+    pts = inputs.uniform(n, seed=0)
+    g = h2d.HODLR2D(pts, h2d.kernel(kind, a), leaf, eps)
+    x = inputs.rhs(n, seed=2)
+    yd = oracle.direct_matvec(pts, oracle.kernel(kind, a), x)
+    y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, yd) <= 10 * eps
+
+
+def test_block_errors_of_gpu_factors(h2d, oracle):
+    n, eps = 3000, 1e-10
+    pts = inputs.uniform(n, seed=4)
+    k_o = oracle.kernel("imq", 0.02)
+    g = h2d.HODLR2D(pts, h2d.kernel("imq", 0.02), 48, eps)
+    o = oracle.Oracle(pts, k_o, 48, eps, compress=False)
+    info, offs, vals = g.export_factors()
+    worst = 0.0
+    for p in range(0, len(info), max(1, len(info) // 200)):
+        lv, ax, ay, bx, by, k = info[p]
+        I = o.box_points(lv, oracle.paper_index(lv, ax, ay))
+        J = o.box_points(lv, oracle.paper_index(lv, bx, by))
+        U = vals[offs[p]: offs[p] + len(I) * k].reshape(k, len(I)).T
+        V = vals[offs[p] + len(I) * k: offs[p + 1]].reshape(k, len(J)).T
+        A = np.array([[oracle.entry(pts, k_o, i, j) for j in J] for i in I])
+        worst = max(worst, rel(U @ V.T, A))
+    assert worst <= 10 * eps
+
+
+def test_deterministic(h2d):
+    pts = inputs.uniform(5000, seed=3)
+    g = h2d.HODLR2D(pts, h2d.kernel("mq", 0.01), 32, 1e-8)
+    x = torch.from_numpy(inputs.rhs(5000, 2, seed=5)).cuda()
+    a = g.matvec(x)
+    b = g.matvec(x)
+    assert torch.equal(a, b)
+    g2 = h2d.HODLR2D(pts, h2d.kernel("mq", 0.01), 32, 1e-8)
+    assert np.array_equal(g.export_factors()[2], g2.export_factors()[2])
+
+
+def test_kappa0_and_tiny(h2d, oracle):
+    for n in (1, 2, 7, 300):
+        pts = inputs.uniform(n, seed=n)
+        g = h2d.HODLR2D(pts, h2d.kernel("imq", 0.05), 1000, 1e-10)
+        assert g.stats()["kappa"] == 0
+        x = inputs.rhs(n, 2, seed=1)
+        yd = oracle.direct_matvec(pts, oracle.kernel("imq", 0.05), x)
+        y = g.matvec(np.ascontiguousarray(x))
+        assert rel(y, yd) <= 1e-14
+
+
+def test_ragged_empty_boxes_and_deep_tree(h2d, oracle):
+    rng = np.random.default_rng(8)
+    pts = np.concatenate([rng.normal(0.3, 0.01, (700, 2)), rng.normal(-0.5, 0.05, (500, 2)),
+                          rng.uniform(-1, 1, (300, 2))])
+    cases = [(pts, 6), (pts, 33), (inputs.uniform(1500, seed=12), 1)]
+    for pts, leaf in cases:
+        g, o = both(h2d, oracle, pts, "imq", 0.001, leaf, 1e-10)
+        assert g.stats()["kappa"] == o.kappa
+        x = inputs.rhs(len(pts), seed=3)
+        g2 = h2d.HODLR2D(pts, h2d.kernel("imq", 0.001), leaf, 1e-10, compress=False)
+        g2.import_factors(*o.export_factors())
+        assert rel(g2.matvec(x), o.matvec(x)) <= 1e-12
+        yd = oracle.direct_matvec(pts, oracle.kernel("imq", 0.001), x)
+        assert rel(g.matvec(x), yd) <= 1e-9
+
+
+def test_forced_levels_and_root(h2d, oracle):
+    pts = inputs.uniform(2000, seed=6)
+    for levels in (0, 1, 2, 5):
+        g, o = both(h2d, oracle, pts, "log", 0.0, 10, 1e-10, root=(-1.0, -1.0, 2.0),
+                    levels=levels)
+        assert g.stats()["kappa"] == levels
+        x = inputs.rhs(2000, seed=1)
+        yd = oracle.direct_matvec(pts, oracle.kernel("log"), x)
+        assert rel(g.matvec(x), yd) <= 1e-9
+
+
+def test_errors(h2d):
+    pts = inputs.uniform(100, seed=1)
+    bad = pts.copy()
+    bad[5, 0] = np.nan
+    with pytest.raises(h2d.HodlrError) as e:
+        h2d.HODLR2D(bad, h2d.kernel("imq", 0.1), 8, 1e-8)
+    assert e.value.code == -1
+    g = h2d.HODLR2D(pts, h2d.kernel("imq", 0.1), 8, 1e-8, compress=False)
+    with pytest.raises(h2d.HodlrError) as e:
+        g.matvec(np.zeros(100))
+    assert e.value.code == -7  # no factors yet
+
+
+def test_gmres_solves_rbf_system(h2d, oracle):
+    """Eq. ker: beta lambda_i + sum_{j != i} phi(r_ij) lambda_j = f_i with
+    beta = N (Sec. 5.2)."""
+    n = 2500
+    pts = inputs.uniform(n, seed=2)
+    lam = inputs.rhs(n, seed=9)
+    ko = oracle.kernel("phi2", 0.001, diag=float(n))
+    f = oracle.direct_matvec(pts, ko, lam)
+    g = h2d.HODLR2D(pts, h2d.kernel("phi2", 0.001, diag=float(n)), 50, 1e-12)
+    x, it, rr, code = g.gmres(torch.from_numpy(f).cuda(), tol=1e-10)
+    assert code == 0 and rr <= 1e-10
+    assert rel(x.cpu().numpy(), lam) <= 1e-8
+    # host buffers
+    xh, it2, rr2, code2 = g.gmres(f, tol=1e-10)
+    assert code2 == 0 and np.array_equal(xh, x.cpu().numpy())
+
+
+def test_full_size_sampled_rows(h2d, oracle):
+    """N = 2^20 uniform points, MQ a = 2^-10, leaf 64, eps = 1e-8, one
+    right-hand side: 256 seeded rows against the direct product."""
+    n, eps = 1 << 20, 1e-8
+    pts = inputs.uniform(n, seed=0)
+    a = 2.0 ** -10
+    g = h2d.HODLR2D(pts, h2d.kernel("mq", a), 64, eps, root=(-1.0, -1.0, 2.0))
+    st = g.stats()
+    assert st["kappa"] == 8 and st["unconverged"] == 0
+    x = inputs.rhs(n, seed=1)
+    y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    rows = np.random.default_rng(7).choice(n, 256, replace=False)
+    yd = oracle.direct_rows(pts, oracle.kernel("mq", a), x, rows)
+    assert rel(y[rows], yd) <= 10 * eps
