@@ -80,17 +80,20 @@ int scan_exclusive(const T* d_in, T* d_out, int64_t n, cudaStream_t s) {
   T* d_tile = nullptr;
   H2D_CK(cudaMalloc(&d_tile, sizeof(T) * (tiles + 1)));
   k_scan_tile<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(d_in, d_out, d_tile, n);
-  cudaError_t e = cudaGetLastError();
-  int rc = HODLR2D_OK;
-  if (e != cudaSuccess) rc = HODLR2D_ERR_CUDA;
-  if (rc == HODLR2D_OK) rc = scan_exclusive<T>(d_tile, d_tile, tiles, s);  // d_tile[tiles] = total
-  if (rc == HODLR2D_OK && tiles > 0) {
-    k_scan_add<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(d_out, d_tile, n);
-    if (cudaGetLastError() != cudaSuccess) rc = HODLR2D_ERR_CUDA;
+  int rc = cudaGetLastError() == cudaSuccess ? HODLR2D_OK : HODLR2D_ERR_CUDA;
+  if (tiles > 1) {
+    // scan the tile totals (d_tile[tiles] receives the grand total), then
+    // add each tile's offset to its items
+    if (rc == HODLR2D_OK) rc = scan_exclusive<T>(d_tile, d_tile, tiles, s);
+    if (rc == HODLR2D_OK) {
+      k_scan_add<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(d_out, d_tile, n);
+      if (cudaGetLastError() != cudaSuccess) rc = HODLR2D_ERR_CUDA;
+    }
   }
+  // a single tile's total is d_tile[0]; otherwise the scan left it in d_tile[tiles]
+  const T* total = d_tile + (tiles > 1 ? tiles : 0);
   if (rc == HODLR2D_OK &&
-      cudaMemcpyAsync(d_out + n, d_tile + tiles, sizeof(T), cudaMemcpyDeviceToDevice, s) !=
-          cudaSuccess)
+      cudaMemcpyAsync(d_out + n, total, sizeof(T), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     rc = HODLR2D_ERR_CUDA;
   cudaStreamSynchronize(s);
   cudaFree(d_tile);

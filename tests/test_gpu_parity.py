@@ -207,9 +207,35 @@ def test_gmres_solves_rbf_system(h2d, oracle):
     assert code2 == 0 and np.array_equal(xh, x.cpu().numpy())
 
 
+def test_independent_builds_agree_at_2e16(h2d, oracle):
+    """N = 2^16 of the headline recipe (uniform, MQ a = 1/sqrt(N), leaf 64,
+    eps = 1e-8): GPU and oracle build independently; the same pivots give the
+    same factors, so the two products agree far below eps (a rare pivot flip
+    on a near-tie would show up as an eps-sized difference)."""
+    n, eps = 1 << 16, 1e-8
+    pts = inputs.uniform(n, seed=0)
+    a = 1.0 / np.sqrt(n)
+    g = h2d.HODLR2D(pts, h2d.kernel("mq", a), 64, eps, root=(-1.0, -1.0, 2.0))
+    o = oracle.Oracle(pts, oracle.kernel("mq", a), 64, eps, root=(-1.0, -1.0, 2.0))
+    gp = {tuple(r[:5]): r[5] for r in g.pairs().tolist()}
+    op = {(d["level"], *d["x"], *d["y"]): d["rank"] for d, _, _ in o.pairs()}
+    assert gp.keys() == op.keys()
+    assert sum(gp[k] == op[k] for k in op) >= 0.999 * len(op)
+    x = inputs.rhs(n, seed=1)
+    y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, o.matvec(x)) <= 1e-10
+
+
 def test_full_size_sampled_rows(h2d, oracle):
     """N = 2^20 uniform points, MQ a = 2^-10, leaf 64, eps = 1e-8, one
-    right-hand side: 256 seeded rows against the direct product."""
+    right-hand side, 256 seeded rows against the direct product.
+
+    ACA's stopping rule |u||v| <= eps |S_k|_F bounds each block's error
+    relative to the block, not relative to |A x|: for MQ the blocks carry a
+    large constant component that a zero-mean x cancels, so the product's
+    relative error exceeds eps on the coarse levels.  The oracle itself gives
+    2.5e-7 (25 eps) at N = 2^18 on these rows.  Bounds: relative 2-norm
+    <= 50 eps, and per row |dy_i| <= eps * sum_j |A_ij| |x_j|."""
     n, eps = 1 << 20, 1e-8
     pts = inputs.uniform(n, seed=0)
     a = 2.0 ** -10
@@ -219,5 +245,8 @@ def test_full_size_sampled_rows(h2d, oracle):
     x = inputs.rhs(n, seed=1)
     y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     rows = np.random.default_rng(7).choice(n, 256, replace=False)
-    yd = oracle.direct_rows(pts, oracle.kernel("mq", a), x, rows)
-    assert rel(y[rows], yd) <= 10 * eps
+    ko = oracle.kernel("mq", a)
+    yd = oracle.direct_rows(pts, ko, x, rows)
+    assert rel(y[rows], yd) <= 50 * eps
+    scale = oracle.direct_rows(pts, ko, np.abs(x), rows)  # MQ > 0: sum |A_ij||x_j|
+    assert np.max(np.abs(y[rows] - yd) / scale) <= eps
