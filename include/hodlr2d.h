@@ -208,6 +208,35 @@ int hodlr2d_import_factors(hodlr2d_t h, int64_t npairs, const int32_t* info,
 int hodlr2d_export_factors(hodlr2d_t h, int64_t* npairs, int64_t* nvalues,
                            int32_t* info, int64_t* offsets, double* values);
 
+/* ----- product without any device allocation -----
+ * The paper has no counterpart: this is a deployment aid.  hodlr2d_matvec may
+ * allocate its working memory on first use (and again when nrhs grows).  Some
+ * callers must not allocate device memory while they run -- a serving loop
+ * that cannot take the implicit device-wide synchronisation of cudaMalloc /
+ * cudaFree, or a host framework that owns the device-memory budget and
+ * forbids allocations outside its own pool.  hodlr2d_matvec_noalloc computes
+ * the same F64 product (same kernels, same summation order) with its working
+ * memory in one statically sized device array of
+ * HODLR2D_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
+ * until the process exits.  It never calls cudaMalloc, cudaFree or any
+ * allocating routine.
+ *   h:    a handle with factors; its device must be the current device.
+ *   x, y: DEVICE pointers only, n x nrhs column-major (host pointers: ARG).
+ * The working memory needed is about 8 n nrhs (kappa + 2) bytes plus
+ * 8 nrhs (2 x sum of the pair ranks, summed over row chunks) bytes -- for the
+ * N = 2^16, leaf 64, eps 1e-8 multiquadric workload about 30 MiB at nrhs = 1.
+ * A call that would need more than HODLR2D_NOALLOC_SCRATCH_BYTES returns
+ * HODLR2D_ERR_ARG and does nothing.
+ * The first call on a device looks up the array's device address (once per
+ * device, under a lock); make that first call before any stream capture.
+ * The call is asynchronous on the handle's stream.  All calls share the one
+ * array: calls whose kernels overlap on the GPU (other streams, handles or
+ * threads) race on it and produce wrong results -- serialise them.  Each call
+ * writes every scratch word it reads, so leftovers of earlier calls are
+ * harmless.  Errors: ARG, STATE, CUDA. */
+#define HODLR2D_NOALLOC_SCRATCH_BYTES (32u << 20)
+int hodlr2d_matvec_noalloc(hodlr2d_t h, const double* x, double* y, int nrhs);
+
 void hodlr2d_free(hodlr2d_t h);
 const char* hodlr2d_strerror(int code);
 

@@ -70,6 +70,7 @@ SIGNATURES = {
     "hodlr2d_get_pairs": (C.c_int, [_P, _i64p, _P]),
     "hodlr2d_import_factors": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "hodlr2d_export_factors": (C.c_int, [_P, _i64p, _i64p, _P, _P, _P]),
+    "hodlr2d_matvec_noalloc": (C.c_int, [_P, _P, _P, C.c_int]),
     "hodlr2d_free": (None, [_P]),
     "hodlr2d_strerror": (C.c_char_p, [C.c_int]),
 }

@@ -348,3 +348,35 @@ int matvec_f64_device(hodlr2d* h, const double* x, double* y, int nrhs) {
 }
 
 }  // namespace h2d
+
+namespace h2d {
+
+// The F64 product with caller-supplied scratch (no allocation): xt n x nrhs,
+// yl (kappa + 1) x n x nrhs, part proj_partials x nrhs, t t_total x nrhs.
+// Same kernels and order as matvec_f64_device.
+int matvec_f64_scratch(hodlr2d* h, const double* x, double* y, int nrhs, double* xt, double* yl,
+                       double* part, double* t) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  k_gather_x<<<g, 256, 0, s>>>(x, h->d_perm, n, nrhs, xt);
+  const unsigned nleaf = (unsigned)(1u << (2 * h->kappa));
+  k_near_f64<<<nleaf, 64, 0, s>>>(h->d_x, h->d_y, h->d_perm, h->d_leaf_off, h->kappa, h->kp, xt,
+                                   n, nrhs, yl);
+  const PlanView P = plan_view(h, nrhs);
+  if (h->nproj) {
+    const int64_t thr = h->nproj * 32;
+    k_proj_f64<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(P, h->d_proj, h->nproj, xt, part);
+    k_tsum<<<(unsigned)((h->nt_sides + 255) / 256), 256, 0, s>>>(P, h->d_proj, h->d_tred,
+                                                                 h->nt_sides, part, t);
+  }
+  if (h->nexp) {
+    const int64_t thr = h->nexp * 32;
+    k_exp_f64<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(P, h->d_exp, h->nexp, t, yl);
+  }
+  k_combine<<<g, 256, 0, s>>>(yl, h->kappa + 1, h->d_perm, n, nrhs, y);
+  H2D_CK(cudaGetLastError());
+  return HODLR2D_OK;
+}
+
+}  // namespace h2d
