@@ -229,9 +229,16 @@ __global__ void k_compact(const double* __restrict__ ws, const int64_t* __restri
   const int64_t k = rank[p];
   const double* U = ws + wsoff[blockIdx.x];
   const double* V = U + m * cap;
+  const int64_t lm = ldpad(m), ln = ldpad(n);
   double* out = fac + foff[p];
-  for (int64_t t = threadIdx.x; t < m * k; t += blockDim.x) out[t] = U[t];
-  for (int64_t t = threadIdx.x; t < n * k; t += blockDim.x) out[m * k + t] = V[t];
+  for (int64_t t = threadIdx.x; t < lm * k; t += blockDim.x) {
+    const int64_t q = t / lm, i = t - q * lm;
+    out[t] = i < m ? U[q * m + i] : 0.0;
+  }
+  for (int64_t t = threadIdx.x; t < ln * k; t += blockDim.x) {
+    const int64_t q = t / ln, j = t - q * ln;
+    out[lm * k + t] = j < n ? V[q * n + j] : 0.0;
+  }
 }
 
 // Compress every pair of every level; fills Level::{d_rank, d_foff, d_fac,
@@ -274,7 +281,7 @@ int aca_build(hodlr2d* h) {
     H2D_CK(cudaMalloc(&d_conv, sizeof(int32_t) * np));
     const int64_t mean_rows = tot_rows / (2 * np);
     // packed level buffer, grown as batches finish
-    int64_t fac_cap = 0, fac_used = 0;
+    int64_t fac_cap = 0, fac_used = 0, stored = 0;
     double* fac = nullptr;
     int64_t p0 = 0;
     while (p0 < np) {
@@ -335,7 +342,8 @@ int aca_build(hodlr2d* h) {
       int64_t add = 0;
       for (int64_t p = p0; p < p1; ++p) {
         L.h_foff[p] = fac_used + add;
-        add += (cnt(px[p]) + cnt(py[p])) * (int64_t)L.h_rank[p];
+        add += (ldpad(cnt(px[p])) + ldpad(cnt(py[p]))) * (int64_t)L.h_rank[p];
+        stored += (cnt(px[p]) + cnt(py[p])) * (int64_t)L.h_rank[p];
       }
       if (fac_used + add > fac_cap) {
         const int64_t ncap = std::max<int64_t>(fac_used + add, 2 * fac_cap);
@@ -365,6 +373,7 @@ int aca_build(hodlr2d* h) {
     }
     L.h_foff[np] = fac_used;
     L.nvalues = fac_used;
+    L.nstored = stored;
     L.d_fac = fac;
     if (!L.d_fac) H2D_CK(cudaMalloc(&L.d_fac, sizeof(double)));
     H2D_CK(cudaMemcpyAsync(L.d_foff, L.h_foff.data(), sizeof(int64_t) * (np + 1),

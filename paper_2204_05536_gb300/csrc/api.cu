@@ -16,8 +16,6 @@ int tree_build(hodlr2d* h, const double* d_pts);
 int lists_build(hodlr2d* h);
 int aca_build(hodlr2d* h);
 int matvec_plan(hodlr2d* h);
-int matvec_scratch(hodlr2d* h, int nrhs);
-int matvec_f64_device(hodlr2d* h, const double* x, double* y, int nrhs);
 int matvec_mode_device(hodlr2d* h, const double* x, double* y, int nrhs, int mode);
 int prepare_mode(hodlr2d* h, int mode);
 void free_modes(hodlr2d* h);
@@ -88,10 +86,10 @@ static void fill_stats(hodlr2d* h) {
   for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) {
     const Level& L = h->lev[l];
     s.pairs_per_level[l] = L.npairs;
-    s.values_per_level[l] = L.nvalues;
+    s.values_per_level[l] = L.nstored;
     s.max_rank_per_level[l] = L.max_rank;
     s.npairs += L.npairs;
-    s.far_values += L.nvalues;
+    s.far_values += L.nstored;
     s.max_rank = std::max(s.max_rank, L.max_rank);
   }
   // dense leaf entries: |X| (|X| + sum_{Y in E_X} |Y|)
@@ -138,6 +136,8 @@ static void free_handle(hodlr2d* h) {
     cudaFree(L.d_fac);
     cudaFree(L.d_ent_off);
     cudaFree(L.d_ent);
+    cudaFree(L.d_prow);
+    cudaFree(L.d_ppoff);
   }
   cudaFree(h->d_proj);
   cudaFree(h->d_exp);
@@ -268,10 +268,16 @@ int hodlr2d_matvec_ex(hodlr2d_t h, const double* x, double* y, int nrhs, int mod
   if (!h || !x || !y || nrhs < 1 || mode < 0 || mode > 3) return HODLR2D_ERR_ARG;
   if (!h->has_factors || !h->prepared[mode]) return HODLR2D_ERR_STATE;
   DeviceGuard g(h->device);
-  int rc = matvec_scratch(h, nrhs);
-  if (rc) return rc;
+  int rc = HODLR2D_OK;
   const bool xd = is_device_ptr(x), yd = is_device_ptr(y);
   const size_t bytes = sizeof(double) * h->n * nrhs;
+  if ((!xd || !yd) && h->io_nrhs < nrhs) {  // staging for host buffers
+    cudaFree(h->d_io);
+    h->d_io = nullptr;
+    h->io_nrhs = 0;
+    H2D_CK(cudaMalloc(&h->d_io, 2 * bytes));
+    h->io_nrhs = nrhs;
+  }
   const double* dx = x;
   double* dy = y;
   if (!xd) {
@@ -279,8 +285,7 @@ int hodlr2d_matvec_ex(hodlr2d_t h, const double* x, double* y, int nrhs, int mod
     dx = h->d_io;
   }
   if (!yd) dy = h->d_io + h->n * nrhs;
-  rc = mode == HODLR2D_MODE_F64 ? matvec_f64_device(h, dx, dy, nrhs)
-                                : matvec_mode_device(h, dx, dy, nrhs, mode);
+  rc = matvec_mode_device(h, dx, dy, nrhs, mode);
   if (rc) return rc;
   if (!yd) {
     H2D_CK(cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -408,7 +413,7 @@ int hodlr2d_import_factors(hodlr2d_t h, int64_t npairs, const int32_t* info,
       return h->h_leaf_off[(int64_t)(b + 1) << sh] - h->h_leaf_off[(int64_t)b << sh];
     };
     L.h_foff.assign(L.npairs + 1, 0);
-    int64_t tot_v = 0;
+    int64_t tot_v = 0, stored_v = 0;
     for (int64_t p = 0; p < L.npairs; ++p) {
       const int64_t q = where[l][p];
       const int k = info[6 * q + 5];
@@ -416,11 +421,13 @@ int hodlr2d_import_factors(hodlr2d_t h, int64_t npairs, const int32_t* info,
       if (k > std::min(m, nn) || offsets[q + 1] - offsets[q] != (m + nn) * k) return HODLR2D_ERR_ARG;
       L.h_rank[p] = k;
       L.h_foff[p] = tot_v;
-      tot_v += (m + nn) * k;
+      tot_v += (ldpad(m) + ldpad(nn)) * k;
+      stored_v += (m + nn) * k;
     }
     L.h_foff[L.npairs] = tot_v;
     L.nvalues = tot_v;
-    std::vector<double> fac(std::max<int64_t>(tot_v, 1));
+    L.nstored = stored_v;
+    std::vector<double> fac(std::max<int64_t>(tot_v, 1), 0.0);
     std::vector<int32_t> cx, cy;
     L.max_rank = 0;
     for (int64_t p = 0; p < L.npairs; ++p) {
@@ -432,11 +439,12 @@ int hodlr2d_import_factors(hodlr2d_t h, int64_t npairs, const int32_t* info,
       canonical_rows(perm, start(PY[l][p]), nn, cy);
       const double* U = values + offsets[q];
       const double* V = U + (int64_t)m * k;
+      const int64_t lm = ldpad(m), ln = ldpad(nn);
       double* Uo = fac.data() + L.h_foff[p];
-      double* Vo = Uo + (int64_t)m * k;
+      double* Vo = Uo + lm * k;
       for (int c = 0; c < k; ++c) {
-        for (int32_t r = 0; r < m; ++r) Uo[(int64_t)c * m + cx[r]] = U[(int64_t)c * m + r];
-        for (int32_t r = 0; r < nn; ++r) Vo[(int64_t)c * nn + cy[r]] = V[(int64_t)c * nn + r];
+        for (int32_t r = 0; r < m; ++r) Uo[c * lm + cx[r]] = U[(int64_t)c * m + r];
+        for (int32_t r = 0; r < nn; ++r) Vo[c * ln + cy[r]] = V[(int64_t)c * nn + r];
       }
     }
     H2D_CK(cudaMalloc(&L.d_rank, sizeof(int32_t) * (L.npairs + 1)));
@@ -464,7 +472,7 @@ int hodlr2d_export_factors(hodlr2d_t h, int64_t* npairs, int64_t* nvalues, int32
   int64_t tp = 0, tv = 0;
   for (int l = 1; l <= h->kappa; ++l) {
     tp += h->lev[l].npairs;
-    tv += h->lev[l].nvalues;
+    tv += h->lev[l].nstored;
   }
   *npairs = tp;
   *nvalues = tv;
@@ -495,13 +503,14 @@ int hodlr2d_export_factors(hodlr2d_t h, int64_t* npairs, int64_t* nvalues, int32
       canonical_rows(perm, sx, m, cx);
       canonical_rows(perm, sy, nn, cy);
       offsets[q] = o;
+      const int64_t lm = ldpad(m), ln = ldpad(nn);
       const double* U = fac.data() + L.h_foff[p];
-      const double* V = U + (int64_t)m * k;
+      const double* V = U + lm * k;
       double* Uo = values + o;
       double* Vo = Uo + (int64_t)m * k;
       for (int c = 0; c < k; ++c) {
-        for (int32_t r = 0; r < m; ++r) Uo[(int64_t)c * m + r] = U[(int64_t)c * m + cx[r]];
-        for (int32_t r = 0; r < nn; ++r) Vo[(int64_t)c * nn + r] = V[(int64_t)c * nn + cy[r]];
+        for (int32_t r = 0; r < m; ++r) Uo[(int64_t)c * m + r] = U[c * lm + cx[r]];
+        for (int32_t r = 0; r < nn; ++r) Vo[(int64_t)c * nn + r] = V[c * ln + cy[r]];
       }
       o += (int64_t)(m + nn) * k;
     }

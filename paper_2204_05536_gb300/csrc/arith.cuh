@@ -1,0 +1,170 @@
+// Arithmetic policies of the product kernels.
+//
+//   F64A   values and sums in IEEE binary64.
+//   DF32A  values stored as float pairs (hi, lo) with hi + lo the binary64
+//          value to ~2^-48 relative; products and sums in float-float
+//          arithmetic (Dekker's product via FMA, Knuth's two-sum).  On GB300
+//          binary32 FMA throughput is ~58x that of binary64, so this keeps
+//          binary64-level accuracy at memory speed.
+//
+// Float-float square root and reciprocal square root: one Newton-Raphson
+// correction of the binary32 estimate, evaluated with an exact square
+// (Karp & Markstein 1997 style), giving ~2^-44 relative accuracy.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace h2d {
+
+struct F64A {
+  typedef double val;
+  typedef double acc;
+  static __device__ __forceinline__ acc zero() { return 0.0; }
+  static __device__ __forceinline__ void fma(acc& s, val a, val b) { s = ::fma(a, b, s); }
+  static __device__ __forceinline__ val fin(acc s) { return s; }
+  static __device__ __forceinline__ val add(val a, val b) { return a + b; }
+  static __device__ __forceinline__ val from_double(double d) { return d; }
+  static __device__ __forceinline__ double to_double(val v) { return v; }
+  static __device__ __forceinline__ val vzero() { return 0.0; }
+  static __device__ __forceinline__ val warp_sum(acc a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+  }
+};
+
+struct DF32A {
+  typedef float2 val;  // x = hi, y = lo
+  typedef float2 acc;  // lazily normalised: hi exact running sum, lo collects errors
+  static __device__ __forceinline__ acc zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ val vzero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ void fma(acc& s, val a, val b) {
+    float p, e;
+    two_prod(a.x, b.x, p, e);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    float t, err;
+    two_sum(s.x, p, t, err);
+    s.x = t;
+    s.y = __fadd_rn(s.y, __fadd_rn(err, e));
+  }
+  static __device__ __forceinline__ val fin(acc s) {
+    float h, l;
+    fast_two_sum(s.x, s.y, h, l);
+    return make_float2(h, l);
+  }
+  static __device__ __forceinline__ val add(val a, val b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    float h, l;
+    fast_two_sum(s, e, h, l);
+    return make_float2(h, l);
+  }
+  static __device__ __forceinline__ val from_double(double d) {
+    const float h = __double2float_rn(d);
+    return make_float2(h, __double2float_rn(d - (double)h));
+  }
+  static __device__ __forceinline__ double to_double(val v) { return (double)v.x + (double)v.y; }
+  static __device__ __forceinline__ val warp_sum(acc a) {
+    val v = fin(a);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      val w;
+      w.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+      w.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+      v = add(v, w);
+    }
+    return v;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// float-float elementary functions for the near field
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 ffv_sub(float2 a, float2 b) {
+  return DF32A::add(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 ffv_mul(float2 a, float2 b) {
+  float p, e;
+  two_prod(a.x, b.x, p, e);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  float h, l;
+  fast_two_sum(p, e, h, l);
+  return make_float2(h, l);
+}
+// sqrt(a) for a >= 0: s = sqrt(a.hi) in binary32, then s + (a - s^2) / (2 s)
+__device__ __forceinline__ float2 ffv_sqrt(float2 a) {
+  if (!(a.x > 0.f)) return make_float2(0.f, 0.f);
+  const float s = __fsqrt_rn(a.x);
+  float p, e;
+  two_prod(s, s, p, e);
+  const float d = __fadd_rn(__fsub_rn(__fsub_rn(a.x, p), e), a.y);
+  const float c = __fdividef(d, 2.0f * s);
+  float h, l;
+  fast_two_sum(s, c, h, l);
+  return make_float2(h, l);
+}
+// 1/sqrt(a) for a > 0: r = rsqrt(a.hi), then r + r (1 - a r^2) / 2 with a r^2
+// formed from the exact square of r
+__device__ __forceinline__ float2 ffv_rsqrt(float2 a) {
+  const float r = rsqrtf(a.x);
+  float p, e;
+  two_prod(r, r, p, e);          // r^2 = p + e exactly
+  const float2 ar2 = ffv_mul(a, make_float2(p, e));
+  float one_minus = __fsub_rn(1.0f, ar2.x);  // exact (ar2 ~ 1)
+  one_minus = __fsub_rn(one_minus, ar2.y);
+  const float c = 0.5f * r * one_minus;
+  float h, l;
+  fast_two_sum(r, c, h, l);
+  return make_float2(h, l);
+}
+// 1/a: r = 1/a.hi, then r + r (1 - a r)
+__device__ __forceinline__ float2 ffv_rcp(float2 a) {
+  const float r = __frcp_rn(a.x);
+  const float2 ar = ffv_mul(a, make_float2(r, 0.f));
+  float one_minus = __fsub_rn(1.0f, ar.x);
+  one_minus = __fsub_rn(one_minus, ar.y);
+  const float c = r * one_minus;
+  float h, l;
+  fast_two_sum(r, c, h, l);
+  return make_float2(h, l);
+}
+__device__ __forceinline__ bool ffv_ge(float2 a, float2 b) {
+  return a.x > b.x || (a.x == b.x && a.y >= b.y);
+}
+
+// Kernel parameters in float-float, plus the binary64 set for the kernels
+// whose logarithm is evaluated in binary64 (log r, phi_1).
+struct KernelFF {
+  int kind;
+  float2 a, a2, inv_a, diag;
+  KernelParams p64;
+};
+
+__device__ __forceinline__ float2 entry_ff(const KernelFF& k, float2 xi, float2 yi, int64_t gi,
+                                           float2 xj, float2 yj, int64_t gj) {
+  if (gi == gj) return k.diag;
+  const float2 dx = ffv_sub(xi, xj), dy = ffv_sub(yi, yj);
+  const float2 r2 = DF32A::add(ffv_mul(dx, dx), ffv_mul(dy, dy));
+  switch (k.kind) {
+    case HODLR2D_IMQ: return ffv_rsqrt(DF32A::add(r2, k.a2));
+    case HODLR2D_MQ: return ffv_sqrt(DF32A::add(r2, k.a2));
+    case HODLR2D_INV_R: return ffv_rsqrt(r2);
+    case HODLR2D_PHI2: {
+      const float2 r = ffv_sqrt(r2);
+      if (ffv_ge(r, k.a)) return ffv_mul(k.a, ffv_rcp(r));
+      return ffv_mul(r, k.inv_a);
+    }
+    default: {  // log r and phi_1: binary64 logarithm of the float-float r^2
+      const double v = phi_r2(k.p64, (double)r2.x + (double)r2.y);
+      return DF32A::from_double(v);
+    }
+  }
+}
+
+}  // namespace h2d

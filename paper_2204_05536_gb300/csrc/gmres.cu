@@ -17,8 +17,6 @@
 namespace h2d {
 
 bool is_device_ptr(const void* p);
-int matvec_scratch(hodlr2d* h, int nrhs);
-int matvec_f64_device(hodlr2d* h, const double* x, double* y, int nrhs);
 int matvec_mode_device(hodlr2d* h, const double* x, double* y, int nrhs, int mode);
 
 constexpr int kDotBlocks = 304;  // 2 x 152 SMs
@@ -97,10 +95,7 @@ struct Work {
     H2D_CK(cudaGetLastError());
     return HODLR2D_OK;
   }
-  int matvec(const double* x, double* y, int mode) {
-    return mode == HODLR2D_MODE_F64 ? matvec_f64_device(h, x, y, 1)
-                                    : matvec_mode_device(h, x, y, 1, mode);
-  }
+  int matvec(const double* x, double* y, int mode) { return matvec_mode_device(h, x, y, 1, mode); }
   double norm(const double* v) {
     double r = 0.0;
     if (dots(v, 0, 1, v, &r) != HODLR2D_OK) return NAN;
@@ -185,7 +180,6 @@ int gmres_run(hodlr2d* h, const double* b, double* x, double tol, int restart, i
               int inner_mode, int* iters, double* relres) {
   const int64_t n = h->n;
   cudaStream_t s = h->stream;
-  H2D_TRY(matvec_scratch(h, 1));
   const bool bd = is_device_ptr(b), xd = is_device_ptr(x);
   Work W;
   W.h = h;
@@ -231,7 +225,7 @@ int gmres_run(hodlr2d* h, const double* b, double* x, double tol, int restart, i
       const unsigned gb = (unsigned)((n + 255) / 256);
       const double inner_rel = 1e-3;
       while (rc == HODLR2D_OK) {
-        rc = matvec_f64_device(h, X, w, 1);
+        rc = matvec_mode_device(h, X, w, 1, HODLR2D_MODE_F64);
         if (rc) break;
         ++used;
         k_axpby<<<gb, 256, 0, s>>>(1.0, B, -1.0, w, r, n);

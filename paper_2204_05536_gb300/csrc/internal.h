@@ -6,13 +6,19 @@
 
 #include <vector>
 
+#include "arith.cuh"
 #include "common.cuh"
 
 namespace h2d {
 
+__host__ __device__ __forceinline__ int64_t ldpad(int64_t r) { return r + (r & 1); }
+
 // Stored factors of one level: pairs sorted by (row box, column box) in
-// Morton order; pair p's U (|X| x k, column-major) starts at foff[p] and its
-// V (|Y| x k, column-major) follows at foff[p] + |X| k.
+// Morton order.  Columns are padded to an even length ld(r) = r + (r & 1)
+// (pad entries are zero) so that every column starts on a 16-byte boundary:
+// pair p's U (|X| x k, column-major, leading dimension ld(|X|)) starts at
+// foff[p] and its V (|Y| x k, leading dimension ld(|Y|)) at
+// foff[p] + ld(|X|) k.
 struct Level {
   int l = 0;
   int64_t npairs = 0;
@@ -23,8 +29,12 @@ struct Level {
   int64_t* d_toff = nullptr;     // npairs + 1 offsets into the projection buffer
   double* d_fac = nullptr;       // F64 factor values
   void* d_fac_mode[4] = {nullptr, nullptr, nullptr, nullptr};  // per hodlr2d_mode copy
-  int64_t nvalues = 0;
+  int64_t nvalues = 0;   // allocated values, padding included
+  int64_t nstored = 0;   // sum (|X| + |Y|) k: the values the method stores
   int max_rank = 0;
+  int64_t* d_prow = nullptr;   // 4^l + 1: first stored pair of each row box
+  int64_t* d_ppoff = nullptr;  // npairs + 1: partial-result offsets (|Y| per pair)
+  int64_t npart = 0;
   // per box: entries (pair * 2 + side) of its interaction list, ascending
   // partner; side 0 = the box is the row side (applies U), 1 = column (V)
   int32_t* d_ent_off = nullptr;  // 4^l + 1
@@ -50,6 +60,32 @@ struct ExpTask {
   int32_t r0, nr;
 };
 
+// Plan and scratch of the second-generation product (product.cu).
+struct V2Plan {
+  bool ready = false;
+  int lfuse = 1;  // first level handled by the fused kernel
+  ProjTask* d_proj = nullptr;
+  ExpTask* d_exp = nullptr;
+  int64_t* d_red = nullptr;
+  int64_t nproj = 0, nexp = 0, proj_partials = 0, nsides = 0;
+  int kmax = 1;
+  int64_t rmax_big = 1, rmax_small = 1;
+  int2* d_big = nullptr;
+  int2* d_small = nullptr;
+  int64_t nbig = 0, nsmall = 0;
+  int64_t pstride = 1;
+  int32_t* d_leaf_of = nullptr;
+  int scratch_nrhs = 0;
+  void* d_xt = nullptr;
+  void* d_yl = nullptr;
+  void* d_ppart = nullptr;
+  void* d_part = nullptr;
+  void* d_t = nullptr;
+  void* d_xf = nullptr;  // float-float coordinates (DF32)
+  void* d_yf = nullptr;
+  KernelFF kff{};
+};
+
 }  // namespace h2d
 
 struct hodlr2d {
@@ -72,6 +108,7 @@ struct hodlr2d {
   std::vector<int32_t> h_leaf_off;
 
   h2d::Level lev[HODLR2D_MAX_LEVELS];
+  h2d::V2Plan v2;
   bool has_factors = false;
   bool prepared[4] = {true, false, false, false};
 
@@ -91,6 +128,7 @@ struct hodlr2d {
   double* d_part = nullptr;    // proj_partials x nrhs
   double* d_t = nullptr;       // t_total x nrhs
   double* d_io = nullptr;      // staging for host x / y (n x nrhs each)
+  int io_nrhs = 0;
 
   hodlr2d_stats st{};
 

@@ -1,4 +1,6 @@
-// MatVec (Alg. 2) on the GPU, FP64.
+// MatVec (Alg. 2) on the GPU, FP64, first generation: kept as the product
+// behind hodlr2d_matvec_noalloc (caller-provided scratch) and for its plan
+// (projection / expansion task lists and t offsets, shared with product.cu).
 //
 //   1. x is gathered into tree order.
 //   2. Near field: every leaf X adds K(X,X) x_X + sum_{Y in E_X} K(X,Y) x_Y,
@@ -128,11 +130,12 @@ __global__ void k_proj_f64(PlanView P, const ProjTask* __restrict__ tasks, int64
   const int32_t nrow = T.side == 0 ? box_size(P.leaf_off, P.kappa, T.level, by) : m;
   const int32_t base = box_start(P.leaf_off, P.kappa, T.level, T.side == 0 ? by : bx);
   const int k = L.rank[T.pair];
-  const double* M = L.fac + L.foff[T.pair] + (T.side == 0 ? (int64_t)m * k : 0);
+  const double* M = L.fac + L.foff[T.pair] + (T.side == 0 ? ldpad(m) * k : 0);
+  const int64_t ld = ldpad(nrow);
   for (int c = 0; c < P.nrhs; ++c) {
     const double* xv = xt + c * P.n + base;
     for (int q = 0; q < k; ++q) {
-      const double* col = M + (int64_t)q * nrow;
+      const double* col = M + (int64_t)q * ld;
       double acc = 0.0;
       for (int i = T.r0 + lane; i < T.r0 + T.nr; i += 32) acc += col[i] * xv[i];
 #pragma unroll
@@ -185,10 +188,12 @@ __global__ void k_exp_f64(PlanView P, const ExpTask* __restrict__ tasks, int64_t
         const int side = code & 1;
         const int k = L.rank[p];
         int64_t off = L.foff[p];
-        if (side == 1) off += (int64_t)box_size(P.leaf_off, P.kappa, T.level, (uint32_t)L.px[p]) * k;
+        if (side == 1)
+          off += ldpad(box_size(P.leaf_off, P.kappa, T.level, (uint32_t)L.px[p])) * k;
         const double* M = L.fac + off;
         const double* tv = t + L.toff[p] * P.nrhs + (int64_t)side * k * P.nrhs + (int64_t)c * k;
-        for (int q = 0; q < k; ++q) acc += M[(int64_t)q * nX + i] * tv[q];
+        const int64_t ld = ldpad(nX);
+        for (int q = 0; q < k; ++q) acc += M[(int64_t)q * ld + i] * tv[q];
       }
       out[base + i + c * P.n] = acc;
     }
@@ -270,25 +275,6 @@ int matvec_plan(hodlr2d* h) {
   return HODLR2D_OK;
 }
 
-int matvec_scratch(hodlr2d* h, int nrhs) {
-  if (h->scratch_nrhs >= nrhs) return HODLR2D_OK;
-  cudaFree(h->d_xt);
-  cudaFree(h->d_yl);
-  cudaFree(h->d_part);
-  cudaFree(h->d_t);
-  cudaFree(h->d_io);
-  h->d_xt = h->d_yl = h->d_part = h->d_t = h->d_io = nullptr;
-  h->scratch_nrhs = 0;
-  const int64_t n = h->n;
-  H2D_CK(cudaMalloc(&h->d_xt, sizeof(double) * n * nrhs));
-  H2D_CK(cudaMalloc(&h->d_yl, sizeof(double) * n * nrhs * (h->kappa + 1)));
-  H2D_CK(cudaMalloc(&h->d_part, sizeof(double) * std::max<int64_t>(h->proj_partials, 1) * nrhs));
-  H2D_CK(cudaMalloc(&h->d_t, sizeof(double) * std::max<int64_t>(h->t_total, 1) * nrhs));
-  H2D_CK(cudaMalloc(&h->d_io, sizeof(double) * 2 * n * nrhs));
-  h->scratch_nrhs = nrhs;
-  return HODLR2D_OK;
-}
-
 static PlanView plan_view(const hodlr2d* h, int nrhs) {
   PlanView P;
   for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) {
@@ -302,58 +288,14 @@ static PlanView plan_view(const hodlr2d* h, int nrhs) {
   return P;
 }
 
-// y = K_hat x with device x, y (caller order).  Scratch must be sized.
-int matvec_f64_device(hodlr2d* h, const double* x, double* y, int nrhs) {
-  cudaStream_t s = h->stream;
-  const int64_t n = h->n;
-  const int64_t vb = 8 * n * nrhs;  // one vector block
-  const int64_t fac = 8 * h->st.far_values;
-  const unsigned g = (unsigned)((n + 255) / 256);
-  {
-    PhaseScope ps(h, 0, 1, 2 * vb + 8 * n);
-    k_gather_x<<<g, 256, 0, s>>>(x, h->d_perm, n, nrhs, h->d_xt);
-  }
-  {
-    const unsigned nleaf = (unsigned)(1u << (2 * h->kappa));
-    PhaseScope ps(h, 1, 1, 24 * n + 2 * vb);
-    k_near_f64<<<nleaf, 64, 0, s>>>(h->d_x, h->d_y, h->d_perm, h->d_leaf_off, h->kappa, h->kp,
-                                     h->d_xt, n, nrhs, h->d_yl);
-  }
-  const PlanView P = plan_view(h, nrhs);
-  if (h->nproj) {
-    {
-      const int64_t thr = h->nproj * 32;
-      PhaseScope ps(h, 2, 1, fac + 8 * h->proj_partials * nrhs);
-      k_proj_f64<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(P, h->d_proj, h->nproj, h->d_xt,
-                                                                h->d_part);
-    }
-    {
-      PhaseScope ps(h, 3, 1, 8 * (h->proj_partials + h->t_total) * nrhs);
-      k_tsum<<<(unsigned)((h->nt_sides + 255) / 256), 256, 0, s>>>(P, h->d_proj, h->d_tred,
-                                                                   h->nt_sides, h->d_part, h->d_t);
-    }
-  }
-  if (h->nexp) {
-    const int64_t thr = h->nexp * 32;
-    PhaseScope ps(h, 4, 1, fac + 8 * h->t_total * nrhs + vb * h->kappa);
-    k_exp_f64<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(P, h->d_exp, h->nexp, h->d_t,
-                                                             h->d_yl);
-  }
-  {
-    PhaseScope ps(h, 5, 1, vb * (h->kappa + 2) + 8 * n);
-    k_combine<<<g, 256, 0, s>>>(h->d_yl, h->kappa + 1, h->d_perm, n, nrhs, y);
-  }
-  H2D_CK(cudaGetLastError());
-  return HODLR2D_OK;
-}
-
 }  // namespace h2d
 
 namespace h2d {
 
 // The F64 product with caller-supplied scratch (no allocation): xt n x nrhs,
 // yl (kappa + 1) x n x nrhs, part proj_partials x nrhs, t t_total x nrhs.
-// Same kernels and order as matvec_f64_device.
+// First-generation kernels: projection by row chunks, fixed-order chunk sums,
+// expansion, all in FP64.
 int matvec_f64_scratch(hodlr2d* h, const double* x, double* y, int nrhs, double* xt, double* yl,
                        double* part, double* t) {
   cudaStream_t s = h->stream;

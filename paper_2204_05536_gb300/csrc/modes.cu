@@ -1,13 +1,21 @@
-// Reduced-storage factor copies and their products (hodlr2d_mode other than
-// F64).  Filled in by the float-float and mixed-precision paths.
+// Factor copies per hodlr2d_mode and dispatch of the product by mode.
 #include "internal.h"
 
 namespace h2d {
 
+int prepare_df32(hodlr2d* h);
+void free_v2(hodlr2d* h);
+int product_device(hodlr2d* h, const double* x, double* y, int nrhs, int mode);
+
 int prepare_mode(hodlr2d* h, int mode) {
-  if (mode == HODLR2D_MODE_F64) return HODLR2D_OK;
-  (void)h;
-  return HODLR2D_ERR_STATE;
+  int rc = HODLR2D_OK;
+  switch (mode) {
+    case HODLR2D_MODE_F64: break;
+    case HODLR2D_MODE_DF32: rc = prepare_df32(h); break;
+    default: return HODLR2D_ERR_STATE;
+  }
+  if (rc == HODLR2D_OK) h->prepared[mode] = true;
+  return rc;
 }
 
 void free_modes(hodlr2d* h) {
@@ -16,11 +24,11 @@ void free_modes(hodlr2d* h) {
       cudaFree(h->lev[l].d_fac_mode[m]);
       h->lev[l].d_fac_mode[m] = nullptr;
     }
+  free_v2(h);
 }
 
 int matvec_mode_device(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
-  (void)h; (void)x; (void)y; (void)nrhs; (void)mode;
-  return HODLR2D_ERR_STATE;
+  return product_device(h, x, y, nrhs, mode);
 }
 
 }  // namespace h2d

@@ -386,7 +386,7 @@ int lists_build(hodlr2d* h) {
                                       L.d_ent);
     H2D_CK(cudaGetLastError());
     H2D_CK(cudaStreamSynchronize(s));
-    cudaFree(d_poff);
+    L.d_prow = d_poff;  // kept: first stored pair of each row box
     cudaFree(d_nlist);
   }
   return HODLR2D_OK;

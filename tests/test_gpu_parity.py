@@ -250,3 +250,60 @@ def test_full_size_sampled_rows(h2d, oracle):
     assert rel(y[rows], yd) <= 50 * eps
     scale = oracle.direct_rows(pts, ko, np.abs(x), rows)  # MQ > 0: sum |A_ij||x_j|
     assert np.max(np.abs(y[rows] - yd) / scale) <= eps
+
+
+@pytest.mark.parametrize("name,n,kind,a,leaf,eps", CASES)
+def test_p1_df32_same_factors(h2d, oracle, name, n, kind, a, leaf, eps):
+    """The float-float product on the oracle's factors equals the oracle's
+    Alg. 2 product to <= 1e-12 (binary64-level accuracy)."""
+    pts = inputs.uniform(n, seed=0)
+    o = oracle.Oracle(pts, oracle.kernel(kind, a), leaf, eps)
+    g = h2d.HODLR2D(pts, h2d.kernel(kind, a), leaf, eps, compress=False)
+    g.import_factors(*o.export_factors())
+    g.prepare("df32")
+    x = inputs.rhs(n, 2, seed=1)
+    y_o = o.matvec(x)
+    y_g = g.matvec(torch.from_numpy(np.ascontiguousarray(x)).cuda(), mode="df32").cpu().numpy()
+    assert rel(y_g, y_o) <= 1e-12
+
+
+def test_df32_f64_agree_and_deterministic(h2d):
+    n = 20000
+    pts = inputs.uniform(n, seed=5)
+    g = h2d.HODLR2D(pts, h2d.kernel("imq", 1.0 / np.sqrt(n)), 32, 1e-10)
+    g.prepare("df32")
+    x = torch.from_numpy(inputs.rhs(n, 3, seed=2)).cuda()
+    a = g.matvec(x, mode="df32")
+    b = g.matvec(x, mode="df32")
+    assert torch.equal(a, b)
+    c = g.matvec(x, mode="f64")
+    assert rel(a.cpu().numpy(), c.cpu().numpy()) <= 1e-12
+
+
+def test_df32_full_size_sampled_rows(h2d, oracle):
+    n, eps = 1 << 20, 1e-8
+    pts = inputs.uniform(n, seed=0)
+    a = 2.0 ** -10
+    g = h2d.HODLR2D(pts, h2d.kernel("mq", a), 64, eps, root=(-1.0, -1.0, 2.0))
+    g.prepare("df32")
+    x = torch.from_numpy(inputs.rhs(n, seed=1)).cuda()
+    y64 = g.matvec(x, mode="f64").cpu().numpy()
+    y = g.matvec(x, mode="df32").cpu().numpy()
+    assert rel(y, y64) <= 1e-12
+    rows = np.random.default_rng(7).choice(n, 256, replace=False)
+    yd = oracle.direct_rows(pts, oracle.kernel("mq", a), x.cpu().numpy(), rows)
+    assert rel(y[rows], yd) <= 50 * eps
+
+
+def test_gmres_df32_refinement(h2d, oracle):
+    """Iterative refinement: F64 residuals, float-float inner products."""
+    n = 3000
+    pts = inputs.uniform(n, seed=2)
+    lam = inputs.rhs(n, seed=9)
+    ko = oracle.kernel("phi2", 0.001, diag=float(n))
+    f = oracle.direct_matvec(pts, ko, lam)
+    g = h2d.HODLR2D(pts, h2d.kernel("phi2", 0.001, diag=float(n)), 50, 1e-12)
+    g.prepare("df32")
+    x, it, rr, code = g.gmres(torch.from_numpy(f).cuda(), tol=1e-10, inner_mode="df32")
+    assert code == 0 and rr <= 1e-10
+    assert rel(x.cpu().numpy(), lam) <= 1e-8
