@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="f64", choices=["f64", "df32"])
+    p.add_argument("--modes", default="df32,f64",
+                   help="product modes to time; the first is the headline")
     p.add_argument("--n", type=int, default=N_FULL, help="points (smaller for quick checks)")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     return p.parse_args()
@@ -200,34 +201,43 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     t_build = (time.perf_counter() - t0) * 1e3
     st = g.stats()
-    mode = args.mode
-    if mode != "f64":
-        g.prepare(mode)
+    modes = args.modes.split(",")
     stream = torch.cuda.current_stream()
     g.set_stream(stream)
     x = torch.from_numpy(x_h).cuda()
     y = torch.empty_like(x)
-    for _ in range(args.warmup):
-        g.matvec(x, mode=mode, out=y)
-    torch.cuda.synchronize()
-    barrier(ws)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    g.profile(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        g.matvec(x, mode=mode, out=y)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(ws)
-    prof = g.get_profile()
-    g.profile(False)
-    clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    ms_step = max_over_ranks(ms_total / args.steps, ws)
+    per_mode = {}
+    for mode in modes:
+        if mode != "f64":
+            g.prepare(mode)
+        for _ in range(args.warmup):
+            g.matvec(x, mode=mode, out=y)
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        g.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.matvec(x, mode=mode, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        prof = g.get_profile()
+        g.profile(False)
+        clk = clocks.stop()
+        ms_total = e0.elapsed_time(e1)
+        per_mode[mode] = {"ms": max_over_ranks(ms_total / args.steps, ws), "prof": prof,
+                          "clocks": clk, "y_rows": None}
+        per_mode[mode]["y"] = y.clone()
+    mode = modes[0]
+    ms_step = per_mode[mode]["ms"]
+    prof = per_mode[mode]["prof"]
+    clk = per_mode[mode]["clocks"]
+    y = per_mode[mode]["y"]
 
     # end to end through the public API with pinned host buffers
     xp = torch.from_numpy(x_h).pin_memory()
@@ -265,7 +275,7 @@ def run_ours(args, ws, rank, local):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if mode == "f64" else "f64-storage df32-arithmetic",
+        "dtype": mode,
         "data": "synthetic",
         "config": {"workload": WORKLOAD if n == N_FULL else WORKLOAD.replace("2^20", str(n)),
                    "n": n, "leaf": LEAF, "eps": EPS, "kernel": "mq", "a": a, "nrhs": 1,
@@ -287,9 +297,16 @@ def run_ours(args, ws, rank, local):
                   "max_rank": st["max_rank"], "npairs": st["npairs"],
                   "bytes_per_matvec": alg_bytes, "unconverged": st["unconverged"],
                   "compression_ratio": st["compression_ratio"],
-                  "max_rank_per_level": st["max_rank_per_level"]},
+                  "max_rank_per_level": st["max_rank_per_level"],
+                  "values_per_level": st["values_per_level"]},
         "phases_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items()
                                if v["launches"]},
+        "modes": {m: {"ms": round(v["ms"], 4),
+                      "hbm_frac_product": round(st["bytes_per_matvec"][m] / (v["ms"] * 1e-3)
+                                                / 1e9 / peak, 4),
+                      "phases_ms": {k: round(p["ms"] / args.steps, 4)
+                                    for k, p in v["prof"].items() if p["launches"]}}
+                  for m, v in per_mode.items()},
     }
     if rank == 0 and not args.no_cpu:
         rows = np.random.default_rng(7).choice(n, 256, replace=False)

@@ -171,9 +171,10 @@ typedef struct {
 int hodlr2d_get_stats(hodlr2d_t h, hodlr2d_stats* s);
 
 /* ----- tracing: per-phase device time of the product -----
- * Phases of one product: 0 gather x, 1 near field, 2 far-field projection,
- * 3 projection sums, 4 far-field expansion, 5 combine and scatter y,
- * 6 fused far field, 7 other.  While enabled, each phase's launches are
+ * Phases of one product: 0 gather x, 1 near field, 2 far-field projection
+ * (coarse levels), 3 projection sums, 4 far-field expansion (coarse levels),
+ * 5 combine and scatter y, 6 single-read far field, one block per pair
+ * (mid levels), 7 single-read far field, one warp per box (finest levels).  While enabled, each phase's launches are
  * bracketed by CUDA events on the handle's stream.  hodlr2d_profile(h, 1)
  * resets and starts recording, (h, 0) stops.  hodlr2d_get_profile
  * synchronises the stream and returns, per phase, the summed milliseconds,

@@ -11,7 +11,7 @@ from . import build as _build
 
 MAX_LEVELS = 15
 NPHASE = 8
-PHASES = ["gather", "near", "proj", "tsum", "exp", "combine", "far_fused", "other"]
+PHASES = ["gather", "near", "proj", "tsum", "exp", "combine", "pair_mode", "box_mode"]
 
 OK = 0
 ERR_ARG = -1

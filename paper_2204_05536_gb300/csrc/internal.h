@@ -63,16 +63,19 @@ struct ExpTask {
 // Plan and scratch of the second-generation product (product.cu).
 struct V2Plan {
   bool ready = false;
-  int lfuse = 1;  // first level handled by the fused kernel
+  int lfuse = 1;   // first level handled by the fused kernel
   ProjTask* d_proj = nullptr;
   ExpTask* d_exp = nullptr;
   int64_t* d_red = nullptr;
-  int64_t nproj = 0, nexp = 0, proj_partials = 0, nsides = 0;
-  int kmax = 1;
-  int64_t rmax_big = 1, rmax_small = 1;
-  int2* d_big = nullptr;
-  int2* d_small = nullptr;
-  int64_t nbig = 0, nsmall = 0;
+  int64_t nproj = 0, nexp = 0, proj_partials = 0, nsides = 0, ntsum = 0;
+  int32_t* d_wtask = nullptr;  // task of each projection warp
+  int64_t* d_sideq = nullptr;  // (pair side, column) of each chunk-sum warp
+  int lmode[HODLR2D_MAX_LEVELS] = {};  // per level: two-pass, pair or box mode
+  int2* d_pw_big = nullptr;    // pair-mode work (level, pair), large boxes
+  int2* d_pw_small = nullptr;  // pair-mode work, boxes <= 256 points
+  int2* d_bw = nullptr;        // box-mode work (level, box)
+  int64_t npw_big = 0, npw_small = 0, nbw = 0;
+  bool zero_partials = false;
   int64_t pstride = 1;
   int32_t* d_leaf_of = nullptr;
   int scratch_nrhs = 0;

@@ -22,9 +22,9 @@
 
 namespace h2d {
 
-constexpr int kFuseRows = 4096;   // largest box handled by the fused kernel
-constexpr int kSmallRows = 256;   // boxes up to this size use small blocks
-constexpr int kChunk2 = 2048;     // row chunk of the two-pass levels
+constexpr int kFuseRows = 2048;   // largest box handled by the single-read kernels
+constexpr int kSmallPair = 256;   // boxes up to this size: 64-thread pair blocks
+constexpr int kChunk2 = 256;      // row chunk of the two-pass levels (8 rows per lane)
 constexpr int kNearRhs = 4;       // right-hand sides per near-field pass
 
 struct LevelV2 {
@@ -40,8 +40,11 @@ struct LevelV2 {
   const void* fac;
 };
 
+enum { LMODE_TWO = 0, LMODE_PAIR = 1, LMODE_BOX = 2 };
+
 struct ArgsV2 {
   LevelV2 lev[HODLR2D_MAX_LEVELS];
+  int lmode[HODLR2D_MAX_LEVELS];
   const int32_t* leaf_off;
   int kappa;
   int lfuse;
@@ -58,6 +61,13 @@ __device__ __forceinline__ int32_t bsize(const int32_t* leaf_off, int kappa, int
   return leaf_off[(int64_t)(b + 1) << sh] - leaf_off[(int64_t)b << sh];
 }
 
+__device__ __forceinline__ double shfl_val(double v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ float2 shfl_val(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
 // ---------------------------------------------------------------------------
 // gather x into tree order
 // ---------------------------------------------------------------------------
@@ -71,28 +81,33 @@ __global__ void k_gather2(const double* __restrict__ x, const int64_t* __restric
 }
 
 // ---------------------------------------------------------------------------
-// near field, float-float: one block per leaf, sources staged in shared memory
+// near field, float-float: one warp per leaf.  With G = 32 / (targets per
+// round) lanes per target (G = 4 for <= 8 points, 2 for <= 16, else 1), lane
+// group h takes the sources s = h (mod G) of the concatenated source list
+// (the leaf itself, then its edge sharers in ascending Morton order); the G
+// partial sums meet in a fixed shuffle tree.
 // ---------------------------------------------------------------------------
-constexpr int kNearThreads = 64;
-constexpr int kNearStage = 256;
+constexpr int kNearWarps = 4;
 
-__global__ void __launch_bounds__(kNearThreads)
+__global__ void __launch_bounds__(32 * kNearWarps)
     k_near_df32(const float2* __restrict__ xf, const float2* __restrict__ yf,
                 const int64_t* __restrict__ perm, const int32_t* __restrict__ leaf_off, int kappa,
-                KernelFF kp, const float2* __restrict__ xt, int64_t n, int nrhs,
+                int64_t nleaf, KernelFF kp, const float2* __restrict__ xt, int64_t n, int nrhs,
                 float2* __restrict__ yout) {
-  __shared__ float2 sxy[kNearStage][2];
-  __shared__ int64_t sg[kNearStage];
-  __shared__ float2 sv[kNearRhs][kNearStage];
-  const uint32_t b = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t bl = (int64_t)blockIdx.x * kNearWarps + (threadIdx.x >> 5);
+  if (bl >= nleaf) return;
+  const uint32_t b = (uint32_t)bl;
   const int32_t s0 = leaf_off[b], m = leaf_off[b + 1] - s0;
   if (m == 0) return;
   int cx, cy;
   morton_decode(b, cx, cy);
   const int side = 1 << kappa;
-  uint32_t src[5];
+  int32_t sb[5], se[5];
   int ns = 0;
-  src[ns++] = b;
+  sb[0] = s0;
+  se[0] = s0 + m;
+  ns = 1;
   uint32_t nb[4];
   int nn = 0;
   const int dx[4] = {-1, 1, 0, 0}, dy[4] = {0, 0, -1, 1};
@@ -107,10 +122,16 @@ __global__ void __launch_bounds__(kNearThreads)
     while (j >= 0 && nb[j] > v) { nb[j + 1] = nb[j]; --j; }
     nb[j + 1] = v;
   }
-  for (int i = 0; i < nn; ++i) src[ns++] = nb[i];
-  // targets in rounds of kNearThreads, right-hand sides in blocks of kNearRhs
-  for (int t0 = 0; t0 < m; t0 += kNearThreads) {
-    const int t = t0 + threadIdx.x;
+  for (int i = 0; i < nn; ++i) {
+    sb[ns] = leaf_off[nb[i]];
+    se[ns] = leaf_off[nb[i] + 1];
+    ++ns;
+  }
+  const int G = m <= 8 ? 4 : (m <= 16 ? 2 : 1);
+  const int tpr = 32 / G;
+  const int h = lane / tpr, tl = lane - h * tpr;
+  for (int t0 = 0; t0 < m; t0 += tpr) {
+    const int t = t0 + tl;
     const bool act = t < m;
     const int64_t it = s0 + (act ? t : 0);
     const float2 xi = xf[it], yi = yf[it];
@@ -120,208 +141,357 @@ __global__ void __launch_bounds__(kNearThreads)
       float2 acc[kNearRhs];
 #pragma unroll
       for (int r = 0; r < kNearRhs; ++r) acc[r] = DF32A::zero();
+      int sidx = 0;  // running index over the concatenated sources
       for (int q = 0; q < ns; ++q) {
-        const int32_t a = leaf_off[src[q]], e = leaf_off[src[q] + 1];
-        for (int32_t j0 = a; j0 < e; j0 += kNearStage) {
-          const int cnt = min(kNearStage, e - j0);
-          __syncthreads();
-          for (int u = threadIdx.x; u < cnt; u += kNearThreads) {
-            sxy[u][0] = xf[j0 + u];
-            sxy[u][1] = yf[j0 + u];
-            sg[u] = perm[j0 + u];
-            for (int r = 0; r < nc; ++r) sv[r][u] = xt[(int64_t)(c0 + r) * n + j0 + u];
-          }
-          __syncthreads();
-          if (act)
-            for (int u = 0; u < cnt; ++u) {
-              const float2 kij = entry_ff(kp, xi, yi, gi, sxy[u][0], sxy[u][1], sg[u]);
+        const int32_t len = se[q] - sb[q];
+        // first source of this box whose running index is = h (mod G)
+        int j = (h - sidx) % G;
+        if (j < 0) j += G;
+        for (; j < len; j += G) {
+          const int64_t js = sb[q] + j;
+          const float2 kij = entry_ff(kp, xi, yi, gi, xf[js], yf[js], perm[js]);
 #pragma unroll
-              for (int r = 0; r < kNearRhs; ++r)
-                if (r < nc) DF32A::fma(acc[r], kij, sv[r][u]);
-            }
+          for (int r = 0; r < kNearRhs; ++r)
+            if (r < nc) DF32A::fma(acc[r], kij, xt[(int64_t)(c0 + r) * n + js]);
         }
+        sidx += len;
       }
-      if (act)
-        for (int r = 0; r < nc; ++r) yout[(int64_t)(c0 + r) * n + it] = DF32A::fin(acc[r]);
+#pragma unroll
+      for (int r = 0; r < kNearRhs; ++r) {
+        float2 v = DF32A::fin(acc[r]);
+        for (int o = tpr; o < 32; o <<= 1) v = DF32A::add(v, shfl_val(v, o));
+        acc[r] = v;
+      }
+      if (act && h == 0)
+        for (int r = 0; r < nc; ++r) yout[(int64_t)(c0 + r) * n + it] = acc[r];
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// fused far field (levels >= lfuse): one block per row box
+// pair mode (mid levels): one block per stored pair (X,Y).  Phase 1: one warp
+// per column computes t1 = V^T x_Y and t2 = U^T x_X (rows over lanes, shuffle
+// sum).  Phase 2: one thread per row writes U t1 (rows of X) and V t2 (rows of
+// Y) as partial results; its reads of U and V hit L2, which still holds the
+// pair from phase 1.
 // ---------------------------------------------------------------------------
+constexpr int kPairKmax = 256;
+
 template <class A, int T>
 __global__ void __launch_bounds__(T)
-    k_fused(ArgsV2 P, const int2* __restrict__ tasks, int rmax, int kmax, int svals,
-            const typename A::val* __restrict__ xt, typename A::val* __restrict__ yl,
-            typename A::val* __restrict__ ppart) {
+    k_pair(ArgsV2 P, const int2* __restrict__ work, const typename A::val* __restrict__ xt,
+           typename A::val* __restrict__ ppart) {
   using V = typename A::val;
   using Acc = typename A::acc;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  V* sx = reinterpret_cast<V*>(smraw);
-  V* sy = sx + rmax;
-  Acc* yacc = reinterpret_cast<Acc*>(sy + rmax);
-  V* t1 = reinterpret_cast<V*>(yacc + rmax);
-  V* t2 = t1 + kmax;
-  V* stage = t2 + kmax;
+  __shared__ V ts[2 * kPairKmax];
   constexpr int NW = T / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int2 task = tasks[blockIdx.x];
-  const int l = task.x;
-  const uint32_t X = (uint32_t)task.y;
+  const int2 wk = work[blockIdx.x];
+  const int l = wk.x;
+  const int64_t p = wk.y;
   const LevelV2& L = P.lev[l];
-  const int32_t xs = bstart(P.leaf_off, P.kappa, l, X);
-  const int32_t m = bsize(P.leaf_off, P.kappa, l, X);
+  const uint32_t bx = (uint32_t)L.px[p], by = (uint32_t)L.py[p];
+  const int32_t xs = bstart(P.leaf_off, P.kappa, l, bx), m = bsize(P.leaf_off, P.kappa, l, bx);
+  const int32_t ys = bstart(P.leaf_off, P.kappa, l, by), n = bsize(P.leaf_off, P.kappa, l, by);
+  const int64_t lm = ldpad(m), ln = ldpad(n);
+  const int k = L.rank[p];
+  const V* Ug = reinterpret_cast<const V*>(L.fac) + L.foff[p];
+  const V* Vg = Ug + lm * k;
+  for (int c = 0; c < P.nrhs; ++c) {
+    const V* xc = xt + (int64_t)c * P.n;
+    for (int job = warp; job < 2 * k; job += NW) {
+      const bool isV = job < k;
+      const int q = isV ? job : job - k;
+      const int rows = isV ? n : m;
+      const V* col = (isV ? Vg + q * ln : Ug + q * lm);
+      const V* xv = xc + (isV ? ys : xs);
+      Acc a = A::zero();
+      int r = lane;
+      for (; r + 96 < rows; r += 128) {
+        const V v0 = col[r], v1 = col[r + 32], v2 = col[r + 64], v3 = col[r + 96];
+        const V x0 = xv[r], x1 = xv[r + 32], x2 = xv[r + 64], x3 = xv[r + 96];
+        A::fma(a, v0, x0);
+        A::fma(a, v1, x1);
+        A::fma(a, v2, x2);
+        A::fma(a, v3, x3);
+      }
+      for (; r < rows; r += 32) A::fma(a, col[r], xv[r]);
+      const V sum = A::warp_sum(a);
+      if (lane == 0) ts[job] = sum;
+    }
+    __syncthreads();
+    V* outx = ppart + (int64_t)c * P.pstride + L.ppoff[2 * p];
+    V* outy = ppart + (int64_t)c * P.pstride + L.ppoff[2 * p + 1];
+    for (int r = tid; r < m + n; r += T) {
+      const bool own = r < m;
+      const int i = own ? r : r - m;
+      const V* M = own ? Ug + i : Vg + i;
+      const int64_t ld = own ? lm : ln;
+      const V* tv = own ? ts : ts + k;  // U pairs with t1, V with t2
+      Acc a = A::zero();
+      int q = 0;
+      for (; q + 8 <= k; q += 8) {
+        V mv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mv[u] = M[(q + u) * ld];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) A::fma(a, mv[u], tv[q + u]);
+      }
+      for (; q < k; ++q) A::fma(a, M[q * ld], tv[q]);
+      (own ? outx : outy)[i] = A::fin(a);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// box mode (finest levels, boxes of <= kBoxRows points): one warp per row box
+// X, its stored pairs one after another.  A pair that fits kBoxStage values is
+// copied to the warp's shared-memory slice (coalesced), then
+//   lane q < 2k: one column's dot product (V columns -> t1, U columns -> t2),
+//                rows visited from q onwards (mod rows) so that the lanes hit
+//                distinct banks;
+//   lanes over rows: y_X += U t1 kept in registers, V t2 written as the
+//                partial of Y.
+// A larger pair is read from global memory with one warp per column instead.
+// ---------------------------------------------------------------------------
+constexpr int kBoxRows = 64;
+constexpr int kBoxStage = 1024;
+constexpr int kBoxK = 64;
+constexpr int kBoxWarps = 4;
+
+template <class A>
+__global__ void __launch_bounds__(32 * kBoxWarps)
+    k_box(ArgsV2 P, const int2* __restrict__ work, int64_t nwork,
+          const typename A::val* __restrict__ xt, typename A::val* __restrict__ yl,
+          typename A::val* __restrict__ ppart) {
+  using V = typename A::val;
+  using Acc = typename A::acc;
+  __shared__ V st_all[kBoxWarps][kBoxStage];
+  __shared__ V xx_all[kBoxWarps][kBoxRows];
+  __shared__ V xy_all[kBoxWarps][kBoxRows];
+  __shared__ V ts_all[kBoxWarps][2 * kBoxK];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t wid = (int64_t)blockIdx.x * kBoxWarps + warp;
+  if (wid >= nwork) return;
+  V* st = st_all[warp];
+  V* xx = xx_all[warp];
+  V* xy = xy_all[warp];
+  V* ts = ts_all[warp];
+  const int2 wk = work[wid];
+  const int l = wk.x;
+  const uint32_t X = (uint32_t)wk.y;
+  const LevelV2& L = P.lev[l];
+  const int32_t xs = bstart(P.leaf_off, P.kappa, l, X), m = bsize(P.leaf_off, P.kappa, l, X);
   const int64_t lm = ldpad(m);
   const int64_t p0 = L.prow[X], p1 = L.prow[X + 1];
   const V* fac = reinterpret_cast<const V*>(L.fac);
   for (int c = 0; c < P.nrhs; ++c) {
     const V* xc = xt + (int64_t)c * P.n;
-    for (int i = tid; i < m; i += T) {
-      sx[i] = xc[xs + i];
-      yacc[i] = A::zero();
-    }
+    for (int i = lane; i < m; i += 32) xx[i] = xc[xs + i];
+    Acc y0 = A::zero(), y1 = A::zero();  // rows lane and lane + 32
     for (int64_t p = p0; p < p1; ++p) {
       const int k = L.rank[p];
       const uint32_t Y = (uint32_t)L.py[p];
-      const int32_t ys = bstart(P.leaf_off, P.kappa, l, Y);
-      const int32_t n = bsize(P.leaf_off, P.kappa, l, Y);
+      const int32_t ys = bstart(P.leaf_off, P.kappa, l, Y), n = bsize(P.leaf_off, P.kappa, l, Y);
       const int64_t ln = ldpad(n);
       const V* Ug = fac + L.foff[p];
       const V* Vg = Ug + lm * k;
-      const bool staged = (lm + ln) * k <= (int64_t)svals;
-      for (int j = tid; j < n; j += T) sy[j] = xc[ys + j];
-      __syncthreads();
-      for (int job = warp; job < 2 * k; job += NW) {
-        const bool isV = job < k;
-        const int q = isV ? job : job - k;
-        const int rows = isV ? n : m;
-        const int64_t ld = isV ? ln : lm;
-        const V* col = (isV ? Vg : Ug) + q * ld;
-        const V* xv = isV ? sy : sx;
-        Acc a = A::zero();
-        if (staged) {
-          V* st = stage + (isV ? lm * k : 0) + q * ld;
-          for (int r = lane; r < rows; r += 32) {
-            const V v = col[r];
-            st[r] = v;
-            A::fma(a, v, xv[r]);
+      V* outy = ppart + (int64_t)c * P.pstride + L.ppoff[2 * p + 1];
+      for (int j = lane; j < n; j += 32) xy[j] = xc[ys + j];
+      const int64_t tot = (lm + ln) * k;
+      __syncwarp();
+      if (tot <= kBoxStage && k <= kBoxK) {
+        for (int64_t e = lane; e < tot; e += 32) st[e] = Ug[e];
+        __syncwarp();
+        const V* Us = st;
+        const V* Vs = st + lm * k;
+        for (int job = lane; job < 2 * k; job += 32) {
+          const bool isV = job < k;
+          const int q = isV ? job : job - k;
+          const int rows = isV ? n : m;
+          const V* col = isV ? Vs + q * ln : Us + q * lm;
+          const V* xv = isV ? xy : xx;
+          Acc a = A::zero();
+          int r = q;  // q < k <= rows
+          for (int u = 0; u < rows; ++u) {
+            A::fma(a, col[r], xv[r]);
+            if (++r == rows) r = 0;
           }
-        } else {
-          for (int r = lane; r < rows; r += 32) A::fma(a, col[r], xv[r]);
+          ts[job] = A::fin(a);
         }
-        const V s = A::warp_sum(a);
-        if (lane == 0) (isV ? t1 : t2)[q] = s;
+        __syncwarp();
+        for (int r = lane; r < m + n; r += 32) {
+          const bool own = r < m;
+          const int i = own ? r : r - m;
+          const V* M = own ? Us + i : Vs + i;
+          const int64_t ld = own ? lm : ln;
+          const V* tv = own ? ts : ts + k;
+          Acc a = own ? (i < 32 ? y0 : y1) : A::zero();
+          for (int q = 0; q < k; ++q) A::fma(a, M[q * ld], tv[q]);
+          if (own) {
+            if (i < 32) y0 = a;
+            else y1 = a;
+          } else {
+            outy[i] = A::fin(a);
+          }
+        }
+      } else {
+        // the pair does not fit the slice: warp-per-column from global memory
+        for (int job = 0; job < 2 * k; ++job) {
+          const bool isV = job < k;
+          const int q = isV ? job : job - k;
+          const int rows = isV ? n : m;
+          const V* col = isV ? Vg + q * ln : Ug + q * lm;
+          const V* xv = isV ? xy : xx;
+          Acc a = A::zero();
+          for (int r = lane; r < rows; r += 32) A::fma(a, col[r], xv[r]);
+          const V sum = A::warp_sum(a);
+          if (lane == 0) ts[job] = sum;
+        }
+        __syncwarp();
+        for (int r = lane; r < m + n; r += 32) {
+          const bool own = r < m;
+          const int i = own ? r : r - m;
+          const V* M = own ? Ug + i : Vg + i;
+          const int64_t ld = own ? lm : ln;
+          const V* tv = own ? ts : ts + k;
+          Acc a = own ? (i < 32 ? y0 : y1) : A::zero();
+          for (int q = 0; q < k; ++q) A::fma(a, M[q * ld], tv[q]);
+          if (own) {
+            if (i < 32) y0 = a;
+            else y1 = a;
+          } else {
+            outy[i] = A::fin(a);
+          }
+        }
       }
-      __syncthreads();
-      const V* Us = staged ? stage : Ug;
-      const V* Vs = staged ? stage + lm * k : Vg;
-      for (int i = tid; i < m; i += T) {
-        Acc a = yacc[i];
-        for (int q = 0; q < k; ++q) A::fma(a, Us[q * lm + i], t1[q]);
-        yacc[i] = a;
-      }
-      V* out = ppart + (int64_t)c * P.pstride + L.ppoff[p];
-      for (int j = tid; j < n; j += T) {
-        Acc a = A::zero();
-        for (int q = 0; q < k; ++q) A::fma(a, Vs[q * ln + j], t2[q]);
-        out[j] = A::fin(a);
-      }
-      __syncthreads();
+      __syncwarp();
     }
     V* own = yl + ((int64_t)l * P.nrhs + c) * P.n + xs;
-    for (int i = tid; i < m; i += T) own[i] = A::fin(yacc[i]);
-    __syncthreads();
+    if (lane < m) own[lane] = A::fin(y0);
+    if (lane + 32 < m) own[lane + 32] = A::fin(y1);
+    __syncwarp();
   }
 }
 
 // ---------------------------------------------------------------------------
 // two-pass far field (levels < lfuse)
 // ---------------------------------------------------------------------------
+// One warp per (task, column): lanes read rows r0 + lane + 32 u (coalesced),
+// keep them in registers across the right-hand sides, and reduce by shuffles.
+// wtask[w] is the task of warp w; its column is w - out[task].
 template <class A>
-__global__ void k_proj2(ArgsV2 P, const ProjTask* __restrict__ tasks, int64_t ntasks,
-                        const typename A::val* __restrict__ xt, typename A::val* __restrict__ part) {
+__global__ void __launch_bounds__(256)
+    k_proj2(ArgsV2 P, const ProjTask* __restrict__ tasks, const int32_t* __restrict__ wtask,
+            int64_t nwarps, const typename A::val* __restrict__ xt,
+            typename A::val* __restrict__ part) {
   using V = typename A::val;
   using Acc = typename A::acc;
+  constexpr int R = kChunk2 / 32;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= ntasks) return;
-  const ProjTask T = tasks[w];
+  if (w >= nwarps) return;
+  const int64_t lo = wtask[w];
+  const ProjTask T = tasks[lo];
+  const int q = (int)(w - T.out);
   const LevelV2& L = P.lev[T.level];
   const uint32_t bx = (uint32_t)L.px[T.pair], by = (uint32_t)L.py[T.pair];
   const int32_t m = bsize(P.leaf_off, P.kappa, T.level, bx);
   const int32_t nrow = T.side == 0 ? bsize(P.leaf_off, P.kappa, T.level, by) : m;
   const int32_t base = bstart(P.leaf_off, P.kappa, T.level, T.side == 0 ? by : bx);
   const int k = L.rank[T.pair];
-  const V* M = reinterpret_cast<const V*>(L.fac) + L.foff[T.pair] + (T.side == 0 ? ldpad(m) * k : 0);
-  const int64_t ld = ldpad(nrow);
+  const V* col = reinterpret_cast<const V*>(L.fac) + L.foff[T.pair] +
+                 (T.side == 0 ? ldpad(m) * k : 0) + (int64_t)q * ldpad(nrow);
+  V v[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int r = T.r0 + lane + 32 * u;
+    v[u] = r < T.r0 + T.nr ? col[r] : A::vzero();
+  }
   for (int c = 0; c < P.nrhs; ++c) {
     const V* xv = xt + c * P.n + base;
-    for (int q = 0; q < k; ++q) {
-      const V* col = M + q * ld;
-      Acc a = A::zero();
-      for (int i = T.r0 + lane; i < T.r0 + T.nr; i += 32) A::fma(a, col[i], xv[i]);
-      const V s = A::warp_sum(a);
-      if (lane == 0) part[T.out * P.nrhs + (int64_t)c * k + q] = s;
+    Acc a = A::zero();
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int r = T.r0 + lane + 32 * u;
+      if (r < T.r0 + T.nr) A::fma(a, v[u], xv[r]);
     }
+    const V sum = A::warp_sum(a);
+    if (lane == 0) part[T.out * P.nrhs + (int64_t)c * k + q] = sum;
   }
 }
 
+// t[pair, side, q] = sum of the chunk partials in chunk order: one warp per
+// (pair, side, column); lane j sums chunks j, j + 32, ..., then a fixed
+// shuffle tree adds the 32 lane sums.  red[2 s] = {first task, count}.
 template <class A>
-__global__ void k_tsum2(ArgsV2 P, const ProjTask* __restrict__ tasks,
-                        const int64_t* __restrict__ red, int64_t nsides,
-                        const typename A::val* __restrict__ part, typename A::val* __restrict__ t) {
+__global__ void __launch_bounds__(256)
+    k_tsum2(ArgsV2 P, const ProjTask* __restrict__ tasks, const int64_t* __restrict__ red,
+            const int64_t* __restrict__ sideq, int64_t nwork,
+            const typename A::val* __restrict__ part, typename A::val* __restrict__ t) {
   using V = typename A::val;
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= nsides) return;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nwork) return;
+  const int64_t s = sideq[2 * w];
+  const int q = (int)sideq[2 * w + 1];
   const int64_t first = red[2 * s], count = red[2 * s + 1];
-  if (count == 0) return;
   const ProjTask T0 = tasks[first];
   const LevelV2& L = P.lev[T0.level];
   const int k = L.rank[T0.pair];
   V* out = t + L.toff[T0.pair] * P.nrhs + (int64_t)T0.side * k * P.nrhs;
-  for (int c = 0; c < P.nrhs; ++c)
-    for (int q = 0; q < k; ++q) {
-      V acc = A::vzero();
-      for (int64_t j = 0; j < count; ++j)
-        acc = A::add(acc, part[tasks[first + j].out * P.nrhs + c * k + q]);
-      out[c * k + q] = acc;
-    }
+  for (int c = 0; c < P.nrhs; ++c) {
+    V acc = A::vzero();
+    for (int64_t j = lane; j < count; j += 32)
+      acc = A::add(acc, part[tasks[first + j].out * P.nrhs + c * k + q]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = A::add(acc, shfl_val(acc, o));
+    if (lane == 0) out[c * k + q] = acc;
+  }
 }
 
+// One thread per (two-pass level, row): the row's box sums U t1 / V t2 over
+// its list in ascending partner order.
 template <class A>
-__global__ void k_exp2(ArgsV2 P, const ExpTask* __restrict__ tasks, int64_t ntasks,
-                       const typename A::val* __restrict__ t, typename A::val* __restrict__ yl) {
+__global__ void __launch_bounds__(256)
+    k_exp2(ArgsV2 P, const int32_t* __restrict__ leaf_of, const typename A::val* __restrict__ t,
+           typename A::val* __restrict__ yl) {
   using V = typename A::val;
   using Acc = typename A::acc;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= ntasks) return;
-  const ExpTask T = tasks[w];
-  const LevelV2& L = P.lev[T.level];
-  const uint32_t X = (uint32_t)T.box;
-  const int32_t base = bstart(P.leaf_off, P.kappa, T.level, X);
-  const int32_t nX = bsize(P.leaf_off, P.kappa, T.level, X);
-  const int64_t ld = ldpad(nX);
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int nl = P.lfuse - 1;
+  if (gid >= P.n * nl) return;
+  const int l = 1 + (int)(gid / P.n);
+  const int64_t i = gid - (int64_t)(l - 1) * P.n;
+  const LevelV2& L = P.lev[l];
+  const uint32_t X = (uint32_t)leaf_of[i] >> (2 * (P.kappa - l));
+  const int64_t loc = i - bstart(P.leaf_off, P.kappa, l, X);
+  const int64_t ld = ldpad(bsize(P.leaf_off, P.kappa, l, X));
   const int32_t e0 = L.ent_off[X], e1 = L.ent_off[X + 1];
   const V* fac = reinterpret_cast<const V*>(L.fac);
   for (int c = 0; c < P.nrhs; ++c) {
-    V* out = yl + ((int64_t)T.level * P.nrhs + c) * P.n + base;
-    for (int i = T.r0 + lane; i < T.r0 + T.nr; i += 32) {
-      Acc a = A::zero();
-      for (int32_t e = e0; e < e1; ++e) {
-        const int32_t code = L.ent[e];
-        const int64_t p = code >> 1;
-        const int side = code & 1;
-        const int k = L.rank[p];
-        int64_t off = L.foff[p];
-        if (side == 1) off += ldpad(bsize(P.leaf_off, P.kappa, T.level, (uint32_t)L.px[p])) * k;
-        const V* M = fac + off;
-        const V* tv = t + L.toff[p] * P.nrhs + (int64_t)side * k * P.nrhs + (int64_t)c * k;
-        for (int q = 0; q < k; ++q) A::fma(a, M[q * ld + i], tv[q]);
+    Acc a = A::zero();
+    for (int32_t e = e0; e < e1; ++e) {
+      const int32_t code = L.ent[e];
+      const int64_t p = code >> 1;
+      const int side = code & 1;
+      const int k = L.rank[p];
+      int64_t off = L.foff[p];
+      if (side == 1) off += ldpad(bsize(P.leaf_off, P.kappa, l, (uint32_t)L.px[p])) * k;
+      const V* M = fac + off + loc;
+      const V* tv = t + L.toff[p] * P.nrhs + (int64_t)side * k * P.nrhs + (int64_t)c * k;
+      int q = 0;
+      for (; q + 8 <= k; q += 8) {  // eight independent loads in flight
+        V mv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mv[u] = M[(q + u) * ld];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) A::fma(a, mv[u], tv[q + u]);
       }
-      out[i] = A::fin(a);
+      for (; q < k; ++q) A::fma(a, M[q * ld], tv[q]);
     }
+    yl[((int64_t)l * P.nrhs + c) * P.n + i] = A::fin(a);
   }
 }
 
@@ -341,16 +511,19 @@ __global__ void k_combine2(ArgsV2 P, const typename A::val* __restrict__ yl,
   const int64_t g = perm[i];
   for (int c = 0; c < P.nrhs; ++c) {
     V acc = yl[(int64_t)c * P.n + i];
+    const V* pc = ppart + (int64_t)c * P.pstride;
     for (int l = 1; l <= P.kappa; ++l) {
-      acc = A::add(acc, yl[((int64_t)l * P.nrhs + c) * P.n + i]);
-      if (l < P.lfuse) continue;
+      const int mode = P.lmode[l];
+      if (mode != LMODE_PAIR) acc = A::add(acc, yl[((int64_t)l * P.nrhs + c) * P.n + i]);
+      if (mode == LMODE_TWO) continue;
       const LevelV2& L = P.lev[l];
       const uint32_t B = leaf >> (2 * (P.kappa - l));
       const int64_t loc = i - bstart(P.leaf_off, P.kappa, l, B);
-      const V* pc = ppart + (int64_t)c * P.pstride;
       for (int32_t e = L.ent_off[B]; e < L.ent_off[B + 1]; ++e) {
         const int32_t code = L.ent[e];
-        if (code & 1) acc = A::add(acc, pc[L.ppoff[code >> 1] + loc]);
+        const int side = code & 1;
+        if (mode == LMODE_BOX && side == 0) continue;  // own sums are in the slab
+        acc = A::add(acc, pc[L.ppoff[2 * (code >> 1) + side] + loc]);
       }
     }
     y[g + (int64_t)c * P.n] = A::to_double(acc);
@@ -386,6 +559,7 @@ static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
     P.lev[l] = LevelV2{L.d_px, L.d_py, L.d_rank, L.d_foff, L.d_prow, L.d_ppoff,
                        L.d_toff, L.d_ent_off, L.d_ent, fac};
   }
+  for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) P.lmode[l] = h->v2.lmode[l];
   P.leaf_off = h->d_leaf_off;
   P.kappa = h->kappa;
   P.lfuse = h->v2.lfuse;
@@ -410,6 +584,8 @@ int plan_v2(hodlr2d* h) {
   V.lfuse = kappa + 1;
   for (int l = 1; l <= kappa; ++l)
     if (maxcount(l) <= kFuseRows) { V.lfuse = l; break; }
+  for (int l = V.lfuse; l <= kappa; ++l)  // the pair kernel holds at most kPairKmax terms
+    if (h->lev[l].max_rank > kPairKmax) V.lfuse = l + 1;
   // two-pass task lists for levels < lfuse
   std::vector<ProjTask> proj;
   std::vector<ExpTask> exps;
@@ -456,6 +632,29 @@ int plan_v2(hodlr2d* h) {
   }
   V.nproj = (int64_t)proj.size();
   V.nexp = (int64_t)exps.size();
+  {
+    std::vector<int32_t> wt(std::max<int64_t>(out, 1));
+    for (int64_t t = 0; t < V.nproj; ++t) {
+      const int k = h->lev[proj[t].level].h_rank[proj[t].pair];
+      for (int q = 0; q < k; ++q) wt[proj[t].out + q] = (int32_t)t;
+    }
+    std::vector<int64_t> sq;
+    for (int64_t sd = 0; sd < (int64_t)red.size() / 2; ++sd) {
+      if (red[2 * sd + 1] == 0) continue;
+      const ProjTask& T0 = proj[red[2 * sd]];
+      const int k = h->lev[T0.level].h_rank[T0.pair];
+      for (int q = 0; q < k; ++q) {
+        sq.push_back(sd);
+        sq.push_back(q);
+      }
+    }
+    V.ntsum = (int64_t)sq.size() / 2;
+    H2D_CK(cudaMalloc(&V.d_wtask, sizeof(int32_t) * wt.size()));
+    H2D_CK(cudaMemcpy(V.d_wtask, wt.data(), sizeof(int32_t) * wt.size(), cudaMemcpyHostToDevice));
+    H2D_CK(cudaMalloc(&V.d_sideq, sizeof(int64_t) * std::max<size_t>(sq.size(), 2)));
+    if (!sq.empty())
+      H2D_CK(cudaMemcpy(V.d_sideq, sq.data(), sizeof(int64_t) * sq.size(), cudaMemcpyHostToDevice));
+  }
   V.proj_partials = out;
   V.nsides = (int64_t)red.size() / 2;
   H2D_CK(cudaMalloc(&V.d_proj, sizeof(ProjTask) * std::max<int64_t>(V.nproj, 1)));
@@ -467,45 +666,62 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMemcpy(V.d_exp, exps.data(), sizeof(ExpTask) * V.nexp, cudaMemcpyHostToDevice));
   if (!red.empty())
     H2D_CK(cudaMemcpy(V.d_red, red.data(), sizeof(int64_t) * red.size(), cudaMemcpyHostToDevice));
-  // fused levels: partial offsets (|Y| per pair, absolute) and block tasks
-  std::vector<int2> big, small;
+  // single-read levels: pair mode (one block per pair, partials for both
+  // sides) or box mode (one warp per row box, partials for the column side)
+  std::vector<int2> pw_big, pw_small, bw;
   int64_t pbase = 0;
-  V.kmax = 1;
-  V.rmax_big = 1;
-  V.rmax_small = 1;
+  for (int l = 1; l <= kappa; ++l) V.lmode[l] = l < V.lfuse ? LMODE_TWO : LMODE_PAIR;
   for (int l = V.lfuse; l <= kappa; ++l) {
     Level& L = h->lev[l];
     const int64_t np = L.npairs;
     const int sh = 2 * (kappa - l);
-    std::vector<int32_t> py(np);
-    if (np) H2D_CK(cudaMemcpy(py.data(), L.d_py, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
-    std::vector<int64_t> pp(np + 1);
-    for (int64_t p = 0; p < np; ++p) {
-      pp[p] = pbase;
-      pbase += h->h_leaf_off[(int64_t)(py[p] + 1) << sh] - h->h_leaf_off[(int64_t)py[p] << sh];
-    }
-    pp[np] = pbase;
-    L.npart = pp[np] - pp[0];
-    H2D_CK(cudaMalloc(&L.d_ppoff, sizeof(int64_t) * (np + 1)));
-    H2D_CK(cudaMemcpy(L.d_ppoff, pp.data(), sizeof(int64_t) * (np + 1), cudaMemcpyHostToDevice));
-    V.kmax = std::max(V.kmax, L.max_rank);
     const int64_t mc = maxcount(l);
-    const bool is_small = mc <= kSmallRows;
-    if (is_small) V.rmax_small = std::max<int64_t>(V.rmax_small, mc);
-    else V.rmax_big = std::max<int64_t>(V.rmax_big, mc);
-    for (int64_t b = 0; b < ((int64_t)1 << (2 * l)); ++b) {
-      if (h->h_leaf_off[(b + 1) << sh] == h->h_leaf_off[b << sh]) continue;
-      (is_small ? small : big).push_back(make_int2(l, (int)b));
+    V.lmode[l] = mc <= kBoxRows ? LMODE_BOX : LMODE_PAIR;
+    std::vector<int32_t> px(np), py(np);
+    if (np) {
+      H2D_CK(cudaMemcpy(px.data(), L.d_px, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
+      H2D_CK(cudaMemcpy(py.data(), L.d_py, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
+    }
+    auto cnt = [&](int32_t b) {
+      return h->h_leaf_off[(int64_t)(b + 1) << sh] - h->h_leaf_off[(int64_t)b << sh];
+    };
+    std::vector<int64_t> pp(2 * np + 2);
+    for (int64_t p = 0; p < np; ++p) {
+      pp[2 * p] = pbase;
+      if (V.lmode[l] == LMODE_PAIR) pbase += cnt(px[p]);
+      pp[2 * p + 1] = pbase;
+      pbase += cnt(py[p]);
+    }
+    pp[2 * np] = pp[2 * np + 1] = pbase;
+    H2D_CK(cudaMalloc(&L.d_ppoff, sizeof(int64_t) * (2 * np + 2)));
+    H2D_CK(cudaMemcpy(L.d_ppoff, pp.data(), sizeof(int64_t) * (2 * np + 2), cudaMemcpyHostToDevice));
+    if (V.lmode[l] == LMODE_PAIR) {
+      for (int64_t p = 0; p < np; ++p)
+        if (L.h_rank[p] > 0) (mc <= kSmallPair ? pw_small : pw_big).push_back(make_int2(l, (int)p));
+    } else {
+      for (int64_t b = 0; b < ((int64_t)1 << (2 * l)); ++b)
+        if (cnt((int32_t)b) > 0) bw.push_back(make_int2(l, (int)b));
     }
   }
   V.pstride = std::max<int64_t>(pbase, 1);
-  V.nbig = (int64_t)big.size();
-  V.nsmall = (int64_t)small.size();
-  H2D_CK(cudaMalloc(&V.d_big, sizeof(int2) * std::max<int64_t>(V.nbig, 1)));
-  H2D_CK(cudaMalloc(&V.d_small, sizeof(int2) * std::max<int64_t>(V.nsmall, 1)));
-  if (V.nbig) H2D_CK(cudaMemcpy(V.d_big, big.data(), sizeof(int2) * V.nbig, cudaMemcpyHostToDevice));
-  if (V.nsmall)
-    H2D_CK(cudaMemcpy(V.d_small, small.data(), sizeof(int2) * V.nsmall, cudaMemcpyHostToDevice));
+  V.npw_big = (int64_t)pw_big.size();
+  V.npw_small = (int64_t)pw_small.size();
+  V.nbw = (int64_t)bw.size();
+  H2D_CK(cudaMalloc(&V.d_pw_big, sizeof(int2) * std::max<int64_t>(V.npw_big, 1)));
+  H2D_CK(cudaMalloc(&V.d_pw_small, sizeof(int2) * std::max<int64_t>(V.npw_small, 1)));
+  H2D_CK(cudaMalloc(&V.d_bw, sizeof(int2) * std::max<int64_t>(V.nbw, 1)));
+  if (V.npw_big)
+    H2D_CK(cudaMemcpy(V.d_pw_big, pw_big.data(), sizeof(int2) * V.npw_big, cudaMemcpyHostToDevice));
+  if (V.npw_small)
+    H2D_CK(cudaMemcpy(V.d_pw_small, pw_small.data(), sizeof(int2) * V.npw_small,
+                      cudaMemcpyHostToDevice));
+  if (V.nbw) H2D_CK(cudaMemcpy(V.d_bw, bw.data(), sizeof(int2) * V.nbw, cudaMemcpyHostToDevice));
+  // pair-mode values of partial results need zero for pairs of rank 0
+  V.zero_partials = false;
+  for (int l = V.lfuse; l <= kappa; ++l)
+    if (V.lmode[l] == LMODE_PAIR)
+      for (int64_t p = 0; p < h->lev[l].npairs; ++p)
+        if (h->lev[l].h_rank[p] == 0) V.zero_partials = true;
   // leaf of every tree position
   const int64_t nleaf = (int64_t)1 << (2 * kappa);
   H2D_CK(cudaMalloc(&V.d_leaf_of, sizeof(int32_t) * h->n));
@@ -537,10 +753,6 @@ int scratch_v2(hodlr2d* h, int nrhs) {
   return HODLR2D_OK;
 }
 
-static size_t fused_smem(int rmax, int kmax, int svals) {
-  return (size_t)8 * (3 * (size_t)rmax + 2 * (size_t)kmax + (size_t)svals);
-}
-
 template <class A>
 static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   using Val = typename A::val;
@@ -565,54 +777,52 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
                                        reinterpret_cast<const double*>(xt), n, nrhs,
                                        reinterpret_cast<double*>(yl));
     else
-      k_near_df32<<<nleaf, kNearThreads, 0, s>>>(
+      k_near_df32<<<(unsigned)((nleaf + kNearWarps - 1) / kNearWarps), 32 * kNearWarps, 0, s>>>(
           reinterpret_cast<const float2*>(V.d_xf), reinterpret_cast<const float2*>(V.d_yf),
-          h->d_perm, h->d_leaf_off, h->kappa, V.kff, reinterpret_cast<const float2*>(xt), n, nrhs,
-          reinterpret_cast<float2*>(yl));
+          h->d_perm, h->d_leaf_off, h->kappa, (int64_t)nleaf, V.kff,
+          reinterpret_cast<const float2*>(xt), n, nrhs, reinterpret_cast<float2*>(yl));
   }
+  int64_t two_pass_vals = 0;
+  for (int l = 1; l < V.lfuse; ++l) two_pass_vals += h->lev[l].nstored;
   if (V.nproj) {
-    int64_t two_pass_vals = 0;
-    for (int l = 1; l < V.lfuse; ++l) two_pass_vals += h->lev[l].nstored;
     {
       PhaseScope ps(h, 2, 1, 8 * two_pass_vals + 8 * V.proj_partials * nrhs);
-      const int64_t thr = V.nproj * 32;
-      k_proj2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(P, V.d_proj, V.nproj, xt,
-                                                                reinterpret_cast<Val*>(V.d_part));
+      const int64_t thr = V.proj_partials * 32;  // one warp per (task, column)
+      k_proj2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
+          P, V.d_proj, V.d_wtask, V.proj_partials, xt, reinterpret_cast<Val*>(V.d_part));
     }
     {
       PhaseScope ps(h, 3, 1, 8 * (V.proj_partials + h->t_total) * nrhs);
-      k_tsum2<A><<<(unsigned)((V.nsides + 255) / 256), 256, 0, s>>>(
-          P, V.d_proj, V.d_red, V.nsides, reinterpret_cast<const Val*>(V.d_part),
+      const int64_t thr = V.ntsum * 32;
+      k_tsum2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
+          P, V.d_proj, V.d_red, V.d_sideq, V.ntsum, reinterpret_cast<const Val*>(V.d_part),
           reinterpret_cast<Val*>(V.d_t));
     }
+  }
+  if (V.lfuse > 1) {
     {
       PhaseScope ps(h, 4, 1, 8 * two_pass_vals + vb * (V.lfuse - 1));
-      const int64_t thr = V.nexp * 32;
+      const int64_t thr = n * (V.lfuse - 1);
       k_exp2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
-          P, V.d_exp, V.nexp, reinterpret_cast<const Val*>(V.d_t), yl);
+          P, V.d_leaf_of, reinterpret_cast<const Val*>(V.d_t), yl);
     }
   }
-  if (V.nbig || V.nsmall) {
-    int64_t fused_vals = 0;
-    for (int l = V.lfuse; l <= h->kappa; ++l) fused_vals += h->lev[l].nstored;
-    PhaseScope ps(h, 6, (V.nbig ? 1 : 0) + (V.nsmall ? 1 : 0),
-                  8 * fused_vals + 8 * V.pstride * nrhs + vb * (h->kappa - V.lfuse + 1));
-    if (V.nbig) {
-      const int svals = 8192;
-      const size_t sm = fused_smem((int)V.rmax_big, V.kmax, svals);
-      H2D_CK(cudaFuncSetAttribute(k_fused<A, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm));
-      k_fused<A, 256><<<(unsigned)V.nbig, 256, sm, s>>>(P, V.d_big, (int)V.rmax_big, V.kmax, svals,
-                                                        xt, yl, ppart);
-    }
-    if (V.nsmall) {
-      const int svals = 2048;
-      const size_t sm = fused_smem((int)V.rmax_small, V.kmax, svals);
-      H2D_CK(cudaFuncSetAttribute(k_fused<A, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm));
-      k_fused<A, 64><<<(unsigned)V.nsmall, 64, sm, s>>>(P, V.d_small, (int)V.rmax_small, V.kmax,
-                                                        svals, xt, yl, ppart);
-    }
+  if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, s));
+  if (V.npw_big || V.npw_small) {
+    int64_t vals = 0;
+    for (int l = V.lfuse; l <= h->kappa; ++l)
+      if (V.lmode[l] == LMODE_PAIR) vals += h->lev[l].nstored;
+    PhaseScope ps(h, 6, (V.npw_big ? 1 : 0) + (V.npw_small ? 1 : 0), 8 * vals);
+    if (V.npw_big) k_pair<A, 256><<<(unsigned)V.npw_big, 256, 0, s>>>(P, V.d_pw_big, xt, ppart);
+    if (V.npw_small) k_pair<A, 64><<<(unsigned)V.npw_small, 64, 0, s>>>(P, V.d_pw_small, xt, ppart);
+  }
+  if (V.nbw) {
+    int64_t vals = 0;
+    for (int l = V.lfuse; l <= h->kappa; ++l)
+      if (V.lmode[l] == LMODE_BOX) vals += h->lev[l].nstored;
+    PhaseScope ps(h, 7, 1, 8 * vals);
+    k_box<A><<<(unsigned)((V.nbw + kBoxWarps - 1) / kBoxWarps), 32 * kBoxWarps, 0, s>>>(
+        P, V.d_bw, V.nbw, xt, yl, ppart);
   }
   {
     PhaseScope ps(h, 5, 1, vb * (h->kappa + 1) + 8 * V.pstride * nrhs + 16 * n + 8 * n * nrhs);
@@ -670,8 +880,11 @@ void free_v2(hodlr2d* h) {
   cudaFree(V.d_proj);
   cudaFree(V.d_exp);
   cudaFree(V.d_red);
-  cudaFree(V.d_big);
-  cudaFree(V.d_small);
+  cudaFree(V.d_wtask);
+  cudaFree(V.d_sideq);
+  cudaFree(V.d_pw_big);
+  cudaFree(V.d_pw_small);
+  cudaFree(V.d_bw);
   cudaFree(V.d_leaf_of);
   cudaFree(V.d_xt);
   cudaFree(V.d_yl);
