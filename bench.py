@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--modes", default="df32,f64",
+    p.add_argument("--modes", default="df32,f64,f32,bf16",
                    help="product modes to time; the first is the headline")
     p.add_argument("--n", type=int, default=N_FULL, help="points (smaller for quick checks)")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
@@ -154,11 +154,12 @@ def peaks():
 NCU_TRAFFIC = {}
 
 
-def cpu_baseline_leg(g_y_rows, rows, x, pts, n):
+def cpu_baseline_leg(rows, x, pts, n):
     """Oracle (single host core) on a bounded sample of the workload: its full
-    Alg. 2 product at N = 2^16 of the same recipe, scaled to N = 2^20 by the
-    ratio of stored factor values + dense entries; and its direct product on
-    the sampled rows, which also gives the GPU product's error."""
+    Alg. 2 product at N = 2^16 of the same recipe (timed; scaled to N = 2^20
+    by the paper's O(p N kappa) cost model); and its direct product on 256
+    sampled rows of the full problem, against which the GPU products' errors
+    are reported."""
     import oracle
     from paper_2204_05536_gb300 import inputs
     oracle.build()
@@ -166,8 +167,6 @@ def cpu_baseline_leg(g_y_rows, rows, x, pts, n):
     t0 = time.perf_counter()
     yd = oracle.direct_rows(pts, ko, x, rows)
     t_rows = time.perf_counter() - t0
-    err = float(np.linalg.norm(g_y_rows - yd) / np.linalg.norm(yd))
-    err_max = float(np.max(np.abs(g_y_rows - yd) / np.abs(yd)))
     ns = CPU_SAMPLE_N
     ps = inputs.uniform(ns, seed=0)
     xs = inputs.rhs(ns, seed=1)
@@ -182,7 +181,7 @@ def cpu_baseline_leg(g_y_rows, rows, x, pts, n):
         ts.append(time.perf_counter() - t0)
     t_mv = statistics.median(ts)
     return {"t_matvec_s": t_mv, "t_build_s": t_build, "values_sample": o.nvalues,
-            "kappa_sample": o.kappa, "t_rows_s": t_rows, "err_rel2": err, "err_max": err_max}
+            "kappa_sample": o.kappa, "t_rows_s": t_rows, "y_direct_rows": yd}
 
 
 def run_ours(args, ws, rank, local):
@@ -310,8 +309,7 @@ def run_ours(args, ws, rank, local):
     }
     if rank == 0 and not args.no_cpu:
         rows = np.random.default_rng(7).choice(n, 256, replace=False)
-        yrows = y.cpu().numpy()[rows]
-        cb = cpu_baseline_leg(yrows, rows, x_h, pts, n)
+        cb = cpu_baseline_leg(rows, x_h, pts, n)
         # the paper's cost model O(p N kappa) (Sec. 4.1) scales the sample
         scale = (n * st["kappa"]) / (CPU_SAMPLE_N * cb["kappa_sample"])
         full_est_s = cb["t_matvec_s"] * scale
@@ -320,8 +318,18 @@ def run_ours(args, ws, rank, local):
             "sample": "oracle Alg. 2 product at N=2^16 (same recipe, kappa %d), median of 3, "
                       "%.3f s, scaled x%.1f by N*kappa to N=2^20; oracle build %.1f s"
                       % (cb["kappa_sample"], cb["t_matvec_s"], scale, cb["t_build_s"])}
-        out["error_vs_direct"] = {"rel2_256_rows": cb["err_rel2"], "max_rel_256_rows": cb["err_max"],
-                                  "bound": 10 * EPS}
+        yd = cb["y_direct_rows"]
+        errs = {}
+        for m, v in per_mode.items():
+            yr = v["y"].cpu().numpy()[rows]
+            errs[m] = {"rel2_256_rows": float(np.linalg.norm(yr - yd) / np.linalg.norm(yd)),
+                       "max_rel_256_rows": float(np.max(np.abs(yr - yd) / np.abs(yd)))}
+        y64 = per_mode["f64"]["y"] if "f64" in per_mode else None
+        if y64 is not None:
+            for m, v in per_mode.items():
+                errs[m]["rel2_vs_f64_product"] = float(torch.linalg.norm(v["y"] - y64)
+                                                       / torch.linalg.norm(y64))
+        out["error_vs_direct"] = errs
     return out
 
 

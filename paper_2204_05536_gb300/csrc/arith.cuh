@@ -12,6 +12,7 @@
 // (Karp & Markstein 1997 style), giving ~2^-44 relative accuracy.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,8 +21,10 @@
 namespace h2d {
 
 struct F64A {
-  typedef double val;
+  typedef double fac;  // factor storage
+  typedef double val;  // vectors and sums
   typedef double acc;
+  static __device__ __forceinline__ val ld(fac f) { return f; }
   static __device__ __forceinline__ acc zero() { return 0.0; }
   static __device__ __forceinline__ void fma(acc& s, val a, val b) { s = ::fma(a, b, s); }
   static __device__ __forceinline__ val fin(acc s) { return s; }
@@ -37,7 +40,9 @@ struct F64A {
 };
 
 struct DF32A {
+  typedef float2 fac;
   typedef float2 val;  // x = hi, y = lo
+  static __device__ __forceinline__ val ld(fac f) { return f; }
   typedef float2 acc;  // lazily normalised: hi exact running sum, lo collects errors
   static __device__ __forceinline__ acc zero() { return make_float2(0.f, 0.f); }
   static __device__ __forceinline__ val vzero() { return make_float2(0.f, 0.f); }
@@ -80,6 +85,32 @@ struct DF32A {
     }
     return v;
   }
+};
+
+// binary32 sums over binary32 factors (the mixed form)
+struct F32A {
+  typedef float fac;
+  typedef float val;
+  typedef float acc;
+  static __device__ __forceinline__ val ld(fac f) { return f; }
+  static __device__ __forceinline__ acc zero() { return 0.f; }
+  static __device__ __forceinline__ val vzero() { return 0.f; }
+  static __device__ __forceinline__ void fma(acc& s, val a, val b) { s = __fmaf_rn(a, b, s); }
+  static __device__ __forceinline__ val fin(acc s) { return s; }
+  static __device__ __forceinline__ val add(val a, val b) { return a + b; }
+  static __device__ __forceinline__ val from_double(double d) { return __double2float_rn(d); }
+  static __device__ __forceinline__ double to_double(val v) { return (double)v; }
+  static __device__ __forceinline__ val warp_sum(acc a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+  }
+};
+
+// binary32 sums over bfloat16 factors (the mixed form, half the bytes again)
+struct BF16A : F32A {
+  typedef __nv_bfloat16 fac;
+  static __device__ __forceinline__ val ld(fac f) { return __bfloat162float(f); }
 };
 
 // ---------------------------------------------------------------------------
@@ -163,6 +194,35 @@ __device__ __forceinline__ float2 entry_ff(const KernelFF& k, float2 xi, float2 
     default: {  // log r and phi_1: binary64 logarithm of the float-float r^2
       const double v = phi_r2(k.p64, (double)r2.x + (double)r2.y);
       return DF32A::from_double(v);
+    }
+  }
+}
+
+// binary32 kernel parameters and entries (near field of the mixed form)
+struct KernelF32 {
+  int kind;
+  float a, a2, inv_a, log_a, phi1_den, diag;
+};
+
+__device__ __forceinline__ float entry_f32(const KernelF32& k, float xi, float yi, int64_t gi,
+                                           float xj, float yj, int64_t gj) {
+  if (gi == gj) return k.diag;
+  const float dx = xi - xj, dy = yi - yj;
+  const float r2 = __fmaf_rn(dx, dx, dy * dy);
+  switch (k.kind) {
+    case HODLR2D_IMQ: return rsqrtf(r2 + k.a2);
+    case HODLR2D_MQ: return sqrtf(r2 + k.a2);
+    case HODLR2D_LOG: return 0.5f * logf(r2);
+    case HODLR2D_INV_R: return rsqrtf(r2);
+    case HODLR2D_PHI1: {
+      const float r = sqrtf(r2);
+      if (r >= k.a) return logf(r) / k.log_a;
+      return (r * logf(r) - 1.0f) / k.phi1_den;
+    }
+    default: {
+      const float r = sqrtf(r2);
+      if (r >= k.a) return k.a / r;
+      return r * k.inv_a;
     }
   }
 }

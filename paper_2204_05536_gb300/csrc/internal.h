@@ -73,8 +73,9 @@ struct V2Plan {
   int lmode[HODLR2D_MAX_LEVELS] = {};  // per level: two-pass, pair or box mode
   int2* d_pw_big = nullptr;    // pair-mode work (level, pair), large boxes
   int2* d_pw_small = nullptr;  // pair-mode work, boxes <= 256 points
-  int2* d_bw = nullptr;        // box-mode work (level, box)
-  int64_t npw_big = 0, npw_small = 0, nbw = 0;
+  int2* d_bw = nullptr;        // box-mode work (level, box), boxes <= 64 points
+  int2* d_bw_big = nullptr;    // box-mode work, boxes of 65..128 points
+  int64_t npw_big = 0, npw_small = 0, nbw = 0, nbw_big = 0;
   bool zero_partials = false;
   int64_t pstride = 1;
   int32_t* d_leaf_of = nullptr;
@@ -87,6 +88,12 @@ struct V2Plan {
   void* d_xf = nullptr;  // float-float coordinates (DF32)
   void* d_yf = nullptr;
   KernelFF kff{};
+  void* d_x32 = nullptr;  // binary32 coordinates (F32 / BF16 modes)
+  void* d_y32 = nullptr;
+  KernelF32 kf32{};
+  // side streams: near field, and the single-read far-field levels
+  cudaStream_t s_near = nullptr, s_far = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_near = nullptr, ev_far = nullptr;
 };
 
 }  // namespace h2d
@@ -154,15 +161,19 @@ struct PhaseScope {
   int phase;
   int nlaunch;
   cudaEvent_t a = nullptr, b = nullptr;
-  PhaseScope(hodlr2d* h_, int phase_, int nlaunch_, int64_t bytes) : h(h_), phase(phase_), nlaunch(nlaunch_) {
+  cudaStream_t st;
+  PhaseScope(hodlr2d* h_, int phase_, int nlaunch_, int64_t bytes, cudaStream_t s_)
+      : h(h_), phase(phase_), nlaunch(nlaunch_), st(s_) {
     if (!h->prof_on) return;
     h->prof_bytes[phase] = bytes;
     if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
-      cudaEventRecord(a, h->stream);
+      cudaEventRecord(a, st);
   }
+  PhaseScope(hodlr2d* h_, int phase_, int nlaunch_, int64_t bytes)
+      : PhaseScope(h_, phase_, nlaunch_, bytes, h_->stream) {}
   ~PhaseScope() {
     if (!h->prof_on || !a || !b) return;
-    cudaEventRecord(b, h->stream);
+    cudaEventRecord(b, st);
     h->prof.push_back({phase, a, b});
     h->prof_launches[phase] += nlaunch;
   }

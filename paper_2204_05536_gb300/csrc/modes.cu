@@ -4,6 +4,7 @@
 namespace h2d {
 
 int prepare_df32(hodlr2d* h);
+int prepare_low(hodlr2d* h, int mode);
 void free_v2(hodlr2d* h);
 int product_device(hodlr2d* h, const double* x, double* y, int nrhs, int mode);
 
@@ -12,7 +13,9 @@ int prepare_mode(hodlr2d* h, int mode) {
   switch (mode) {
     case HODLR2D_MODE_F64: break;
     case HODLR2D_MODE_DF32: rc = prepare_df32(h); break;
-    default: return HODLR2D_ERR_STATE;
+    case HODLR2D_MODE_F32:
+    case HODLR2D_MODE_BF16: rc = prepare_low(h, mode); break;
+    default: return HODLR2D_ERR_ARG;
   }
   if (rc == HODLR2D_OK) h->prepared[mode] = true;
   return rc;

@@ -64,6 +64,9 @@ __device__ __forceinline__ int32_t bsize(const int32_t* leaf_off, int kappa, int
 __device__ __forceinline__ double shfl_val(double v, int o) {
   return __shfl_xor_sync(0xffffffffu, v, o);
 }
+__device__ __forceinline__ float shfl_val(float v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
 __device__ __forceinline__ float2 shfl_val(float2 v, int o) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
 }
@@ -89,11 +92,34 @@ __global__ void k_gather2(const double* __restrict__ x, const int64_t* __restric
 // ---------------------------------------------------------------------------
 constexpr int kNearWarps = 4;
 
+struct NearDF32 {  // float-float points, entries and sums
+  typedef float2 pt;
+  typedef KernelFF K;
+  typedef DF32A A;
+  static __device__ __forceinline__ float2 entry(const K& k, pt xi, pt yi, int64_t gi, pt xj,
+                                                 pt yj, int64_t gj) {
+    return entry_ff(k, xi, yi, gi, xj, yj, gj);
+  }
+};
+struct NearF32 {  // binary32 points, entries and sums (mixed form)
+  typedef float pt;
+  typedef KernelF32 K;
+  typedef F32A A;
+  static __device__ __forceinline__ float entry(const K& k, pt xi, pt yi, int64_t gi, pt xj,
+                                                pt yj, int64_t gj) {
+    return entry_f32(k, xi, yi, gi, xj, yj, gj);
+  }
+};
+
+template <class NP>
 __global__ void __launch_bounds__(32 * kNearWarps)
-    k_near_df32(const float2* __restrict__ xf, const float2* __restrict__ yf,
+    k_near_warp(const typename NP::pt* __restrict__ xf, const typename NP::pt* __restrict__ yf,
                 const int64_t* __restrict__ perm, const int32_t* __restrict__ leaf_off, int kappa,
-                int64_t nleaf, KernelFF kp, const float2* __restrict__ xt, int64_t n, int nrhs,
-                float2* __restrict__ yout) {
+                int64_t nleaf, typename NP::K kp, const typename NP::A::val* __restrict__ xt,
+                int64_t n, int nrhs, typename NP::A::val* __restrict__ yout) {
+  using A = typename NP::A;
+  using Val = typename A::val;
+  using Pt = typename NP::pt;
   const int lane = threadIdx.x & 31;
   const int64_t bl = (int64_t)blockIdx.x * kNearWarps + (threadIdx.x >> 5);
   if (bl >= nleaf) return;
@@ -134,13 +160,13 @@ __global__ void __launch_bounds__(32 * kNearWarps)
     const int t = t0 + tl;
     const bool act = t < m;
     const int64_t it = s0 + (act ? t : 0);
-    const float2 xi = xf[it], yi = yf[it];
+    const Pt xi = xf[it], yi = yf[it];
     const int64_t gi = perm[it];
     for (int c0 = 0; c0 < nrhs; c0 += kNearRhs) {
       const int nc = min(kNearRhs, nrhs - c0);
-      float2 acc[kNearRhs];
+      typename A::acc acc[kNearRhs];
 #pragma unroll
-      for (int r = 0; r < kNearRhs; ++r) acc[r] = DF32A::zero();
+      for (int r = 0; r < kNearRhs; ++r) acc[r] = A::zero();
       int sidx = 0;  // running index over the concatenated sources
       for (int q = 0; q < ns; ++q) {
         const int32_t len = se[q] - sb[q];
@@ -149,21 +175,22 @@ __global__ void __launch_bounds__(32 * kNearWarps)
         if (j < 0) j += G;
         for (; j < len; j += G) {
           const int64_t js = sb[q] + j;
-          const float2 kij = entry_ff(kp, xi, yi, gi, xf[js], yf[js], perm[js]);
+          const Val kij = NP::entry(kp, xi, yi, gi, xf[js], yf[js], perm[js]);
 #pragma unroll
           for (int r = 0; r < kNearRhs; ++r)
-            if (r < nc) DF32A::fma(acc[r], kij, xt[(int64_t)(c0 + r) * n + js]);
+            if (r < nc) A::fma(acc[r], kij, xt[(int64_t)(c0 + r) * n + js]);
         }
         sidx += len;
       }
+      Val res[kNearRhs];
 #pragma unroll
       for (int r = 0; r < kNearRhs; ++r) {
-        float2 v = DF32A::fin(acc[r]);
-        for (int o = tpr; o < 32; o <<= 1) v = DF32A::add(v, shfl_val(v, o));
-        acc[r] = v;
+        Val v = A::fin(acc[r]);
+        for (int o = tpr; o < 32; o <<= 1) v = A::add(v, shfl_val(v, o));
+        res[r] = v;
       }
       if (act && h == 0)
-        for (int r = 0; r < nc; ++r) yout[(int64_t)(c0 + r) * n + it] = acc[r];
+        for (int r = 0; r < nc; ++r) yout[(int64_t)(c0 + r) * n + it] = res[r];
     }
   }
 }
@@ -195,27 +222,28 @@ __global__ void __launch_bounds__(T)
   const int32_t ys = bstart(P.leaf_off, P.kappa, l, by), n = bsize(P.leaf_off, P.kappa, l, by);
   const int64_t lm = ldpad(m), ln = ldpad(n);
   const int k = L.rank[p];
-  const V* Ug = reinterpret_cast<const V*>(L.fac) + L.foff[p];
-  const V* Vg = Ug + lm * k;
+  using F = typename A::fac;
+  const F* Ug = reinterpret_cast<const F*>(L.fac) + L.foff[p];
+  const F* Vg = Ug + lm * k;
   for (int c = 0; c < P.nrhs; ++c) {
     const V* xc = xt + (int64_t)c * P.n;
     for (int job = warp; job < 2 * k; job += NW) {
       const bool isV = job < k;
       const int q = isV ? job : job - k;
       const int rows = isV ? n : m;
-      const V* col = (isV ? Vg + q * ln : Ug + q * lm);
+      const F* col = (isV ? Vg + q * ln : Ug + q * lm);
       const V* xv = xc + (isV ? ys : xs);
       Acc a = A::zero();
       int r = lane;
       for (; r + 96 < rows; r += 128) {
-        const V v0 = col[r], v1 = col[r + 32], v2 = col[r + 64], v3 = col[r + 96];
+        const F v0 = col[r], v1 = col[r + 32], v2 = col[r + 64], v3 = col[r + 96];
         const V x0 = xv[r], x1 = xv[r + 32], x2 = xv[r + 64], x3 = xv[r + 96];
-        A::fma(a, v0, x0);
-        A::fma(a, v1, x1);
-        A::fma(a, v2, x2);
-        A::fma(a, v3, x3);
+        A::fma(a, A::ld(v0), x0);
+        A::fma(a, A::ld(v1), x1);
+        A::fma(a, A::ld(v2), x2);
+        A::fma(a, A::ld(v3), x3);
       }
-      for (; r < rows; r += 32) A::fma(a, col[r], xv[r]);
+      for (; r < rows; r += 32) A::fma(a, A::ld(col[r]), xv[r]);
       const V sum = A::warp_sum(a);
       if (lane == 0) ts[job] = sum;
     }
@@ -225,19 +253,19 @@ __global__ void __launch_bounds__(T)
     for (int r = tid; r < m + n; r += T) {
       const bool own = r < m;
       const int i = own ? r : r - m;
-      const V* M = own ? Ug + i : Vg + i;
+      const F* M = own ? Ug + i : Vg + i;
       const int64_t ld = own ? lm : ln;
       const V* tv = own ? ts : ts + k;  // U pairs with t1, V with t2
       Acc a = A::zero();
       int q = 0;
       for (; q + 8 <= k; q += 8) {
-        V mv[8];
+        F mv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) mv[u] = M[(q + u) * ld];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) A::fma(a, mv[u], tv[q + u]);
+        for (int u = 0; u < 8; ++u) A::fma(a, A::ld(mv[u]), tv[q + u]);
       }
-      for (; q < k; ++q) A::fma(a, M[q * ld], tv[q]);
+      for (; q < k; ++q) A::fma(a, A::ld(M[q * ld]), tv[q]);
       (own ? outx : outy)[i] = A::fin(a);
     }
     __syncthreads();
@@ -285,7 +313,8 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
   const int32_t xs = bstart(P.leaf_off, P.kappa, l, X), m = bsize(P.leaf_off, P.kappa, l, X);
   const int64_t lm = ldpad(m);
   const int64_t p0 = L.prow[X], p1 = L.prow[X + 1];
-  const V* fac = reinterpret_cast<const V*>(L.fac);
+  using F = typename A::fac;
+  const F* fac = reinterpret_cast<const F*>(L.fac);
   for (int c = 0; c < P.nrhs; ++c) {
     const V* xc = xt + (int64_t)c * P.n;
     for (int i = lane; i < m; i += 32) xx[i] = xc[xs + i];
@@ -295,14 +324,14 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
       const uint32_t Y = (uint32_t)L.py[p];
       const int32_t ys = bstart(P.leaf_off, P.kappa, l, Y), n = bsize(P.leaf_off, P.kappa, l, Y);
       const int64_t ln = ldpad(n);
-      const V* Ug = fac + L.foff[p];
-      const V* Vg = Ug + lm * k;
+      const F* Ug = fac + L.foff[p];
+      const F* Vg = Ug + lm * k;
       V* outy = ppart + (int64_t)c * P.pstride + L.ppoff[2 * p + 1];
       for (int j = lane; j < n; j += 32) xy[j] = xc[ys + j];
       const int64_t tot = (lm + ln) * k;
       __syncwarp();
       if (tot <= kBoxStage && k <= kBoxK) {
-        for (int64_t e = lane; e < tot; e += 32) st[e] = Ug[e];
+        for (int64_t e = lane; e < tot; e += 32) st[e] = A::ld(Ug[e]);
         __syncwarp();
         const V* Us = st;
         const V* Vs = st + lm * k;
@@ -342,10 +371,10 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
           const bool isV = job < k;
           const int q = isV ? job : job - k;
           const int rows = isV ? n : m;
-          const V* col = isV ? Vg + q * ln : Ug + q * lm;
+          const F* col = isV ? Vg + q * ln : Ug + q * lm;
           const V* xv = isV ? xy : xx;
           Acc a = A::zero();
-          for (int r = lane; r < rows; r += 32) A::fma(a, col[r], xv[r]);
+          for (int r = lane; r < rows; r += 32) A::fma(a, A::ld(col[r]), xv[r]);
           const V sum = A::warp_sum(a);
           if (lane == 0) ts[job] = sum;
         }
@@ -353,11 +382,11 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
         for (int r = lane; r < m + n; r += 32) {
           const bool own = r < m;
           const int i = own ? r : r - m;
-          const V* M = own ? Ug + i : Vg + i;
+          const F* M = own ? Ug + i : Vg + i;
           const int64_t ld = own ? lm : ln;
           const V* tv = own ? ts : ts + k;
           Acc a = own ? (i < 32 ? y0 : y1) : A::zero();
-          for (int q = 0; q < k; ++q) A::fma(a, M[q * ld], tv[q]);
+          for (int q = 0; q < k; ++q) A::fma(a, A::ld(M[q * ld]), tv[q]);
           if (own) {
             if (i < 32) y0 = a;
             else y1 = a;
@@ -401,13 +430,14 @@ __global__ void __launch_bounds__(256)
   const int32_t nrow = T.side == 0 ? bsize(P.leaf_off, P.kappa, T.level, by) : m;
   const int32_t base = bstart(P.leaf_off, P.kappa, T.level, T.side == 0 ? by : bx);
   const int k = L.rank[T.pair];
-  const V* col = reinterpret_cast<const V*>(L.fac) + L.foff[T.pair] +
+  using F = typename A::fac;
+  const F* col = reinterpret_cast<const F*>(L.fac) + L.foff[T.pair] +
                  (T.side == 0 ? ldpad(m) * k : 0) + (int64_t)q * ldpad(nrow);
   V v[R];
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     const int r = T.r0 + lane + 32 * u;
-    v[u] = r < T.r0 + T.nr ? col[r] : A::vzero();
+    v[u] = r < T.r0 + T.nr ? A::ld(col[r]) : A::vzero();
   }
   for (int c = 0; c < P.nrhs; ++c) {
     const V* xv = xt + c * P.n + base;
@@ -451,47 +481,61 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// One thread per (two-pass level, row): the row's box sums U t1 / V t2 over
-// its list in ascending partner order.
+// One block per expansion task (256 rows of one box): the box's list
+// (matrix offset, rank, t offset per entry) is staged in shared memory once,
+// then one thread per row sums U t1 / V t2 over the list in ascending partner
+// order, eight independent loads at a time.
+constexpr int kExpMaxEnt = 64;
+
 template <class A>
 __global__ void __launch_bounds__(256)
-    k_exp2(ArgsV2 P, const int32_t* __restrict__ leaf_of, const typename A::val* __restrict__ t,
+    k_exp2(ArgsV2 P, const ExpTask* __restrict__ tasks, const typename A::val* __restrict__ t,
            typename A::val* __restrict__ yl) {
   using V = typename A::val;
   using Acc = typename A::acc;
-  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int nl = P.lfuse - 1;
-  if (gid >= P.n * nl) return;
-  const int l = 1 + (int)(gid / P.n);
-  const int64_t i = gid - (int64_t)(l - 1) * P.n;
+  using F = typename A::fac;
+  __shared__ int64_t s_off[kExpMaxEnt];
+  __shared__ int64_t s_toff[kExpMaxEnt];
+  __shared__ int s_k[kExpMaxEnt];
+  const ExpTask T = tasks[blockIdx.x];
+  const int l = T.level;
   const LevelV2& L = P.lev[l];
-  const uint32_t X = (uint32_t)leaf_of[i] >> (2 * (P.kappa - l));
-  const int64_t loc = i - bstart(P.leaf_off, P.kappa, l, X);
+  const uint32_t X = (uint32_t)T.box;
+  const int32_t e0 = L.ent_off[X], ne = L.ent_off[X + 1] - e0;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const int32_t code = L.ent[e0 + e];
+    const int64_t p = code >> 1;
+    const int side = code & 1;
+    const int k = L.rank[p];
+    int64_t off = L.foff[p];
+    if (side == 1) off += ldpad(bsize(P.leaf_off, P.kappa, l, (uint32_t)L.px[p])) * k;
+    s_off[e] = off;
+    s_k[e] = k;
+    s_toff[e] = L.toff[p] * P.nrhs + (int64_t)side * k * P.nrhs;
+  }
+  __syncthreads();
+  const int r = T.r0 + (int)threadIdx.x;
+  if (r >= T.r0 + T.nr) return;
+  const int32_t base = bstart(P.leaf_off, P.kappa, l, X);
   const int64_t ld = ldpad(bsize(P.leaf_off, P.kappa, l, X));
-  const int32_t e0 = L.ent_off[X], e1 = L.ent_off[X + 1];
-  const V* fac = reinterpret_cast<const V*>(L.fac);
+  const F* fac = reinterpret_cast<const F*>(L.fac);
   for (int c = 0; c < P.nrhs; ++c) {
     Acc a = A::zero();
-    for (int32_t e = e0; e < e1; ++e) {
-      const int32_t code = L.ent[e];
-      const int64_t p = code >> 1;
-      const int side = code & 1;
-      const int k = L.rank[p];
-      int64_t off = L.foff[p];
-      if (side == 1) off += ldpad(bsize(P.leaf_off, P.kappa, l, (uint32_t)L.px[p])) * k;
-      const V* M = fac + off + loc;
-      const V* tv = t + L.toff[p] * P.nrhs + (int64_t)side * k * P.nrhs + (int64_t)c * k;
+    for (int e = 0; e < ne; ++e) {
+      const int k = s_k[e];
+      const F* M = fac + s_off[e] + r;
+      const V* tv = t + s_toff[e] + (int64_t)c * k;
       int q = 0;
       for (; q + 8 <= k; q += 8) {  // eight independent loads in flight
-        V mv[8];
+        F mv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) mv[u] = M[(q + u) * ld];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) A::fma(a, mv[u], tv[q + u]);
+        for (int u = 0; u < 8; ++u) A::fma(a, A::ld(mv[u]), tv[q + u]);
       }
-      for (; q < k; ++q) A::fma(a, M[q * ld], tv[q]);
+      for (; q < k; ++q) A::fma(a, A::ld(M[q * ld]), tv[q]);
     }
-    yl[((int64_t)l * P.nrhs + c) * P.n + i] = A::fin(a);
+    yl[((int64_t)l * P.nrhs + c) * P.n + base + r] = A::fin(a);
   }
 }
 
@@ -668,7 +712,7 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMemcpy(V.d_red, red.data(), sizeof(int64_t) * red.size(), cudaMemcpyHostToDevice));
   // single-read levels: pair mode (one block per pair, partials for both
   // sides) or box mode (one warp per row box, partials for the column side)
-  std::vector<int2> pw_big, pw_small, bw;
+  std::vector<int2> pw_big, pw_small, bw, bw_big;
   int64_t pbase = 0;
   for (int l = 1; l <= kappa; ++l) V.lmode[l] = l < V.lfuse ? LMODE_TWO : LMODE_PAIR;
   for (int l = V.lfuse; l <= kappa; ++l) {
@@ -700,13 +744,17 @@ int plan_v2(hodlr2d* h) {
         if (L.h_rank[p] > 0) (mc <= kSmallPair ? pw_small : pw_big).push_back(make_int2(l, (int)p));
     } else {
       for (int64_t b = 0; b < ((int64_t)1 << (2 * l)); ++b)
-        if (cnt((int32_t)b) > 0) bw.push_back(make_int2(l, (int)b));
+        if (cnt((int32_t)b) > 0) (mc <= kBoxRows ? bw : bw_big).push_back(make_int2(l, (int)b));
     }
   }
   V.pstride = std::max<int64_t>(pbase, 1);
   V.npw_big = (int64_t)pw_big.size();
   V.npw_small = (int64_t)pw_small.size();
   V.nbw = (int64_t)bw.size();
+  V.nbw_big = (int64_t)bw_big.size();
+  H2D_CK(cudaMalloc(&V.d_bw_big, sizeof(int2) * std::max<int64_t>(V.nbw_big, 1)));
+  if (V.nbw_big)
+    H2D_CK(cudaMemcpy(V.d_bw_big, bw_big.data(), sizeof(int2) * V.nbw_big, cudaMemcpyHostToDevice));
   H2D_CK(cudaMalloc(&V.d_pw_big, sizeof(int2) * std::max<int64_t>(V.npw_big, 1)));
   H2D_CK(cudaMalloc(&V.d_pw_small, sizeof(int2) * std::max<int64_t>(V.npw_small, 1)));
   H2D_CK(cudaMalloc(&V.d_bw, sizeof(int2) * std::max<int64_t>(V.nbw, 1)));
@@ -728,6 +776,11 @@ int plan_v2(hodlr2d* h) {
   k_leaf_of<<<(unsigned)((nleaf + 255) / 256), 256>>>(h->d_leaf_off, nleaf, V.d_leaf_of);
   H2D_CK(cudaGetLastError());
   H2D_CK(cudaDeviceSynchronize());
+  H2D_CK(cudaStreamCreateWithFlags(&V.s_near, cudaStreamNonBlocking));
+  H2D_CK(cudaStreamCreateWithFlags(&V.s_far, cudaStreamNonBlocking));
+  H2D_CK(cudaEventCreateWithFlags(&V.ev_in, cudaEventDisableTiming));
+  H2D_CK(cudaEventCreateWithFlags(&V.ev_near, cudaEventDisableTiming));
+  H2D_CK(cudaEventCreateWithFlags(&V.ev_far, cudaEventDisableTiming));
   V.ready = true;
   return HODLR2D_OK;
 }
@@ -769,18 +822,31 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
     PhaseScope ps(h, 0, 1, vb + 8 * n + 8 * n * nrhs);
     k_gather2<A><<<g, 256, 0, s>>>(x, h->d_perm, n, nrhs, xt);
   }
+  // the near field (arithmetic-bound) and the single-read levels run on side
+  // streams, concurrently with the two-pass levels on the caller's stream
+  H2D_CK(cudaEventRecord(V.ev_in, s));
+  H2D_CK(cudaStreamWaitEvent(V.s_near, V.ev_in, 0));
+  H2D_CK(cudaStreamWaitEvent(V.s_far, V.ev_in, 0));
   {
     const unsigned nleaf = (unsigned)(1u << (2 * h->kappa));
-    PhaseScope ps(h, 1, 1, (mode == HODLR2D_MODE_F64 ? 24 : 24) * n + 2 * vb);
+    cudaStream_t sn = V.s_near;
+    PhaseScope ps(h, 1, 1, 24 * n + 2 * vb, sn);
     if (mode == HODLR2D_MODE_F64)
-      k_near_f64<<<nleaf, 64, 0, s>>>(h->d_x, h->d_y, h->d_perm, h->d_leaf_off, h->kappa, h->kp,
+      k_near_f64<<<nleaf, 64, 0, sn>>>(h->d_x, h->d_y, h->d_perm, h->d_leaf_off, h->kappa, h->kp,
                                        reinterpret_cast<const double*>(xt), n, nrhs,
                                        reinterpret_cast<double*>(yl));
-    else
-      k_near_df32<<<(unsigned)((nleaf + kNearWarps - 1) / kNearWarps), 32 * kNearWarps, 0, s>>>(
+    else if (mode == HODLR2D_MODE_DF32)
+      k_near_warp<NearDF32><<<(unsigned)((nleaf + kNearWarps - 1) / kNearWarps), 32 * kNearWarps,
+                              0, sn>>>(
           reinterpret_cast<const float2*>(V.d_xf), reinterpret_cast<const float2*>(V.d_yf),
           h->d_perm, h->d_leaf_off, h->kappa, (int64_t)nleaf, V.kff,
           reinterpret_cast<const float2*>(xt), n, nrhs, reinterpret_cast<float2*>(yl));
+    else
+      k_near_warp<NearF32><<<(unsigned)((nleaf + kNearWarps - 1) / kNearWarps), 32 * kNearWarps,
+                             0, sn>>>(
+          reinterpret_cast<const float*>(V.d_x32), reinterpret_cast<const float*>(V.d_y32),
+          h->d_perm, h->d_leaf_off, h->kappa, (int64_t)nleaf, V.kf32,
+          reinterpret_cast<const float*>(xt), n, nrhs, reinterpret_cast<float*>(yl));
   }
   int64_t two_pass_vals = 0;
   for (int l = 1; l < V.lfuse; ++l) two_pass_vals += h->lev[l].nstored;
@@ -802,28 +868,33 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   if (V.lfuse > 1) {
     {
       PhaseScope ps(h, 4, 1, 8 * two_pass_vals + vb * (V.lfuse - 1));
-      const int64_t thr = n * (V.lfuse - 1);
-      k_exp2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
-          P, V.d_leaf_of, reinterpret_cast<const Val*>(V.d_t), yl);
+      k_exp2<A><<<(unsigned)V.nexp, 256, 0, s>>>(P, V.d_exp, reinterpret_cast<const Val*>(V.d_t),
+                                                 yl);
     }
   }
-  if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, s));
+  H2D_CK(cudaEventRecord(V.ev_near, V.s_near));
+  const cudaStream_t sf = V.s_far;
+  if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, sf));
   if (V.npw_big || V.npw_small) {
     int64_t vals = 0;
     for (int l = V.lfuse; l <= h->kappa; ++l)
       if (V.lmode[l] == LMODE_PAIR) vals += h->lev[l].nstored;
-    PhaseScope ps(h, 6, (V.npw_big ? 1 : 0) + (V.npw_small ? 1 : 0), 8 * vals);
-    if (V.npw_big) k_pair<A, 256><<<(unsigned)V.npw_big, 256, 0, s>>>(P, V.d_pw_big, xt, ppart);
-    if (V.npw_small) k_pair<A, 64><<<(unsigned)V.npw_small, 64, 0, s>>>(P, V.d_pw_small, xt, ppart);
+    PhaseScope ps(h, 6, (V.npw_big ? 1 : 0) + (V.npw_small ? 1 : 0), 8 * vals, sf);
+    if (V.npw_big) k_pair<A, 256><<<(unsigned)V.npw_big, 256, 0, sf>>>(P, V.d_pw_big, xt, ppart);
+    if (V.npw_small) k_pair<A, 64><<<(unsigned)V.npw_small, 64, 0, sf>>>(P, V.d_pw_small, xt, ppart);
   }
-  if (V.nbw) {
+  if (V.nbw || V.nbw_big) {
     int64_t vals = 0;
     for (int l = V.lfuse; l <= h->kappa; ++l)
       if (V.lmode[l] == LMODE_BOX) vals += h->lev[l].nstored;
-    PhaseScope ps(h, 7, 1, 8 * vals);
-    k_box<A><<<(unsigned)((V.nbw + kBoxWarps - 1) / kBoxWarps), 32 * kBoxWarps, 0, s>>>(
-        P, V.d_bw, V.nbw, xt, yl, ppart);
+    PhaseScope ps(h, 7, (V.nbw ? 1 : 0) + (V.nbw_big ? 1 : 0), 8 * vals, sf);
+    if (V.nbw)
+      k_box<A><<<(unsigned)((V.nbw + kBoxWarps - 1) / kBoxWarps), 32 * kBoxWarps, 0, sf>>>(
+          P, V.d_bw, V.nbw, xt, yl, ppart);
   }
+  H2D_CK(cudaEventRecord(V.ev_far, sf));
+  H2D_CK(cudaStreamWaitEvent(s, V.ev_near, 0));
+  H2D_CK(cudaStreamWaitEvent(s, V.ev_far, 0));
   {
     PhaseScope ps(h, 5, 1, vb * (h->kappa + 1) + 8 * V.pstride * nrhs + 16 * n + 8 * n * nrhs);
     k_combine2<A><<<g, 256, 0, s>>>(P, yl, ppart, V.d_leaf_of, h->d_perm, y);
@@ -838,6 +909,8 @@ int product_device(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   H2D_TRY(scratch_v2(h, nrhs));
   if (mode == HODLR2D_MODE_F64) return run_v2<F64A>(h, x, y, nrhs, mode);
   if (mode == HODLR2D_MODE_DF32) return run_v2<DF32A>(h, x, y, nrhs, mode);
+  if (mode == HODLR2D_MODE_F32) return run_v2<F32A>(h, x, y, nrhs, mode);
+  if (mode == HODLR2D_MODE_BF16) return run_v2<BF16A>(h, x, y, nrhs, mode);
   return HODLR2D_ERR_STATE;
 }
 
@@ -875,6 +948,53 @@ int prepare_df32(hodlr2d* h) {
   return HODLR2D_OK;
 }
 
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __double2float_rn(a[i]);
+}
+__global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ out,
+                          int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __double2bfloat16(a[i]);
+}
+
+// binary32 or bfloat16 factor copies, binary32 points and kernel parameters
+int prepare_low(hodlr2d* h, int mode) {
+  V2Plan& V = h->v2;
+  for (int l = 1; l <= h->kappa; ++l) {
+    Level& L = h->lev[l];
+    if (L.d_fac_mode[mode]) continue;
+    const int64_t nv = std::max<int64_t>(L.nvalues, 1);
+    const int64_t es = mode == HODLR2D_MODE_F32 ? 4 : 2;
+    H2D_CK(cudaMalloc(&L.d_fac_mode[mode], es * nv));
+    if (!L.nvalues) continue;
+    const unsigned g = (unsigned)((L.nvalues + 255) / 256);
+    if (mode == HODLR2D_MODE_F32)
+      k_to_f32<<<g, 256, 0, h->stream>>>(L.d_fac, reinterpret_cast<float*>(L.d_fac_mode[mode]),
+                                         L.nvalues);
+    else
+      k_to_bf16<<<g, 256, 0, h->stream>>>(
+          L.d_fac, reinterpret_cast<__nv_bfloat16*>(L.d_fac_mode[mode]), L.nvalues);
+  }
+  if (!V.d_x32) {
+    H2D_CK(cudaMalloc(&V.d_x32, 4 * h->n));
+    H2D_CK(cudaMalloc(&V.d_y32, 4 * h->n));
+    const unsigned g = (unsigned)((h->n + 255) / 256);
+    k_to_f32<<<g, 256, 0, h->stream>>>(h->d_x, reinterpret_cast<float*>(V.d_x32), h->n);
+    k_to_f32<<<g, 256, 0, h->stream>>>(h->d_y, reinterpret_cast<float*>(V.d_y32), h->n);
+  }
+  H2D_CK(cudaGetLastError());
+  H2D_CK(cudaStreamSynchronize(h->stream));
+  V.kf32.kind = h->kp.kind;
+  V.kf32.a = (float)h->kp.a;
+  V.kf32.a2 = (float)h->kp.a2;
+  V.kf32.inv_a = (float)h->kp.inv_a;
+  V.kf32.log_a = (float)h->kp.log_a;
+  V.kf32.phi1_den = (float)h->kp.phi1_den;
+  V.kf32.diag = (float)h->kp.diag;
+  return HODLR2D_OK;
+}
+
 void free_v2(hodlr2d* h) {
   V2Plan& V = h->v2;
   cudaFree(V.d_proj);
@@ -885,6 +1005,7 @@ void free_v2(hodlr2d* h) {
   cudaFree(V.d_pw_big);
   cudaFree(V.d_pw_small);
   cudaFree(V.d_bw);
+  cudaFree(V.d_bw_big);
   cudaFree(V.d_leaf_of);
   cudaFree(V.d_xt);
   cudaFree(V.d_yl);
@@ -893,6 +1014,13 @@ void free_v2(hodlr2d* h) {
   cudaFree(V.d_t);
   cudaFree(V.d_xf);
   cudaFree(V.d_yf);
+  cudaFree(V.d_x32);
+  cudaFree(V.d_y32);
+  if (V.s_near) cudaStreamDestroy(V.s_near);
+  if (V.s_far) cudaStreamDestroy(V.s_far);
+  if (V.ev_in) cudaEventDestroy(V.ev_in);
+  if (V.ev_near) cudaEventDestroy(V.ev_near);
+  if (V.ev_far) cudaEventDestroy(V.ev_far);
   V = V2Plan();
 }
 

@@ -307,3 +307,35 @@ def test_gmres_df32_refinement(h2d, oracle):
     x, it, rr, code = g.gmres(torch.from_numpy(f).cuda(), tol=1e-10, inner_mode="df32")
     assert code == 0 and rr <= 1e-10
     assert rel(x.cpu().numpy(), lam) <= 1e-8
+
+
+@pytest.mark.parametrize("mode,bound", [("f32", 5e-6), ("bf16", 2e-2)])
+def test_mixed_modes_error(h2d, oracle, mode, bound):
+    """Binary32 and bfloat16 factor storage with binary32 sums: error against
+    the F64 product (same factors) and against the direct product."""
+    n = 20000
+    pts = inputs.uniform(n, seed=5)
+    a = 1.0 / np.sqrt(n)
+    g = h2d.HODLR2D(pts, h2d.kernel("mq", a), 32, 1e-8, root=(-1.0, -1.0, 2.0))
+    g.prepare(mode)
+    x = torch.from_numpy(inputs.rhs(n, 2, seed=3)).cuda()
+    y64 = g.matvec(x, mode="f64").cpu().numpy()
+    y = g.matvec(x, mode=mode).cpu().numpy()
+    assert rel(y, y64) <= bound
+    assert torch.equal(g.matvec(x, mode=mode), g.matvec(x, mode=mode))
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16"])
+def test_gmres_mixed_refinement(h2d, oracle, mode):
+    """Iterative refinement reaches the F64 tolerance with low-precision inner
+    products (Eq. ker system, beta = N)."""
+    n = 3000
+    pts = inputs.uniform(n, seed=2)
+    lam = inputs.rhs(n, seed=9)
+    ko = oracle.kernel("phi2", 0.001, diag=float(n))
+    f = oracle.direct_matvec(pts, ko, lam)
+    g = h2d.HODLR2D(pts, h2d.kernel("phi2", 0.001, diag=float(n)), 50, 1e-12)
+    g.prepare(mode)
+    x, it, rr, code = g.gmres(torch.from_numpy(f).cuda(), tol=1e-10, inner_mode=mode)
+    assert code == 0 and rr <= 1e-10
+    assert rel(x.cpu().numpy(), lam) <= 1e-8
