@@ -91,6 +91,11 @@ typedef struct {
   int max_rank;    /* ACA rank cap per block (default 256).  A block that hits
                       the cap before eps is counted in stats.unconverged.      */
   int mode;        /* hodlr2d_mode used by hodlr2d_matvec (default F64).      */
+  void* rank_model; /* NULL (default), or a hodlr2d_rank_model_t: each ACA runs
+                      with the rank cap the model predicts (workspace sized up
+                      front); a pair that reaches it without meeting eps is
+                      redone with the full cap, so the factors are those of
+                      the build without a model.                              */
 } hodlr2d_opts;
 
 typedef struct hodlr2d* hodlr2d_t;
@@ -166,6 +171,9 @@ typedef struct {
   double compression_ratio;                  /* (far_values + near_entries)/N^2 */
   double build_ms[4];                        /* tree, lists, ACA, pack        */
   int64_t bytes_per_matvec[4];               /* algorithmic bytes, per mode   */
+  int64_t aca_fallbacks;                     /* pairs redone after a predicted
+                                                cap (rank model) was too small */
+  int64_t aca_workspace_values;              /* largest ACA workspace batch   */
 } hodlr2d_stats;
 
 int hodlr2d_get_stats(hodlr2d_t h, hodlr2d_stats* s);
@@ -208,6 +216,38 @@ int hodlr2d_import_factors(hodlr2d_t h, int64_t npairs, const int32_t* info,
 /* Export: pass values = NULL to get *npairs and *nvalues only. */
 int hodlr2d_export_factors(hodlr2d_t h, int64_t* npairs, int64_t* nvalues,
                            int32_t* info, int64_t* offsets, double* values);
+
+/* ----- learned rank predictor (spec extension; not in the paper) -----
+ * An 8 -> H -> H -> 1 ReLU network in binary32 mapping the geometry of an
+ * admissible block to log2(rank + 1) of its ACA factorisation.  Features per
+ * pair (hodlr2d_pair_features): level/16, (ixY - ixX)/3, (iyY - iyX)/3,
+ * log2|X|/16, log2|Y|/16, min(a / box width, 4)/4, -log10(eps)/16, kind/8.
+ * Parameters: one flat vector W1 (8 x H row-major), b1, W2 (H x H), b2, w3,
+ * b3.  Training (forward, backward, Adam) runs on the GPU; loss is the mean
+ * squared error.  feats are n x 8 row-major binary32, targets and predictions
+ * n binary32; host or device pointers.  Every reduction runs in a fixed
+ * order, so results are reproducible bit for bit. */
+typedef struct hodlr2d_rank_model* hodlr2d_rank_model_t;
+/* params: NULL (zeros) or the initial flat vector (host or device). */
+int hodlr2d_rank_model_create(int hidden, const float* params, hodlr2d_rank_model_t* out);
+/* Current parameters (params may be NULL to query the count). */
+int hodlr2d_rank_model_params(hodlr2d_rank_model_t m, float* params, int64_t* nparams);
+/* Loss and its gradient (host outputs, either may be NULL) on one batch. */
+int hodlr2d_rank_model_loss_grad(hodlr2d_rank_model_t m, const float* feats,
+                                 const float* targets, int64_t n, float* loss,
+                                 float* grad);
+/* epochs passes of Adam over the data in the given order, mini-batches of
+ * batch rows, learning rate lr; *loss_out (may be NULL) = final loss. */
+int hodlr2d_rank_model_train(hodlr2d_rank_model_t m, const float* feats,
+                             const float* targets, int64_t n, int batch,
+                             int epochs, float lr, float* loss_out);
+int hodlr2d_rank_model_predict(hodlr2d_rank_model_t m, const float* feats,
+                               int64_t n, float* pred);
+void hodlr2d_rank_model_free(hodlr2d_rank_model_t m);
+/* Training data from a built handle: per stored pair (in hodlr2d_get_pairs
+ * order) its 8 features and log2(rank + 1).  feats / log2rank: host arrays of
+ * 8 * npairs / npairs floats, or NULL to query *npairs. */
+int hodlr2d_pair_features(hodlr2d_t h, int64_t* npairs, float* feats, float* log2rank);
 
 /* ----- product without any device allocation -----
  * The paper has no counterpart: this is a deployment aid.  hodlr2d_matvec may

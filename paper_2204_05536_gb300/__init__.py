@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib
 from ._lib import KINDS, MODES, HodlrError, check, load
 
-__all__ = ["HODLR2D", "kernel", "load", "HodlrError", "KINDS", "MODES"]
+__all__ = ["HODLR2D", "RankModel", "kernel", "load", "HodlrError", "KINDS", "MODES"]
 
 
 def kernel(kind: str, a: float = 0.0, diag: float | None = None) -> _lib.Kernel:
@@ -64,7 +64,7 @@ class HODLR2D:
 
     def __init__(self, points, k: _lib.Kernel, leaf_size: int, eps: float, root=None,
                  levels: int = -1, compress: bool = True, max_rank: int = 256,
-                 mode: str = "f64", stream=None):
+                 mode: str = "f64", stream=None, rank_model=None):
         lib = load()
         self._lib = lib
         opts = _lib.Opts()
@@ -76,6 +76,7 @@ class HODLR2D:
         opts.compress = int(bool(compress))
         opts.max_rank = int(max_rank)
         opts.mode = MODES[mode]
+        opts.rank_model = None if rank_model is None else rank_model.handle.value
         if _is_torch(points):
             pts = points.contiguous()
         else:
@@ -175,7 +176,20 @@ class HODLR2D:
             "near_entries": s.near_entries, "unconverged": s.unconverged,
             "compression_ratio": s.compression_ratio, "build_ms": list(s.build_ms),
             "bytes_per_matvec": dict(zip(MODES, list(s.bytes_per_matvec))),
+            "aca_fallbacks": s.aca_fallbacks, "aca_workspace_values": s.aca_workspace_values,
         }
+
+    def pair_features(self):
+        """(features npairs x 8 float32, log2(rank + 1) npairs float32) of the
+        stored pairs, in pairs() order: training data of the rank predictor."""
+        n = C.c_int64()
+        check(self._lib.hodlr2d_pair_features(self._h, C.byref(n), None, None),
+              "hodlr2d_pair_features")
+        f = np.zeros((max(n.value, 1), 8), dtype=np.float32)
+        r = np.zeros(max(n.value, 1), dtype=np.float32)
+        check(self._lib.hodlr2d_pair_features(self._h, C.byref(n), C.c_void_p(f.ctypes.data),
+                                              C.c_void_p(r.ctypes.data)), "hodlr2d_pair_features")
+        return f[: n.value], r[: n.value]
 
     def profile(self, enable: bool):
         check(self._lib.hodlr2d_profile(self._h, int(bool(enable))), "hodlr2d_profile")
@@ -225,3 +239,73 @@ class HODLR2D:
             self._h, C.byref(npairs), C.byref(nvals), C.c_void_p(info.ctypes.data),
             C.c_void_p(offs.ctypes.data), C.c_void_p(vals.ctypes.data)), "hodlr2d_export_factors")
         return info[: npairs.value], offs, vals[: nvals.value]
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, C.c_void_p(a.ctypes.data)
+
+
+class RankModel:
+    """Rank predictor network (hodlr2d_rank_model_*), trained on the GPU."""
+
+    def __init__(self, hidden: int = 64, params=None):
+        self._lib = load()
+        h = C.c_void_p()
+        keep = None
+        ptr = None
+        if params is not None:
+            keep, ptr = _f32(params)
+        check(self._lib.hodlr2d_rank_model_create(int(hidden), ptr, C.byref(h)),
+              "hodlr2d_rank_model_create")
+        self._h = h
+        self.hidden = hidden
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.hodlr2d_rank_model_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        n = C.c_int64()
+        check(self._lib.hodlr2d_rank_model_params(self._h, None, C.byref(n)), "params")
+        out = np.zeros(n.value, dtype=np.float32)
+        check(self._lib.hodlr2d_rank_model_params(self._h, C.c_void_p(out.ctypes.data),
+                                                  C.byref(n)), "params")
+        return out
+
+    def loss_grad(self, feats, targets):
+        f, fp = _f32(feats)
+        t, tp = _f32(targets)
+        n = C.c_int64()
+        self._lib.hodlr2d_rank_model_params(self._h, None, C.byref(n))
+        g = np.zeros(n.value, dtype=np.float32)
+        loss = C.c_float()
+        check(self._lib.hodlr2d_rank_model_loss_grad(self._h, fp, tp, len(t), C.byref(loss),
+                                                     C.c_void_p(g.ctypes.data)), "loss_grad")
+        return loss.value, g
+
+    def train(self, feats, targets, batch: int = 4096, epochs: int = 10, lr: float = 1e-3):
+        f, fp = _f32(feats)
+        t, tp = _f32(targets)
+        loss = C.c_float()
+        check(self._lib.hodlr2d_rank_model_train(self._h, fp, tp, len(t), int(batch),
+                                                 int(epochs), float(lr), C.byref(loss)), "train")
+        return loss.value
+
+    def predict(self, feats) -> np.ndarray:
+        f, fp = _f32(feats)
+        out = np.zeros(len(f), dtype=np.float32)
+        check(self._lib.hodlr2d_rank_model_predict(self._h, fp, len(f),
+                                                   C.c_void_p(out.ctypes.data)), "predict")
+        return out

@@ -33,7 +33,7 @@ class Kernel(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("root", C.c_double * 3), ("levels", C.c_int), ("compress", C.c_int),
-                ("max_rank", C.c_int), ("mode", C.c_int)]
+                ("max_rank", C.c_int), ("mode", C.c_int), ("rank_model", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -43,7 +43,8 @@ class Stats(C.Structure):
                 ("max_rank_per_level", C.c_int * MAX_LEVELS), ("max_rank", C.c_int),
                 ("far_values", C.c_int64), ("near_entries", C.c_int64),
                 ("unconverged", C.c_int64), ("compression_ratio", C.c_double),
-                ("build_ms", C.c_double * 4), ("bytes_per_matvec", C.c_int64 * 4)]
+                ("build_ms", C.c_double * 4), ("bytes_per_matvec", C.c_int64 * 4),
+                ("aca_fallbacks", C.c_int64), ("aca_workspace_values", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -71,6 +72,14 @@ SIGNATURES = {
     "hodlr2d_import_factors": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "hodlr2d_export_factors": (C.c_int, [_P, _i64p, _i64p, _P, _P, _P]),
     "hodlr2d_matvec_noalloc": (C.c_int, [_P, _P, _P, C.c_int]),
+    "hodlr2d_rank_model_create": (C.c_int, [C.c_int, _P, C.POINTER(_P)]),
+    "hodlr2d_rank_model_params": (C.c_int, [_P, _P, _i64p]),
+    "hodlr2d_rank_model_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(C.c_float), _P]),
+    "hodlr2d_rank_model_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, C.c_int, C.c_float,
+                                           C.POINTER(C.c_float)]),
+    "hodlr2d_rank_model_predict": (C.c_int, [_P, _P, C.c_int64, _P]),
+    "hodlr2d_rank_model_free": (None, [_P]),
+    "hodlr2d_pair_features": (C.c_int, [_P, _i64p, _P, _P]),
     "hodlr2d_free": (None, [_P]),
     "hodlr2d_strerror": (C.c_char_p, [C.c_int]),
 }

@@ -86,6 +86,8 @@ struct AcaArgs {
   uint8_t* flags;
   int32_t* rank;          // per level pair
   int32_t* conv;          // per level pair
+  const int64_t* plist;   // batch pair ids (fallback pass) or null: p0 + block
+  const int32_t* bcap;    // per batch pair rank cap (predicted) or null
 };
 
 template <int T>
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(T) k_aca(AcaArgs A) {
   double* s_dv = s_du + capmax + 1;  // V_q . v, q <= k
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  const int64_t p = A.p0 + blockIdx.x;
+  const int64_t p = A.plist ? A.plist[blockIdx.x] : A.p0 + blockIdx.x;
   const uint32_t bx = (uint32_t)A.px[p], by = (uint32_t)A.py[p];
   const int sh = 2 * (A.kappa - A.l);
   const int32_t xs = A.leaf_off[(int64_t)bx << sh];
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(T) k_aca(AcaArgs A) {
   const int32_t ys = A.leaf_off[(int64_t)by << sh];
   const int32_t n = A.leaf_off[(int64_t)(by + 1) << sh] - ys;
   const int kfull = min(m, n);
-  const int cap = min(kfull, capmax);
+  const int cap = A.bcap ? min(A.bcap[blockIdx.x], min(kfull, capmax)) : min(kfull, capmax);
   double* U = A.ws + A.wsoff[blockIdx.x];
   double* V = U + (int64_t)m * cap;
   uint8_t* used = A.flags + A.fgoff[blockIdx.x];
@@ -214,23 +216,27 @@ __global__ void __launch_bounds__(T) k_aca(AcaArgs A) {
   }
 }
 
-// copy U[:, :k] and V[:, :k] of each batch pair to the level's packed buffer
+// copy U[:, :k] and V[:, :k] of each batch pair (columns padded to even
+// length) to dst + dstoff[b]; dstoff < 0 skips the pair
 __global__ void k_compact(const double* __restrict__ ws, const int64_t* __restrict__ wsoff,
                           const int32_t* __restrict__ leaf_off, int kappa, int l,
                           const int32_t* __restrict__ px, const int32_t* __restrict__ py,
-                          int64_t p0, const int32_t* __restrict__ rank, int max_rank,
-                          const int64_t* __restrict__ foff, double* __restrict__ fac) {
-  const int64_t p = p0 + blockIdx.x;
+                          const int64_t* __restrict__ plist, const int32_t* __restrict__ rank,
+                          const int32_t* __restrict__ bcap, const int64_t* __restrict__ dstoff,
+                          double* __restrict__ dst) {
+  const int64_t doff = dstoff[blockIdx.x];
+  if (doff < 0) return;
+  const int64_t p = plist[blockIdx.x];
   const int sh = 2 * (kappa - l);
   const uint32_t bx = (uint32_t)px[p], by = (uint32_t)py[p];
   const int64_t m = leaf_off[(int64_t)(bx + 1) << sh] - leaf_off[(int64_t)bx << sh];
   const int64_t n = leaf_off[(int64_t)(by + 1) << sh] - leaf_off[(int64_t)by << sh];
-  const int64_t cap = min(min(m, n), (int64_t)max_rank);
+  const int64_t cap = bcap[blockIdx.x];
   const int64_t k = rank[p];
   const double* U = ws + wsoff[blockIdx.x];
   const double* V = U + m * cap;
   const int64_t lm = ldpad(m), ln = ldpad(n);
-  double* out = fac + foff[p];
+  double* out = dst + doff;
   for (int64_t t = threadIdx.x; t < lm * k; t += blockDim.x) {
     const int64_t q = t / lm, i = t - q * lm;
     out[t] = i < m ? U[q * m + i] : 0.0;
@@ -241,14 +247,56 @@ __global__ void k_compact(const double* __restrict__ ws, const int64_t* __restri
   }
 }
 
+// gather each pair's packed block from its staging place into the level
+// buffer, in pair order
+__global__ void k_pack_pairs(const double* const* __restrict__ src,
+                             const int64_t* __restrict__ cnt, const int64_t* __restrict__ foff,
+                             double* __restrict__ fac) {
+  const int64_t p = blockIdx.x;
+  const double* s = src[p];
+  double* d = fac + foff[p];
+  for (int64_t t = threadIdx.x; t < cnt[p]; t += blockDim.x) d[t] = s[t];
+}
+
+int mlp_predict_device(hodlr2d_rank_model* M, const float* d_feats, int64_t n, float* d_out,
+                       cudaStream_t s);
+
+// The 8 geometry features of a stored pair (X, Y) at level l: level, offset
+// of Y from X in box units, box sizes (log2), kernel parameter relative to
+// the box width, -log10(eps), kernel kind.  Inputs of the rank predictor.
+void pair_features(const hodlr2d* h, int l, int32_t bx, int32_t by, int64_t m, int64_t n,
+                   float* f) {
+  int ax, ay, cx, cy;
+  morton_decode((uint32_t)bx, ax, ay);
+  morton_decode((uint32_t)by, cx, cy);
+  const double wl = h->root[2] / (double)(1 << l);
+  f[0] = (float)l / 16.f;
+  f[1] = (float)(cx - ax) / 3.f;
+  f[2] = (float)(cy - ay) / 3.f;
+  f[3] = (float)(log2((double)std::max<int64_t>(m, 1)) / 16.0);
+  f[4] = (float)(log2((double)std::max<int64_t>(n, 1)) / 16.0);
+  f[5] = (float)(std::min(h->kp.a / wl, 4.0) / 4.0);
+  f[6] = (float)(-log10(h->eps) / 16.0);
+  f[7] = (float)h->kp.kind / 8.f;
+}
+
 // Compress every pair of every level; fills Level::{d_rank, d_foff, d_fac,
-// nvalues, max_rank, h_rank, h_foff} and the unconverged count.
+// nvalues, nstored, max_rank, h_rank, h_foff}, the unconverged count, and the
+// predictor statistics.
+//
+// With a rank model in the options, each pair's ACA runs with the cap the
+// model predicts (1.25 (2^y - 1) + 4, within min(|X|, |Y|, max_rank)): the
+// workspace is sized from the predictions.  A pair that reaches its
+// predicted cap without meeting eps is compressed again with the full cap
+// (plain adaptive ACA); the first terms are the same, so the factors equal
+// those of a build without the model.
 int aca_build(hodlr2d* h) {
   cudaStream_t s = h->stream;
   const int capmax = h->opts.max_rank;
   const size_t smem = sizeof(double) * (4 * (size_t)capmax + 2);
-  const int64_t ws_budget = (int64_t)1 << 28;  // values per batch (2 GiB)
-  int64_t unconverged = 0;
+  const int64_t ws_budget = (int64_t)1 << 28;  // workspace values per batch (2 GiB)
+  hodlr2d_rank_model* model = reinterpret_cast<hodlr2d_rank_model*>(h->opts.rank_model);
+  int64_t unconverged = 0, fallbacks = 0, ws_peak = 0;
   for (int l = h->kappa; l >= 1; --l) {  // Alg. 1: levels kappa down to 1
     Level& L = h->lev[l];
     const int64_t np = L.npairs;
@@ -258,6 +306,7 @@ int aca_build(hodlr2d* h) {
     L.h_foff.assign(np + 1, 0);
     if (np == 0) {
       H2D_CK(cudaMemsetAsync(L.d_foff, 0, sizeof(int64_t), s));
+      H2D_CK(cudaMalloc(&L.d_fac, sizeof(double)));
       continue;
     }
     std::vector<int32_t> px(np), py(np);
@@ -268,119 +317,179 @@ int aca_build(hodlr2d* h) {
     auto cnt = [&](int32_t b) {
       return (int64_t)h->h_leaf_off[(int64_t)(b + 1) << sh] - h->h_leaf_off[(int64_t)b << sh];
     };
-    std::vector<int64_t> wsz(np), fsz(np);
+    std::vector<int64_t> mm(np), nn(np);
+    std::vector<int32_t> full(np), capv(np);
     int64_t tot_rows = 0;
     for (int64_t p = 0; p < np; ++p) {
-      const int64_t m = cnt(px[p]), n = cnt(py[p]);
-      const int64_t cap = std::min<int64_t>(std::min(m, n), capmax);
-      wsz[p] = (m + n) * cap;
-      fsz[p] = m;
-      tot_rows += m + n;
+      mm[p] = cnt(px[p]);
+      nn[p] = cnt(py[p]);
+      full[p] = (int32_t)std::min<int64_t>(std::min(mm[p], nn[p]), capmax);
+      capv[p] = full[p];
+      tot_rows += mm[p] + nn[p];
+    }
+    if (model) {  // predicted caps
+      std::vector<float> feats(8 * np), pred(np);
+      for (int64_t p = 0; p < np; ++p)
+        pair_features(h, l, px[p], py[p], mm[p], nn[p], feats.data() + 8 * p);
+      float *d_f = nullptr, *d_p = nullptr;
+      H2D_CK(cudaMalloc(&d_f, 4 * 8 * np));
+      H2D_CK(cudaMalloc(&d_p, 4 * np));
+      H2D_CK(cudaMemcpy(d_f, feats.data(), 4 * 8 * np, cudaMemcpyHostToDevice));
+      H2D_TRY(mlp_predict_device(model, d_f, np, d_p, 0));
+      H2D_CK(cudaMemcpy(pred.data(), d_p, 4 * np, cudaMemcpyDeviceToHost));
+      cudaFree(d_f);
+      cudaFree(d_p);
+      for (int64_t p = 0; p < np; ++p) {
+        const double y = std::min<double>(std::max<double>(pred[p], 0.0), 20.0);
+        const int c = (int)ceil(1.25 * (exp2(y) - 1.0)) + 4;
+        capv[p] = std::max(1, std::min(full[p], c));
+      }
     }
     int32_t* d_conv = nullptr;
     H2D_CK(cudaMalloc(&d_conv, sizeof(int32_t) * np));
-    const int64_t mean_rows = tot_rows / (2 * np);
-    // packed level buffer, grown as batches finish
-    int64_t fac_cap = 0, fac_used = 0, stored = 0;
-    double* fac = nullptr;
-    int64_t p0 = 0;
-    while (p0 < np) {
-      int64_t p1 = p0, wtot = 0, ftot = 0;
-      while (p1 < np && (p1 == p0 || wtot + wsz[p1] <= ws_budget) && p1 - p0 < (1 << 20)) {
-        wtot += wsz[p1];
-        ftot += fsz[p1];
-        ++p1;
-      }
-      const int64_t nbp = p1 - p0;
-      std::vector<int64_t> wsoff(nbp), fgoff(nbp);
-      int64_t wo = 0, fo = 0;
-      for (int64_t p = p0; p < p1; ++p) {
-        wsoff[p - p0] = wo;
-        fgoff[p - p0] = fo;
-        wo += wsz[p];
-        fo += fsz[p];
-      }
-      double* d_ws = nullptr;
-      uint8_t* d_flags = nullptr;
-      int64_t *d_wsoff = nullptr, *d_fgoff = nullptr, *d_foff_b = nullptr;
-      H2D_CK(cudaMalloc(&d_ws, sizeof(double) * std::max<int64_t>(wo, 1)));
-      H2D_CK(cudaMalloc(&d_flags, std::max<int64_t>(fo, 1)));
-      H2D_CK(cudaMalloc(&d_wsoff, sizeof(int64_t) * nbp));
-      H2D_CK(cudaMalloc(&d_fgoff, sizeof(int64_t) * nbp));
-      H2D_CK(cudaMemcpyAsync(d_wsoff, wsoff.data(), sizeof(int64_t) * nbp,
-                             cudaMemcpyHostToDevice, s));
-      H2D_CK(cudaMemcpyAsync(d_fgoff, fgoff.data(), sizeof(int64_t) * nbp,
-                             cudaMemcpyHostToDevice, s));
-      AcaArgs A;
-      A.x = h->d_x;
-      A.y = h->d_y;
-      A.perm = h->d_perm;
-      A.leaf_off = h->d_leaf_off;
-      A.kappa = h->kappa;
-      A.l = l;
-      A.kp = h->kp;
-      A.eps = h->eps;
-      A.max_rank = capmax;
-      A.px = L.d_px;
-      A.py = L.d_py;
-      A.p0 = p0;
-      A.wsoff = d_wsoff;
-      A.fgoff = d_fgoff;
-      A.ws = d_ws;
-      A.flags = d_flags;
-      A.rank = L.d_rank;
-      A.conv = d_conv;
-      if (mean_rows <= 96)
-        k_aca<64><<<(unsigned)nbp, 64, smem, s>>>(A);
-      else
-        k_aca<256><<<(unsigned)nbp, 256, smem, s>>>(A);
-      H2D_CK(cudaGetLastError());
-      // ranks of the batch -> packed offsets
-      H2D_CK(cudaMemcpyAsync(L.h_rank.data() + p0, L.d_rank + p0, sizeof(int32_t) * nbp,
-                             cudaMemcpyDeviceToHost, s));
-      H2D_CK(cudaStreamSynchronize(s));
-      int64_t add = 0;
-      for (int64_t p = p0; p < p1; ++p) {
-        L.h_foff[p] = fac_used + add;
-        add += (ldpad(cnt(px[p])) + ldpad(cnt(py[p]))) * (int64_t)L.h_rank[p];
-        stored += (cnt(px[p]) + cnt(py[p])) * (int64_t)L.h_rank[p];
-      }
-      if (fac_used + add > fac_cap) {
-        const int64_t ncap = std::max<int64_t>(fac_used + add, 2 * fac_cap);
-        double* nf = nullptr;
-        H2D_CK(cudaMalloc(&nf, sizeof(double) * std::max<int64_t>(ncap, 1)));
-        if (fac_used > 0)
-          H2D_CK(cudaMemcpyAsync(nf, fac, sizeof(double) * fac_used, cudaMemcpyDeviceToDevice, s));
+    const int mean_rows = (int)(tot_rows / (2 * np));
+    // staging of finished pairs: (buffer, offset) per pair
+    std::vector<double*> stage_bufs;
+    std::vector<const double*> src_of(np, nullptr);
+    std::vector<int64_t> packed(np, 0);
+    std::vector<int32_t> conv(np, 0);
+    std::vector<int64_t> todo(np);
+    for (int64_t p = 0; p < np; ++p) todo[p] = p;
+    for (int pass = 0; pass < 2 && !todo.empty(); ++pass) {
+      const std::vector<int32_t>& caps = pass == 0 ? capv : full;
+      std::vector<int64_t> again;
+      size_t b0 = 0;
+      while (b0 < todo.size()) {
+        size_t b1 = b0;
+        int64_t wtot = 0;
+        while (b1 < todo.size() &&
+               (b1 == b0 || wtot + (mm[todo[b1]] + nn[todo[b1]]) * caps[todo[b1]] <= ws_budget) &&
+               b1 - b0 < (1u << 20)) {
+          wtot += (mm[todo[b1]] + nn[todo[b1]]) * caps[todo[b1]];
+          ++b1;
+        }
+        const int64_t nbp = (int64_t)(b1 - b0);
+        ws_peak = std::max(ws_peak, wtot);
+        std::vector<int64_t> plist(nbp), wsoff(nbp), fgoff(nbp);
+        std::vector<int32_t> bcap(nbp);
+        int64_t wo = 0, fo = 0;
+        for (int64_t i = 0; i < nbp; ++i) {
+          const int64_t p = todo[b0 + i];
+          plist[i] = p;
+          bcap[i] = caps[p];
+          wsoff[i] = wo;
+          fgoff[i] = fo;
+          wo += (mm[p] + nn[p]) * caps[p];
+          fo += mm[p];
+        }
+        double* d_ws = nullptr;
+        uint8_t* d_flags = nullptr;
+        int64_t *d_plist = nullptr, *d_wsoff = nullptr, *d_fgoff = nullptr, *d_dst = nullptr;
+        int32_t* d_bcap = nullptr;
+        H2D_CK(cudaMalloc(&d_ws, sizeof(double) * std::max<int64_t>(wo, 1)));
+        H2D_CK(cudaMalloc(&d_flags, std::max<int64_t>(fo, 1)));
+        H2D_CK(cudaMalloc(&d_plist, sizeof(int64_t) * nbp));
+        H2D_CK(cudaMalloc(&d_wsoff, sizeof(int64_t) * nbp));
+        H2D_CK(cudaMalloc(&d_fgoff, sizeof(int64_t) * nbp));
+        H2D_CK(cudaMalloc(&d_dst, sizeof(int64_t) * nbp));
+        H2D_CK(cudaMalloc(&d_bcap, sizeof(int32_t) * nbp));
+        H2D_CK(cudaMemcpyAsync(d_plist, plist.data(), 8 * nbp, cudaMemcpyHostToDevice, s));
+        H2D_CK(cudaMemcpyAsync(d_wsoff, wsoff.data(), 8 * nbp, cudaMemcpyHostToDevice, s));
+        H2D_CK(cudaMemcpyAsync(d_fgoff, fgoff.data(), 8 * nbp, cudaMemcpyHostToDevice, s));
+        H2D_CK(cudaMemcpyAsync(d_bcap, bcap.data(), 4 * nbp, cudaMemcpyHostToDevice, s));
+        AcaArgs A;
+        A.x = h->d_x;
+        A.y = h->d_y;
+        A.perm = h->d_perm;
+        A.leaf_off = h->d_leaf_off;
+        A.kappa = h->kappa;
+        A.l = l;
+        A.kp = h->kp;
+        A.eps = h->eps;
+        A.max_rank = capmax;
+        A.px = L.d_px;
+        A.py = L.d_py;
+        A.p0 = 0;
+        A.wsoff = d_wsoff;
+        A.fgoff = d_fgoff;
+        A.ws = d_ws;
+        A.flags = d_flags;
+        A.rank = L.d_rank;
+        A.conv = d_conv;
+        A.plist = d_plist;
+        A.bcap = d_bcap;
+        if (mean_rows <= 96)
+          k_aca<64><<<(unsigned)nbp, 64, smem, s>>>(A);
+        else
+          k_aca<256><<<(unsigned)nbp, 256, smem, s>>>(A);
+        H2D_CK(cudaGetLastError());
+        std::vector<int32_t> rk(np), cv(np);
+        H2D_CK(cudaMemcpyAsync(rk.data(), L.d_rank, 4 * np, cudaMemcpyDeviceToHost, s));
+        H2D_CK(cudaMemcpyAsync(cv.data(), d_conv, 4 * np, cudaMemcpyDeviceToHost, s));
         H2D_CK(cudaStreamSynchronize(s));
-        cudaFree(fac);
-        fac = nf;
-        fac_cap = ncap;
+        // finished pairs go to a staging buffer; capped ones are redone
+        std::vector<int64_t> dst(nbp, -1);
+        int64_t so = 0;
+        for (int64_t i = 0; i < nbp; ++i) {
+          const int64_t p = plist[i];
+          L.h_rank[p] = rk[p];
+          conv[p] = cv[p];
+          if (pass == 0 && !cv[p] && rk[p] == caps[p] && caps[p] < full[p]) {
+            again.push_back(p);
+            continue;
+          }
+          dst[i] = so;
+          packed[p] = (ldpad(mm[p]) + ldpad(nn[p])) * (int64_t)rk[p];
+          so += packed[p];
+        }
+        double* sb = nullptr;
+        H2D_CK(cudaMalloc(&sb, sizeof(double) * std::max<int64_t>(so, 1)));
+        stage_bufs.push_back(sb);
+        for (int64_t i = 0; i < nbp; ++i)
+          if (dst[i] >= 0) src_of[plist[i]] = sb + dst[i];
+        H2D_CK(cudaMemcpyAsync(d_dst, dst.data(), 8 * nbp, cudaMemcpyHostToDevice, s));
+        k_compact<<<(unsigned)nbp, 256, 0, s>>>(d_ws, d_wsoff, h->d_leaf_off, h->kappa, l, L.d_px,
+                                                L.d_py, d_plist, L.d_rank, d_bcap, d_dst, sb);
+        H2D_CK(cudaGetLastError());
+        H2D_CK(cudaStreamSynchronize(s));
+        cudaFree(d_ws);
+        cudaFree(d_flags);
+        cudaFree(d_plist);
+        cudaFree(d_wsoff);
+        cudaFree(d_fgoff);
+        cudaFree(d_dst);
+        cudaFree(d_bcap);
+        b0 = b1;
       }
-      H2D_CK(cudaMalloc(&d_foff_b, sizeof(int64_t) * np));
-      H2D_CK(cudaMemcpyAsync(d_foff_b, L.h_foff.data(), sizeof(int64_t) * p1,
-                             cudaMemcpyHostToDevice, s));
-      k_compact<<<(unsigned)nbp, 256, 0, s>>>(d_ws, d_wsoff, h->d_leaf_off, h->kappa, l, L.d_px,
-                                              L.d_py, p0, L.d_rank, capmax, d_foff_b, fac);
+      if (pass == 0) fallbacks += (int64_t)again.size();
+      todo.swap(again);
+    }
+    // pack in pair order
+    int64_t tot = 0, stored = 0;
+    for (int64_t p = 0; p < np; ++p) {
+      L.h_foff[p] = tot;
+      tot += packed[p];
+      stored += (mm[p] + nn[p]) * (int64_t)L.h_rank[p];
+    }
+    L.h_foff[np] = tot;
+    L.nvalues = tot;
+    L.nstored = stored;
+    H2D_CK(cudaMalloc(&L.d_fac, sizeof(double) * std::max<int64_t>(tot, 1)));
+    H2D_CK(cudaMemcpy(L.d_foff, L.h_foff.data(), sizeof(int64_t) * (np + 1), cudaMemcpyHostToDevice));
+    {
+      const double** d_src = nullptr;
+      int64_t* d_cnt = nullptr;
+      H2D_CK(cudaMalloc(&d_src, sizeof(double*) * np));
+      H2D_CK(cudaMalloc(&d_cnt, sizeof(int64_t) * np));
+      H2D_CK(cudaMemcpy(d_src, src_of.data(), sizeof(double*) * np, cudaMemcpyHostToDevice));
+      H2D_CK(cudaMemcpy(d_cnt, packed.data(), sizeof(int64_t) * np, cudaMemcpyHostToDevice));
+      k_pack_pairs<<<(unsigned)np, 256, 0, s>>>(d_src, d_cnt, L.d_foff, L.d_fac);
       H2D_CK(cudaGetLastError());
       H2D_CK(cudaStreamSynchronize(s));
-      fac_used += add;
-      cudaFree(d_ws);
-      cudaFree(d_flags);
-      cudaFree(d_wsoff);
-      cudaFree(d_fgoff);
-      cudaFree(d_foff_b);
-      p0 = p1;
+      cudaFree(d_src);
+      cudaFree(d_cnt);
     }
-    L.h_foff[np] = fac_used;
-    L.nvalues = fac_used;
-    L.nstored = stored;
-    L.d_fac = fac;
-    if (!L.d_fac) H2D_CK(cudaMalloc(&L.d_fac, sizeof(double)));
-    H2D_CK(cudaMemcpyAsync(L.d_foff, L.h_foff.data(), sizeof(int64_t) * (np + 1),
-                           cudaMemcpyHostToDevice, s));
-    std::vector<int32_t> conv(np);
-    H2D_CK(cudaMemcpyAsync(conv.data(), d_conv, sizeof(int32_t) * np, cudaMemcpyDeviceToHost, s));
-    H2D_CK(cudaStreamSynchronize(s));
+    for (double* b : stage_bufs) cudaFree(b);
     cudaFree(d_conv);
     L.max_rank = 0;
     for (int64_t p = 0; p < np; ++p) {
@@ -389,6 +498,8 @@ int aca_build(hodlr2d* h) {
     }
   }
   h->st.unconverged = unconverged;
+  h->st.aca_fallbacks = fallbacks;
+  h->st.aca_workspace_values = ws_peak;
   return HODLR2D_OK;
 }
 

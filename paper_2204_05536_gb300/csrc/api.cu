@@ -21,6 +21,8 @@ int prepare_mode(hodlr2d* h, int mode);
 void free_modes(hodlr2d* h);
 int gmres_run(hodlr2d* h, const double* b, double* x, double tol, int restart, int maxit,
               int inner_mode, int* iters, double* relres);
+void pair_features(const hodlr2d* h, int l, int32_t bx, int32_t by, int64_t m, int64_t n,
+                   float* f);
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -159,6 +161,7 @@ extern "C" {
 void hodlr2d_default_opts(hodlr2d_opts* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
+  o->rank_model = nullptr;
   o->root[0] = o->root[1] = o->root[2] = 0.0;
   o->levels = -1;
   o->compress = 1;
@@ -318,6 +321,33 @@ int hodlr2d_gmres_ex(hodlr2d_t h, const double* b, double* x, double tol, int re
 int hodlr2d_get_stats(hodlr2d_t h, hodlr2d_stats* s) {
   if (!h || !s) return HODLR2D_ERR_ARG;
   *s = h->st;
+  return HODLR2D_OK;
+}
+
+int hodlr2d_pair_features(hodlr2d_t h, int64_t* npairs, float* feats, float* log2rank) {
+  if (!h || !npairs) return HODLR2D_ERR_ARG;
+  int64_t tot = 0;
+  for (int l = 1; l <= h->kappa; ++l) tot += h->lev[l].npairs;
+  *npairs = tot;
+  if (!feats && !log2rank) return HODLR2D_OK;
+  if (!h->has_factors) return HODLR2D_ERR_STATE;
+  DeviceGuard g(h->device);
+  int64_t o = 0;
+  for (int l = 1; l <= h->kappa; ++l) {
+    const Level& L = h->lev[l];
+    const int64_t np = L.npairs;
+    if (!np) continue;
+    std::vector<int32_t> px(np), py(np);
+    H2D_CK(cudaMemcpy(px.data(), L.d_px, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
+    H2D_CK(cudaMemcpy(py.data(), L.d_py, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
+    const int sh = 2 * (h->kappa - l);
+    for (int64_t p = 0; p < np; ++p, ++o) {
+      const int64_t m = h->h_leaf_off[(int64_t)(px[p] + 1) << sh] - h->h_leaf_off[(int64_t)px[p] << sh];
+      const int64_t n = h->h_leaf_off[(int64_t)(py[p] + 1) << sh] - h->h_leaf_off[(int64_t)py[p] << sh];
+      if (feats) pair_features(h, l, px[p], py[p], m, n, feats + 8 * o);
+      if (log2rank) log2rank[o] = (float)log2(1.0 + (double)L.h_rank[p]);
+    }
+  }
   return HODLR2D_OK;
 }
 

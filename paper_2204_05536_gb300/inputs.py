@@ -58,3 +58,14 @@ def point_sets(count: int, seed: int = 0, nmin: int = 2048, nmax: int = 65536):
         p = rng.uniform(-0.5, 0.5, (n, 2)) * np.array([wx, wy]) + c
         sets.append(p)
     return sets
+
+
+def mlp_init(hidden: int = 64, seed: int = 0, nfeat: int = 8) -> np.ndarray:
+    """He-normal initial parameters of the rank-predictor MLP as one flat
+    float32 vector (W1, b1, W2, b2, w3, b3; biases zero)."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((nfeat, hidden)) * np.sqrt(2.0 / nfeat)
+    W2 = rng.standard_normal((hidden, hidden)) * np.sqrt(2.0 / hidden)
+    w3 = rng.standard_normal(hidden) * np.sqrt(2.0 / hidden)
+    return np.concatenate([W1.ravel(), np.zeros(hidden), W2.ravel(), np.zeros(hidden), w3,
+                           [0.0]]).astype(np.float32)
