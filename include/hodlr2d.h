@@ -249,6 +249,22 @@ void hodlr2d_rank_model_free(hodlr2d_rank_model_t m);
  * 8 * npairs / npairs floats, or NULL to query *npairs. */
 int hodlr2d_pair_features(hodlr2d_t h, int64_t* npairs, float* feats, float* log2rank);
 
+/* ----- many independent matrices (point sets of uneven size) -----
+ * Not in the paper (deployment batching).  A batch multiplies all its handles
+ * with one CUDA graph launch: the first hodlr2d_batch_matvec (and any call
+ * whose pointers, nrhs or mode differ from the recorded ones) runs the
+ * products once, then records them into a graph (sets spread over eight
+ * forked streams); later calls replay that graph on the batch's stream.
+ * The handles must outlive the batch and must not be used concurrently with
+ * it.  x[i], y[i]: device pointers, n_i x nrhs[i] column-major.  Profiling
+ * (hodlr2d_profile) must be off on every handle.  Errors: ARG, STATE, CUDA. */
+typedef struct hodlr2d_batch* hodlr2d_batch_t;
+int hodlr2d_batch_create(const hodlr2d_t* handles, int count, hodlr2d_batch_t* out);
+int hodlr2d_batch_set_stream(hodlr2d_batch_t b, void* stream);
+int hodlr2d_batch_matvec(hodlr2d_batch_t b, const double* const* x, double* const* y,
+                         const int* nrhs, int mode);
+void hodlr2d_batch_free(hodlr2d_batch_t b);
+
 /* ----- product without any device allocation -----
  * The paper has no counterpart: this is a deployment aid.  hodlr2d_matvec may
  * allocate its working memory on first use (and again when nrhs grows).  Some

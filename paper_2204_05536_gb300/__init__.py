@@ -15,7 +15,8 @@ import numpy as np
 from . import _lib
 from ._lib import KINDS, MODES, HodlrError, check, load
 
-__all__ = ["HODLR2D", "RankModel", "kernel", "load", "HodlrError", "KINDS", "MODES"]
+__all__ = ["HODLR2D", "RankModel", "Batch", "autotune_leaf", "kernel", "load", "HodlrError",
+           "KINDS", "MODES"]
 
 
 def kernel(kind: str, a: float = 0.0, diag: float | None = None) -> _lib.Kernel:
@@ -309,3 +310,71 @@ class RankModel:
         check(self._lib.hodlr2d_rank_model_predict(self._h, fp, len(f),
                                                    C.c_void_p(out.ctypes.data)), "predict")
         return out
+
+
+class Batch:
+    """Independent HODLR2D matrices multiplied with one CUDA graph launch
+    (hodlr2d_batch_*).  Keeps the handles alive."""
+
+    def __init__(self, matrices, stream=None):
+        self._lib = load()
+        self.mats = list(matrices)
+        arr = (C.c_void_p * len(self.mats))(*[m.handle.value for m in self.mats])
+        h = C.c_void_p()
+        check(self._lib.hodlr2d_batch_create(arr, len(self.mats), C.byref(h)),
+              "hodlr2d_batch_create")
+        self._h = h
+        if stream is not None:
+            s = getattr(stream, "cuda_stream", stream)
+            check(self._lib.hodlr2d_batch_set_stream(self._h, C.c_void_p(int(s))),
+                  "hodlr2d_batch_set_stream")
+
+    def matvec(self, xs, ys, mode: str = "f64"):
+        """xs[i], ys[i]: float64 CUDA tensors holding n_i x nrhs_i column-major
+        data (shape (nrhs_i, n_i) contiguous, or (n_i,))."""
+        n = len(self.mats)
+        xa = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        ya = (C.c_void_p * n)(*[y.data_ptr() for y in ys])
+        nr = (C.c_int * n)(*[1 if x.dim() == 1 else x.shape[0] for x in xs])
+        check(self._lib.hodlr2d_batch_matvec(self._h, xa, ya, nr, MODES[mode]),
+              "hodlr2d_batch_matvec")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.hodlr2d_batch_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_leaf(points, k, eps, candidates=(32, 64, 128), nrhs: int = 1, mode: str = "f64",
+                  reps: int = 5, root=None):
+    """Leaf size (N_max of Alg. 1) with the fastest product for this point set:
+    builds the matrix for every candidate, times reps products with CUDA
+    events, and returns (best leaf, {leaf: ms})."""
+    import torch
+    times = {}
+    n = len(points)
+    x = torch.ones((nrhs, n), dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    for leaf in candidates:
+        g = HODLR2D(points, k, leaf, eps, root=root)
+        if mode != "f64":
+            g.prepare(mode)
+        g.set_stream(torch.cuda.current_stream())
+        g.matvec(x.t() if nrhs > 1 else x[0], mode=mode)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            g.matvec(x.t() if nrhs > 1 else x[0], mode=mode)
+        e1.record()
+        torch.cuda.synchronize()
+        times[leaf] = e0.elapsed_time(e1) / reps
+        g.close()
+    best = min(times, key=times.get)
+    return best, times

@@ -80,6 +80,10 @@ SIGNATURES = {
     "hodlr2d_rank_model_predict": (C.c_int, [_P, _P, C.c_int64, _P]),
     "hodlr2d_rank_model_free": (None, [_P]),
     "hodlr2d_pair_features": (C.c_int, [_P, _i64p, _P, _P]),
+    "hodlr2d_batch_create": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
+    "hodlr2d_batch_set_stream": (C.c_int, [_P, _P]),
+    "hodlr2d_batch_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+    "hodlr2d_batch_free": (None, [_P]),
     "hodlr2d_free": (None, [_P]),
     "hodlr2d_strerror": (C.c_char_p, [C.c_int]),
 }
