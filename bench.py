@@ -49,6 +49,9 @@ def parse():
                    help="product modes to time; the first is the headline")
     p.add_argument("--n", type=int, default=N_FULL, help="points (smaller for quick checks)")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    p.add_argument("--n-learned", type=int, default=1 << 22,
+                   help="points of the learned-rank build (log r kernel)")
     return p.parse_args()
 
 
@@ -184,6 +187,218 @@ def cpu_baseline_leg(rows, x, pts, n):
             "kappa_sample": o.kappa, "t_rows_s": t_rows, "y_direct_rows": yd}
 
 
+def timed(g, x, y, mode, steps, warmup, stream):
+    """steps products after warmup ones; ms per product (CUDA events)."""
+    import torch
+    for _ in range(warmup):
+        g.matvec(x, mode=mode, out=y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.matvec(x, mode=mode, out=y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def events(stream):
+    import torch
+    return (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+
+def extra_gmres_nrhs(pkg, inputs, n, stream):
+    """RBF interpolation system of Eq. ker with the headline points and MQ
+    kernel, beta = N on the diagonal (Sec. 5.1): GMRES(50) to a 1e-8 relative
+    residual with the F64 product, and FP64 iterative refinement around
+    binary32 / bfloat16 / float-float inner solves; then one product of 32
+    right-hand sides per mode."""
+    import torch
+    g = pkg.HODLR2D(inputs.uniform(n, seed=0), pkg.kernel("mq", 1.0 / np.sqrt(n), diag=float(n)),
+                    LEAF, EPS, root=ROOT_BOX)
+    g.set_stream(stream)
+    lam = torch.from_numpy(inputs.rhs(n, seed=2)).cuda()
+    f = g.matvec(lam, mode="f64")
+    gm = {}
+    for mode in ("f64", "f32", "bf16", "df32"):
+        if mode != "f64":
+            g.prepare(mode)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xs, it, rr, code = g.gmres(f, tol=1e-8, restart=50, maxit=2000, inner_mode=mode)
+        torch.cuda.synchronize()
+        r = f - g.matvec(xs, mode="f64")
+        gm[mode] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "products": it,
+                    "relres_reported": rr, "relres_f64": float(torch.linalg.norm(r)
+                                                               / torch.linalg.norm(f)),
+                    "converged": code == 0,
+                    "rel_err_lambda": float(torch.linalg.norm(xs - lam) / torch.linalg.norm(lam))}
+    nr = 32
+    Xc = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n, nr, seed=3).T)).cuda()  # nrhs x n
+    Yc = torch.empty_like(Xc)
+    Y64 = torch.empty_like(Xc)
+    g.matvec(Xc.t(), mode="f64", out=Y64)
+    mr = {}
+    for mode in ("f64", "df32", "f32", "bf16"):
+        for _ in range(2):
+            g.matvec(Xc.t(), mode=mode, out=Yc)
+        torch.cuda.synchronize()
+        e0, e1 = events(stream)
+        e0.record(stream)
+        for _ in range(3):
+            g.matvec(Xc.t(), mode=mode, out=Yc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        mr[mode] = {"ms": round(ms, 3), "products_per_s": round(nr / (ms * 1e-3), 1),
+                    "rel2_vs_f64": float(torch.linalg.norm(Yc - Y64) / torch.linalg.norm(Y64))}
+    g.close()
+    return {"gmres_mq_beta_n": gm, "nrhs32": mr}
+
+
+def extra_batch(pkg, inputs, stream, count=256):
+    """Independent point sets (sizes log-uniform in [2048, 65536], rectangles of
+    aspect ratio up to 4), IMQ a = 1/sqrt(n_i), binary32 factors, 1-8
+    right-hand sides each, all products replayed as one CUDA graph.  The leaf
+    size is tuned per size class (four log-spaced classes) on one member."""
+    import torch
+    sets = inputs.point_sets(count, seed=0)
+    sizes = np.array([len(p) for p in sets])
+    edges = np.exp(np.linspace(np.log(2048), np.log(65536), 5))
+    cls = np.clip(np.searchsorted(edges, sizes, side="right") - 1, 0, 3)
+    t0 = time.perf_counter()
+    leaf_of = {}
+    for c in range(4):
+        members = np.nonzero(cls == c)[0]
+        if len(members) == 0:
+            continue
+        i = int(members[len(members) // 2])
+        best, _ = pkg.autotune_leaf(sets[i], pkg.kernel("imq", 1.0 / np.sqrt(sizes[i])), EPS,
+                                    candidates=(32, 64, 128), nrhs=4, mode="f32", reps=3)
+        leaf_of[c] = best
+    t_tune = time.perf_counter() - t0
+    rng = np.random.default_rng(5)
+    mats, xs, ys = [], [], []
+    t0 = time.perf_counter()
+    for p, c in zip(sets, cls):
+        m = pkg.HODLR2D(p, pkg.kernel("imq", 1.0 / np.sqrt(len(p))), leaf_of[int(c)], EPS)
+        m.prepare("f32")
+        mats.append(m)
+        r = int(rng.integers(1, 9))
+        xs.append(torch.from_numpy(rng.standard_normal((r, len(p)))).cuda())
+        ys.append(torch.empty_like(xs[-1]))
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    nprod = int(sum(x.shape[0] for x in xs))
+    b = pkg.Batch(mats, stream=stream)
+    b.matvec(xs, ys, mode="f32")  # records the graph
+    torch.cuda.synchronize()
+    e0, e1 = events(stream)
+    e0.record(stream)
+    for _ in range(5):
+        b.matvec(xs, ys, mode="f32")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / 5
+    for m in mats:
+        m.set_stream(stream)
+    ys2 = [torch.empty_like(y) for y in ys]
+    e0.record(stream)
+    for _ in range(5):
+        for m, x, y in zip(mats, xs, ys2):
+            m.matvec(x.t(), mode="f32", out=y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 5
+    same = all(bool(torch.equal(y, y2)) for y, y2 in zip(ys, ys2))
+    y64 = [m.matvec(x.t(), mode="f64") for m, x in zip(mats[:8], xs[:8])]
+    err = max(float(torch.linalg.norm(y.t() - z) / torch.linalg.norm(z))
+              for y, z in zip(ys[:8], y64))
+    b.close()
+    for m in mats:
+        m.close()
+    return {"sets": count, "points": int(sizes.sum()), "products": nprod,
+            "leaf_per_class": {str(int(round(edges[c]))): v for c, v in leaf_of.items()},
+            "graph_ms": round(t_graph, 3), "sequential_launches_ms": round(t_seq, 3),
+            "products_per_s_graph": round(nprod / (t_graph * 1e-3), 1),
+            "graph_equals_sequential": same, "rel2_f32_vs_f64_first8": err,
+            "tune_s": round(t_tune, 2), "build_s": round(t_build, 2)}
+
+
+def extra_learned(pkg, inputs, stream, n_big):
+    """Rank predictor trained on the GPU on the ACA ranks of log r builds at
+    N = 2^16, 2^18, 2^20 (eps 1e-8), then used in an N = n_big build: build
+    time, ACA workspace and fallbacks against the plain adaptive build; then
+    a 16-RHS binary32 product of the result."""
+    import torch
+    feats, targets = [], []
+    for nn in (1 << 16, 1 << 18, 1 << 20):
+        gg = pkg.HODLR2D(inputs.uniform(nn, seed=nn), pkg.kernel("log"), LEAF, EPS, root=ROOT_BOX)
+        f_, r_ = gg.pair_features()
+        feats.append(f_)
+        targets.append(r_)
+        gg.close()
+    F = np.concatenate(feats)
+    T = np.concatenate(targets)
+    perm = np.random.default_rng(0).permutation(len(T))
+    model = pkg.RankModel(64, inputs.mlp_init(64, seed=1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = model.train(F[perm], T[perm], batch=1024, epochs=30, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    pts = inputs.uniform(n_big, seed=0)
+    res = {"train": {"pairs": int(len(T)), "final_mse_log2rank": loss,
+                     "train_s": round(t_train, 2)}}
+    Xc = torch.from_numpy(np.ascontiguousarray(inputs.rhs(n_big, 16, seed=3).T)).cuda()
+    ys = {}
+    for name, mdl in (("plain", None), ("learned", model)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gg = pkg.HODLR2D(pts, pkg.kernel("log"), LEAF, EPS, root=ROOT_BOX, rank_model=mdl)
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - t0
+        st = gg.stats()
+        gg.set_stream(stream)
+        gg.prepare("f32")
+        Y = torch.empty_like(Xc)
+        for _ in range(2):
+            gg.matvec(Xc.t(), mode="f32", out=Y)
+        torch.cuda.synchronize()
+        e0, e1 = events(stream)
+        e0.record(stream)
+        for _ in range(3):
+            gg.matvec(Xc.t(), mode="f32", out=Y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ys[name] = Y
+        res[name] = {"build_ms": round(t_b * 1e3, 1), "aca_ms": round(st["build_ms"][2], 1),
+                     "aca_workspace_gb": round(st["aca_workspace_values"] * 8 / 1e9, 3),
+                     "fallbacks": st["aca_fallbacks"], "npairs": st["npairs"],
+                     "far_values": st["far_values"], "max_rank": st["max_rank"],
+                     "f32_nrhs16_ms": round(e0.elapsed_time(e1) / 3, 3)}
+        gg.close()
+    res["products_identical"] = bool(torch.equal(ys["plain"], ys["learned"]))
+    res["n"] = n_big
+    model.close()
+    return res
+
+
+def extras(pkg, inputs, n, n_learned):
+    """Secondary measurements on one GPU (each section timed on its own)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, fn in (("rbf_system", lambda: extra_gmres_nrhs(pkg, inputs, n, stream)),
+                     ("batch_point_sets", lambda: extra_batch(pkg, inputs, stream)),
+                     ("learned_rank_log", lambda: extra_learned(pkg, inputs, stream, n_learned))):
+        t0 = time.perf_counter()
+        out[name] = fn()
+        out[name]["section_s"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_2204_05536_gb300 as pkg
@@ -209,34 +424,25 @@ def run_ours(args, ws, rank, local):
     for mode in modes:
         if mode != "f64":
             g.prepare(mode)
-        for _ in range(args.warmup):
-            g.matvec(x, mode=mode, out=y)
-        torch.cuda.synchronize()
         barrier(ws)
         torch.cuda.synchronize()
         clocks = ClockSampler(local)
         clocks.start()
+        ms = timed(g, x, y, mode, args.steps, args.warmup, stream)
+        clk = clocks.stop()
+        barrier(ws)
+        # second pass with per-phase events (kernels serialized)
         g.profile(True)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
         for _ in range(args.steps):
             g.matvec(x, mode=mode, out=y)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier(ws)
         prof = g.get_profile()
         g.profile(False)
-        clk = clocks.stop()
-        ms_total = e0.elapsed_time(e1)
-        per_mode[mode] = {"ms": max_over_ranks(ms_total / args.steps, ws), "prof": prof,
-                          "clocks": clk, "y_rows": None}
-        per_mode[mode]["y"] = y.clone()
+        per_mode[mode] = {"ms": max_over_ranks(ms, ws), "prof": prof, "clocks": clk,
+                          "y": y.clone()}
     mode = modes[0]
     ms_step = per_mode[mode]["ms"]
     prof = per_mode[mode]["prof"]
     clk = per_mode[mode]["clocks"]
-    y = per_mode[mode]["y"]
 
     # end to end through the public API with pinned host buffers
     xp = torch.from_numpy(x_h).pin_memory()
@@ -251,15 +457,16 @@ def run_ours(args, ws, rank, local):
         g.matvec(xnp, mode=mode, out=ynp)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     e2e_ms = max_over_ranks(e2e_ms, ws)
+    g.set_stream(stream)
 
-    # dominant kernel and its roofline
+    # dominant kernel (serialized per-phase times) and its roofline
     peak, peak_src = peaks()
     dom = max((k for k in prof if prof[k]["launches"]), key=lambda k: prof[k]["ms"])
     d = prof[dom]
-    per_launch_ms = d["ms"] / d["launches"]
+    # one product runs the phase's kernel(s) once; bytes are per product
+    per_launch_ms = d["ms"] / args.steps
     achieved = d["bytes"] / (per_launch_ms * 1e-3) / 1e9
-    launches = sum(v["launches"] for v in prof.values())
-    # whole-product algorithmic bytes against the product time
+    launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
     alg_bytes = st["bytes_per_matvec"][mode]
     hbm_frac_product = alg_bytes / (ms_step * 1e-3) / 1e9 / peak
 
@@ -283,12 +490,14 @@ def run_ours(args, ws, rank, local):
                          % (st["far_values"] * 8 / 1e9)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "peak_source": peak_src,
+                     "peak_source": peak_src, "bytes_per_launch": d["bytes"],
+                     "ms_per_launch": round(per_launch_ms, 4),
+                     "launches_per_product": d["launches"] // args.steps,
                      "traffic": NCU_TRAFFIC.get((dom, mode, n))},
         "hbm_frac_product": round(hbm_frac_product, 4),
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
-        "gpu_launches": launches,
+        "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
         "t_build_ms": round(t_build, 1),
         "build_phase_ms": [round(v, 1) for v in st["build_ms"]],
@@ -298,13 +507,14 @@ def run_ours(args, ws, rank, local):
                   "compression_ratio": st["compression_ratio"],
                   "max_rank_per_level": st["max_rank_per_level"],
                   "values_per_level": st["values_per_level"]},
-        "phases_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items()
-                               if v["launches"]},
+        "phases_ms_serialized": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items()
+                                 if v["launches"]},
         "modes": {m: {"ms": round(v["ms"], 4),
                       "hbm_frac_product": round(st["bytes_per_matvec"][m] / (v["ms"] * 1e-3)
                                                 / 1e9 / peak, 4),
-                      "phases_ms": {k: round(p["ms"] / args.steps, 4)
-                                    for k, p in v["prof"].items() if p["launches"]}}
+                      "clocks_sm_mhz": v["clocks"].get("sm_mhz"),
+                      "phases_ms_serialized": {k: round(p["ms"] / args.steps, 4)
+                                               for k, p in v["prof"].items() if p["launches"]}}
                   for m, v in per_mode.items()},
     }
     if rank == 0 and not args.no_cpu:
@@ -330,6 +540,11 @@ def run_ours(args, ws, rank, local):
                 errs[m]["rel2_vs_f64_product"] = float(torch.linalg.norm(v["y"] - y64)
                                                        / torch.linalg.norm(y64))
         out["error_vs_direct"] = errs
+    for v in per_mode.values():
+        del v["y"]
+    g.close()
+    if ws == 1 and not args.no_extras:
+        out["extras"] = extras(pkg, inputs, n, args.n_learned)
     return out
 
 

@@ -179,16 +179,19 @@ typedef struct {
 int hodlr2d_get_stats(hodlr2d_t h, hodlr2d_stats* s);
 
 /* ----- tracing: per-phase device time of the product -----
- * Phases of one product: 0 gather x, 1 near field, 2 far-field projection
- * (coarse levels), 3 projection sums, 4 far-field expansion (coarse levels),
- * 5 combine and scatter y, 6 single-read far field, one block per pair
- * (mid levels), 7 single-read far field, one warp per box (finest levels).  While enabled, each phase's launches are
- * bracketed by CUDA events on the handle's stream.  hodlr2d_profile(h, 1)
- * resets and starts recording, (h, 0) stops.  hodlr2d_get_profile
- * synchronises the stream and returns, per phase, the summed milliseconds,
- * the number of kernel launches, and the algorithmic bytes one launch moves
- * (arrays of HODLR2D_NPHASE entries; any may be NULL). */
-#define HODLR2D_NPHASE 8
+ * Phases of one product (one kernel each): 0 gather x, 1 near field,
+ * 2 far-field projection (coarse levels), 3 projection sums, 4 far-field
+ * expansion (coarse levels), 5 combine and scatter y, 6 single-read far
+ * field, one block per pair (mid levels), 7 single-read far field, one warp
+ * per box (finest levels), 8 as 6 for smaller boxes, 9 unused.  While
+ * enabled, each phase is bracketed by CUDA events and the product runs on the
+ * handle's stream alone (no side streams), so each time is that of its
+ * kernel running by itself.  hodlr2d_profile(h, 1) resets and starts
+ * recording, (h, 0) stops.  hodlr2d_get_profile synchronises the stream and
+ * returns, per phase, the summed milliseconds, the number of kernel launches,
+ * and the algorithmic bytes one launch moves (arrays of HODLR2D_NPHASE
+ * entries; any may be NULL). */
+#define HODLR2D_NPHASE 10
 int hodlr2d_profile(hodlr2d_t h, int enable);
 int hodlr2d_get_profile(hodlr2d_t h, double* ms, int64_t* launches, int64_t* bytes);
 

@@ -10,8 +10,9 @@ import threading
 from . import build as _build
 
 MAX_LEVELS = 15
-NPHASE = 8
-PHASES = ["gather", "near", "proj", "tsum", "exp", "combine", "pair_mode", "box_mode"]
+NPHASE = 10
+PHASES = ["gather", "near", "proj", "tsum", "exp", "combine", "pair_big", "box", "pair_small",
+          "unused"]
 
 OK = 0
 ERR_ARG = -1

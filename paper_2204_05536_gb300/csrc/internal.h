@@ -13,6 +13,27 @@ namespace h2d {
 
 __host__ __device__ __forceinline__ int64_t ldpad(int64_t r) { return r + (r & 1); }
 
+// One row box of a box-mode level: its row pairs are meta[p0 .. p0 + np).
+struct BoxWork {
+  int64_t p0;
+  int32_t level, np, xs, m;
+};
+
+// Everything a product kernel needs about one stored pair, in one record.
+struct PairMeta {
+  int64_t foff;   // first value of U (V follows at foff + ldpad(m) k)
+  int64_t ppx;    // partial-result offset of the X rows (pair mode)
+  int64_t ppy;    // partial-result offset of the Y rows
+  int32_t k, xs, m, ys, n, pad;
+};
+
+// One unit of the expansion pass: rows [r0, r0 + nr) of one box.
+struct ExpTask {
+  int32_t level;
+  int32_t box;
+  int32_t r0, nr;
+};
+
 // Stored factors of one level: pairs sorted by (row box, column box) in
 // Morton order.  Columns are padded to an even length ld(r) = r + (r & 1)
 // (pad entries are zero) so that every column starts on a 16-byte boundary:
@@ -34,6 +55,7 @@ struct Level {
   int max_rank = 0;
   int64_t* d_prow = nullptr;   // 4^l + 1: first stored pair of each row box
   int64_t* d_ppoff = nullptr;  // npairs + 1: partial-result offsets (|Y| per pair)
+  PairMeta* d_meta = nullptr;  // npairs: per-pair records for the product
   int64_t npart = 0;
   // per box: entries (pair * 2 + side) of its interaction list, ascending
   // partner; side 0 = the box is the row side (applies U), 1 = column (V)
@@ -51,13 +73,11 @@ struct ProjTask {
   int64_t pair;
   int32_t r0, nr;
   int64_t out;    // offset of its k partial sums (per right-hand side)
-};
-
-// One unit of the expansion pass: rows [r0, r0 + nr) of one box.
-struct ExpTask {
-  int32_t level;
-  int32_t box;
-  int32_t r0, nr;
+  int64_t mat;    // first value of the matrix (U or V) in the level's factors
+  int32_t ld;     // its (padded) column length
+  int32_t base;   // tree position of its first row
+  int32_t k;
+  int32_t pad;
 };
 
 // Plan and scratch of the second-generation product (product.cu).
@@ -71,9 +91,10 @@ struct V2Plan {
   int32_t* d_wtask = nullptr;  // task of each projection warp
   int64_t* d_sideq = nullptr;  // (pair side, column) of each chunk-sum warp
   int lmode[HODLR2D_MAX_LEVELS] = {};  // per level: two-pass, pair or box mode
+  int lpair_small = 1 << 20;           // first pair-mode level with 64-thread blocks
   int2* d_pw_big = nullptr;    // pair-mode work (level, pair), large boxes
   int2* d_pw_small = nullptr;  // pair-mode work, boxes <= 256 points
-  int2* d_bw = nullptr;        // box-mode work (level, box), boxes <= 64 points
+  BoxWork* d_bw = nullptr;     // box-mode work, boxes <= 64 points
   int2* d_bw_big = nullptr;    // box-mode work, boxes of 65..128 points
   int64_t npw_big = 0, npw_small = 0, nbw = 0, nbw_big = 0;
   bool zero_partials = false;

@@ -22,7 +22,19 @@
 
 namespace h2d {
 
-constexpr int kFuseRows = 2048;   // largest box handled by the single-read kernels
+#ifndef H2D_FUSE_ROWS
+#define H2D_FUSE_ROWS 2048
+#endif
+#ifndef H2D_PAIR_SMEM
+#define H2D_PAIR_SMEM 0
+#endif
+#ifndef H2D_BOX_STAGE
+#define H2D_BOX_STAGE 1024
+#endif
+constexpr int kFuseRows = H2D_FUSE_ROWS;  // largest box handled by the single-read kernels
+// dynamic shared memory reserved by each large pair block; limits how many
+// pairs are in flight per SM, so that the second read of a pair hits L2
+constexpr int kPairSmem = H2D_PAIR_SMEM;
 constexpr int kSmallPair = 256;   // boxes up to this size: 64-thread pair blocks
 constexpr int kChunk2 = 256;      // row chunk of the two-pass levels (8 rows per lane)
 constexpr int kNearRhs = 4;       // right-hand sides per near-field pass
@@ -38,6 +50,7 @@ struct LevelV2 {
   const int32_t* ent_off;
   const int32_t* ent;
   const void* fac;
+  const PairMeta* meta;
 };
 
 enum { LMODE_TWO = 0, LMODE_PAIR = 1, LMODE_BOX = 2 };
@@ -217,13 +230,12 @@ __global__ void __launch_bounds__(T)
   const int l = wk.x;
   const int64_t p = wk.y;
   const LevelV2& L = P.lev[l];
-  const uint32_t bx = (uint32_t)L.px[p], by = (uint32_t)L.py[p];
-  const int32_t xs = bstart(P.leaf_off, P.kappa, l, bx), m = bsize(P.leaf_off, P.kappa, l, bx);
-  const int32_t ys = bstart(P.leaf_off, P.kappa, l, by), n = bsize(P.leaf_off, P.kappa, l, by);
+  const PairMeta PM = L.meta[p];
+  const int32_t xs = PM.xs, m = PM.m, ys = PM.ys, n = PM.n;
   const int64_t lm = ldpad(m), ln = ldpad(n);
-  const int k = L.rank[p];
+  const int k = PM.k;
   using F = typename A::fac;
-  const F* Ug = reinterpret_cast<const F*>(L.fac) + L.foff[p];
+  const F* Ug = reinterpret_cast<const F*>(L.fac) + PM.foff;
   const F* Vg = Ug + lm * k;
   for (int c = 0; c < P.nrhs; ++c) {
     const V* xc = xt + (int64_t)c * P.n;
@@ -248,8 +260,8 @@ __global__ void __launch_bounds__(T)
       if (lane == 0) ts[job] = sum;
     }
     __syncthreads();
-    V* outx = ppart + (int64_t)c * P.pstride + L.ppoff[2 * p];
-    V* outy = ppart + (int64_t)c * P.pstride + L.ppoff[2 * p + 1];
+    V* outx = ppart + (int64_t)c * P.pstride + PM.ppx;
+    V* outy = ppart + (int64_t)c * P.pstride + PM.ppy;
     for (int r = tid; r < m + n; r += T) {
       const bool own = r < m;
       const int i = own ? r : r - m;
@@ -284,13 +296,15 @@ __global__ void __launch_bounds__(T)
 // A larger pair is read from global memory with one warp per column instead.
 // ---------------------------------------------------------------------------
 constexpr int kBoxRows = 64;
-constexpr int kBoxStage = 1024;
+constexpr int kBoxStage = H2D_BOX_STAGE;
 constexpr int kBoxK = 64;
 constexpr int kBoxWarps = 4;
 
+constexpr int kBoxMaxPairs = 16;  // row pairs of one box (at most 15)
+
 template <class A>
 __global__ void __launch_bounds__(32 * kBoxWarps)
-    k_box(ArgsV2 P, const int2* __restrict__ work, int64_t nwork,
+    k_box(ArgsV2 P, const BoxWork* __restrict__ work, int64_t nwork,
           const typename A::val* __restrict__ xt, typename A::val* __restrict__ yl,
           typename A::val* __restrict__ ppart) {
   using V = typename A::val;
@@ -299,6 +313,7 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
   __shared__ V xx_all[kBoxWarps][kBoxRows];
   __shared__ V xy_all[kBoxWarps][kBoxRows];
   __shared__ V ts_all[kBoxWarps][2 * kBoxK];
+  __shared__ PairMeta pm_all[kBoxWarps][kBoxMaxPairs];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t wid = (int64_t)blockIdx.x * kBoxWarps + warp;
   if (wid >= nwork) return;
@@ -306,27 +321,29 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
   V* xx = xx_all[warp];
   V* xy = xy_all[warp];
   V* ts = ts_all[warp];
-  const int2 wk = work[wid];
-  const int l = wk.x;
-  const uint32_t X = (uint32_t)wk.y;
+  PairMeta* pm = pm_all[warp];
+  const BoxWork wk = work[wid];
+  const int l = wk.level;
   const LevelV2& L = P.lev[l];
-  const int32_t xs = bstart(P.leaf_off, P.kappa, l, X), m = bsize(P.leaf_off, P.kappa, l, X);
+  const int32_t xs = wk.xs, m = wk.m;
   const int64_t lm = ldpad(m);
-  const int64_t p0 = L.prow[X], p1 = L.prow[X + 1];
+  const int npb = wk.np;
+  if (lane < npb) pm[lane] = L.meta[wk.p0 + lane];
+  __syncwarp();
   using F = typename A::fac;
   const F* fac = reinterpret_cast<const F*>(L.fac);
   for (int c = 0; c < P.nrhs; ++c) {
     const V* xc = xt + (int64_t)c * P.n;
     for (int i = lane; i < m; i += 32) xx[i] = xc[xs + i];
     Acc y0 = A::zero(), y1 = A::zero();  // rows lane and lane + 32
-    for (int64_t p = p0; p < p1; ++p) {
-      const int k = L.rank[p];
-      const uint32_t Y = (uint32_t)L.py[p];
-      const int32_t ys = bstart(P.leaf_off, P.kappa, l, Y), n = bsize(P.leaf_off, P.kappa, l, Y);
+    for (int ip = 0; ip < npb; ++ip) {
+      const PairMeta& PM = pm[ip];
+      const int k = PM.k;
+      const int32_t ys = PM.ys, n = PM.n;
       const int64_t ln = ldpad(n);
-      const F* Ug = fac + L.foff[p];
+      const F* Ug = fac + PM.foff;
       const F* Vg = Ug + lm * k;
-      V* outy = ppart + (int64_t)c * P.pstride + L.ppoff[2 * p + 1];
+      V* outy = ppart + (int64_t)c * P.pstride + PM.ppy;
       for (int j = lane; j < n; j += 32) xy[j] = xc[ys + j];
       const int64_t tot = (lm + ln) * k;
       __syncwarp();
@@ -425,14 +442,10 @@ __global__ void __launch_bounds__(256)
   const ProjTask T = tasks[lo];
   const int q = (int)(w - T.out);
   const LevelV2& L = P.lev[T.level];
-  const uint32_t bx = (uint32_t)L.px[T.pair], by = (uint32_t)L.py[T.pair];
-  const int32_t m = bsize(P.leaf_off, P.kappa, T.level, bx);
-  const int32_t nrow = T.side == 0 ? bsize(P.leaf_off, P.kappa, T.level, by) : m;
-  const int32_t base = bstart(P.leaf_off, P.kappa, T.level, T.side == 0 ? by : bx);
-  const int k = L.rank[T.pair];
+  const int32_t base = T.base;
+  const int k = T.k;
   using F = typename A::fac;
-  const F* col = reinterpret_cast<const F*>(L.fac) + L.foff[T.pair] +
-                 (T.side == 0 ? ldpad(m) * k : 0) + (int64_t)q * ldpad(nrow);
+  const F* col = reinterpret_cast<const F*>(L.fac) + T.mat + (int64_t)q * T.ld;
   V v[R];
 #pragma unroll
   for (int u = 0; u < R; ++u) {
@@ -601,7 +614,7 @@ static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
     const Level& L = h->lev[l];
     const void* fac = mode == HODLR2D_MODE_F64 ? (const void*)L.d_fac : L.d_fac_mode[mode];
     P.lev[l] = LevelV2{L.d_px, L.d_py, L.d_rank, L.d_foff, L.d_prow, L.d_ppoff,
-                       L.d_toff, L.d_ent_off, L.d_ent, fac};
+                       L.d_toff, L.d_ent_off, L.d_ent, fac, L.d_meta};
   }
   for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) P.lmode[l] = h->v2.lmode[l];
   P.leaf_off = h->d_leaf_off;
@@ -661,6 +674,11 @@ int plan_v2(hodlr2d* h) {
             T.r0 = r0;
             T.nr = std::min(kChunk2, rows - r0);
             T.out = out;
+            T.mat = L.h_foff[p] + (side == 0 ? ldpad(cnt(px[p])) * k : 0);
+            T.ld = (int32_t)ldpad(rows);
+            T.base = (int32_t)h->h_leaf_off[(int64_t)(side == 0 ? py[p] : px[p]) << sh];
+            T.k = k;
+            T.pad = 0;
             out += k;
             proj.push_back(T);
           }
@@ -712,9 +730,11 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMemcpy(V.d_red, red.data(), sizeof(int64_t) * red.size(), cudaMemcpyHostToDevice));
   // single-read levels: pair mode (one block per pair, partials for both
   // sides) or box mode (one warp per row box, partials for the column side)
-  std::vector<int2> pw_big, pw_small, bw, bw_big;
+  std::vector<int2> pw_big, pw_small, bw_big;
+  std::vector<BoxWork> bw;
   int64_t pbase = 0;
   for (int l = 1; l <= kappa; ++l) V.lmode[l] = l < V.lfuse ? LMODE_TWO : LMODE_PAIR;
+  V.lpair_small = kappa + 1;
   for (int l = V.lfuse; l <= kappa; ++l) {
     Level& L = h->lev[l];
     const int64_t np = L.npairs;
@@ -740,14 +760,53 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMalloc(&L.d_ppoff, sizeof(int64_t) * (2 * np + 2)));
     H2D_CK(cudaMemcpy(L.d_ppoff, pp.data(), sizeof(int64_t) * (2 * np + 2), cudaMemcpyHostToDevice));
     if (V.lmode[l] == LMODE_PAIR) {
+      if (mc <= kSmallPair) V.lpair_small = std::min(V.lpair_small, l);
       for (int64_t p = 0; p < np; ++p)
         if (L.h_rank[p] > 0) (mc <= kSmallPair ? pw_small : pw_big).push_back(make_int2(l, (int)p));
     } else {
+      std::vector<int64_t> prow(((int64_t)1 << (2 * l)) + 1);
+      H2D_CK(cudaMemcpy(prow.data(), L.d_prow, sizeof(int64_t) * prow.size(),
+                        cudaMemcpyDeviceToHost));
       for (int64_t b = 0; b < ((int64_t)1 << (2 * l)); ++b)
-        if (cnt((int32_t)b) > 0) (mc <= kBoxRows ? bw : bw_big).push_back(make_int2(l, (int)b));
+        if (cnt((int32_t)b) > 0) {
+          BoxWork w;
+          w.level = l;
+          w.np = (int32_t)(prow[b + 1] - prow[b]);
+          w.p0 = prow[b];
+          w.xs = (int32_t)h->h_leaf_off[b << sh];
+          w.m = (int32_t)cnt((int32_t)b);
+          bw.push_back(w);
+        }
     }
   }
   V.pstride = std::max<int64_t>(pbase, 1);
+  for (int l = 1; l <= kappa; ++l) {  // one record per stored pair
+    Level& L = h->lev[l];
+    const int64_t np = L.npairs;
+    if (!np) continue;
+    const int sh = 2 * (kappa - l);
+    std::vector<int32_t> px(np), py(np);
+    H2D_CK(cudaMemcpy(px.data(), L.d_px, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
+    H2D_CK(cudaMemcpy(py.data(), L.d_py, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
+    std::vector<int64_t> pp(2 * np + 2, 0);
+    if (L.d_ppoff)
+      H2D_CK(cudaMemcpy(pp.data(), L.d_ppoff, sizeof(int64_t) * (2 * np + 2), cudaMemcpyDeviceToHost));
+    std::vector<PairMeta> meta(np);
+    for (int64_t p = 0; p < np; ++p) {
+      PairMeta& M = meta[p];
+      M.foff = L.h_foff[p];
+      M.ppx = pp[2 * p];
+      M.ppy = pp[2 * p + 1];
+      M.k = L.h_rank[p];
+      M.xs = h->h_leaf_off[(int64_t)px[p] << sh];
+      M.m = h->h_leaf_off[(int64_t)(px[p] + 1) << sh] - M.xs;
+      M.ys = h->h_leaf_off[(int64_t)py[p] << sh];
+      M.n = h->h_leaf_off[(int64_t)(py[p] + 1) << sh] - M.ys;
+      M.pad = 0;
+    }
+    H2D_CK(cudaMalloc(&L.d_meta, sizeof(PairMeta) * np));
+    H2D_CK(cudaMemcpy(L.d_meta, meta.data(), sizeof(PairMeta) * np, cudaMemcpyHostToDevice));
+  }
   V.npw_big = (int64_t)pw_big.size();
   V.npw_small = (int64_t)pw_small.size();
   V.nbw = (int64_t)bw.size();
@@ -757,13 +816,13 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMemcpy(V.d_bw_big, bw_big.data(), sizeof(int2) * V.nbw_big, cudaMemcpyHostToDevice));
   H2D_CK(cudaMalloc(&V.d_pw_big, sizeof(int2) * std::max<int64_t>(V.npw_big, 1)));
   H2D_CK(cudaMalloc(&V.d_pw_small, sizeof(int2) * std::max<int64_t>(V.npw_small, 1)));
-  H2D_CK(cudaMalloc(&V.d_bw, sizeof(int2) * std::max<int64_t>(V.nbw, 1)));
+  H2D_CK(cudaMalloc(&V.d_bw, sizeof(BoxWork) * std::max<int64_t>(V.nbw, 1)));
   if (V.npw_big)
     H2D_CK(cudaMemcpy(V.d_pw_big, pw_big.data(), sizeof(int2) * V.npw_big, cudaMemcpyHostToDevice));
   if (V.npw_small)
     H2D_CK(cudaMemcpy(V.d_pw_small, pw_small.data(), sizeof(int2) * V.npw_small,
                       cudaMemcpyHostToDevice));
-  if (V.nbw) H2D_CK(cudaMemcpy(V.d_bw, bw.data(), sizeof(int2) * V.nbw, cudaMemcpyHostToDevice));
+  if (V.nbw) H2D_CK(cudaMemcpy(V.d_bw, bw.data(), sizeof(BoxWork) * V.nbw, cudaMemcpyHostToDevice));
   // pair-mode values of partial results need zero for pairs of rank 0
   V.zero_partials = false;
   for (int l = V.lfuse; l <= kappa; ++l)
@@ -817,19 +876,24 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   Val* xt = reinterpret_cast<Val*>(V.d_xt);
   Val* yl = reinterpret_cast<Val*>(V.d_yl);
   Val* ppart = reinterpret_cast<Val*>(V.d_ppart);
-  const int64_t vb = 8 * n * nrhs;
+  const int64_t fs = (int64_t)sizeof(typename A::fac);  // bytes per factor value
+  const int64_t vs = (int64_t)sizeof(Val);                // bytes per vector value
+  const int64_t vb = vs * n * nrhs;                       // one vector block
   {
     PhaseScope ps(h, 0, 1, vb + 8 * n + 8 * n * nrhs);
     k_gather2<A><<<g, 256, 0, s>>>(x, h->d_perm, n, nrhs, xt);
   }
   // the near field (arithmetic-bound) and the single-read levels run on side
   // streams, concurrently with the two-pass levels on the caller's stream
+  // (while profiling, everything stays on the caller's stream so that the
+  // per-phase event times are those of each kernel alone)
+  const cudaStream_t sn = h->prof_on ? s : V.s_near;
+  const cudaStream_t sf = h->prof_on ? s : V.s_far;
   H2D_CK(cudaEventRecord(V.ev_in, s));
-  H2D_CK(cudaStreamWaitEvent(V.s_near, V.ev_in, 0));
-  H2D_CK(cudaStreamWaitEvent(V.s_far, V.ev_in, 0));
+  H2D_CK(cudaStreamWaitEvent(sn, V.ev_in, 0));
+  H2D_CK(cudaStreamWaitEvent(sf, V.ev_in, 0));
   {
     const unsigned nleaf = (unsigned)(1u << (2 * h->kappa));
-    cudaStream_t sn = V.s_near;
     PhaseScope ps(h, 1, 1, 24 * n + 2 * vb, sn);
     if (mode == HODLR2D_MODE_F64)
       k_near_f64<<<nleaf, 64, 0, sn>>>(h->d_x, h->d_y, h->d_perm, h->d_leaf_off, h->kappa, h->kp,
@@ -852,13 +916,13 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   for (int l = 1; l < V.lfuse; ++l) two_pass_vals += h->lev[l].nstored;
   if (V.nproj) {
     {
-      PhaseScope ps(h, 2, 1, 8 * two_pass_vals + 8 * V.proj_partials * nrhs);
+      PhaseScope ps(h, 2, 1, fs * two_pass_vals + vs * V.proj_partials * nrhs);
       const int64_t thr = V.proj_partials * 32;  // one warp per (task, column)
       k_proj2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
           P, V.d_proj, V.d_wtask, V.proj_partials, xt, reinterpret_cast<Val*>(V.d_part));
     }
     {
-      PhaseScope ps(h, 3, 1, 8 * (V.proj_partials + h->t_total) * nrhs);
+      PhaseScope ps(h, 3, 1, vs * (V.proj_partials + h->t_total) * nrhs);
       const int64_t thr = V.ntsum * 32;
       k_tsum2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
           P, V.d_proj, V.d_red, V.d_sideq, V.ntsum, reinterpret_cast<const Val*>(V.d_part),
@@ -867,27 +931,35 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   }
   if (V.lfuse > 1) {
     {
-      PhaseScope ps(h, 4, 1, 8 * two_pass_vals + vb * (V.lfuse - 1));
+      PhaseScope ps(h, 4, 1, fs * two_pass_vals + vb * (V.lfuse - 1));
       k_exp2<A><<<(unsigned)V.nexp, 256, 0, s>>>(P, V.d_exp, reinterpret_cast<const Val*>(V.d_t),
                                                  yl);
     }
   }
-  H2D_CK(cudaEventRecord(V.ev_near, V.s_near));
-  const cudaStream_t sf = V.s_far;
+  H2D_CK(cudaEventRecord(V.ev_near, sn));
   if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, sf));
-  if (V.npw_big || V.npw_small) {
+  if (V.npw_big) {
     int64_t vals = 0;
     for (int l = V.lfuse; l <= h->kappa; ++l)
-      if (V.lmode[l] == LMODE_PAIR) vals += h->lev[l].nstored;
-    PhaseScope ps(h, 6, (V.npw_big ? 1 : 0) + (V.npw_small ? 1 : 0), 8 * vals, sf);
-    if (V.npw_big) k_pair<A, 256><<<(unsigned)V.npw_big, 256, 0, sf>>>(P, V.d_pw_big, xt, ppart);
-    if (V.npw_small) k_pair<A, 64><<<(unsigned)V.npw_small, 64, 0, sf>>>(P, V.d_pw_small, xt, ppart);
+      if (V.lmode[l] == LMODE_PAIR && l < V.lpair_small) vals += h->lev[l].nstored;
+    PhaseScope ps(h, 6, 1, fs * vals, sf);
+    if (kPairSmem > 48 * 1024)
+      H2D_CK(cudaFuncSetAttribute(k_pair<A, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kPairSmem));
+    k_pair<A, 256><<<(unsigned)V.npw_big, 256, kPairSmem, sf>>>(P, V.d_pw_big, xt, ppart);
+  }
+  if (V.npw_small) {
+    int64_t vals = 0;
+    for (int l = V.lfuse; l <= h->kappa; ++l)
+      if (V.lmode[l] == LMODE_PAIR && l >= V.lpair_small) vals += h->lev[l].nstored;
+    PhaseScope ps(h, 8, 1, fs * vals, sf);
+    k_pair<A, 64><<<(unsigned)V.npw_small, 64, 0, sf>>>(P, V.d_pw_small, xt, ppart);
   }
   if (V.nbw || V.nbw_big) {
     int64_t vals = 0;
     for (int l = V.lfuse; l <= h->kappa; ++l)
       if (V.lmode[l] == LMODE_BOX) vals += h->lev[l].nstored;
-    PhaseScope ps(h, 7, (V.nbw ? 1 : 0) + (V.nbw_big ? 1 : 0), 8 * vals, sf);
+    PhaseScope ps(h, 7, (V.nbw ? 1 : 0) + (V.nbw_big ? 1 : 0), fs * vals, sf);
     if (V.nbw)
       k_box<A><<<(unsigned)((V.nbw + kBoxWarps - 1) / kBoxWarps), 32 * kBoxWarps, 0, sf>>>(
           P, V.d_bw, V.nbw, xt, yl, ppart);
@@ -896,7 +968,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   H2D_CK(cudaStreamWaitEvent(s, V.ev_near, 0));
   H2D_CK(cudaStreamWaitEvent(s, V.ev_far, 0));
   {
-    PhaseScope ps(h, 5, 1, vb * (h->kappa + 1) + 8 * V.pstride * nrhs + 16 * n + 8 * n * nrhs);
+    PhaseScope ps(h, 5, 1, vb * (h->kappa + 1) + vs * V.pstride * nrhs + 16 * n + 8 * n * nrhs);
     k_combine2<A><<<g, 256, 0, s>>>(P, yl, ppart, V.d_leaf_of, h->d_perm, y);
   }
   H2D_CK(cudaGetLastError());
