@@ -463,9 +463,10 @@ def run_ours(args, ws, rank, local):
     peak, peak_src = peaks()
     dom = max((k for k in prof if prof[k]["launches"]), key=lambda k: prof[k]["ms"])
     d = prof[dom]
-    # one product runs the phase's kernel(s) once; bytes are per product
+    # per product: the phase's launches, their device time and algorithmic bytes
     per_launch_ms = d["ms"] / args.steps
-    achieved = d["bytes"] / (per_launch_ms * 1e-3) / 1e9
+    bytes_step = d["bytes"] // args.steps
+    achieved = bytes_step / (per_launch_ms * 1e-3) / 1e9
     launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
     alg_bytes = st["bytes_per_matvec"][mode]
     hbm_frac_product = alg_bytes / (ms_step * 1e-3) / 1e9 / peak
@@ -490,7 +491,7 @@ def run_ours(args, ws, rank, local):
                          % (st["far_values"] * 8 / 1e9)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "peak_source": peak_src, "bytes_per_launch": d["bytes"],
+                     "peak_source": peak_src, "bytes_per_launch": bytes_step,
                      "ms_per_launch": round(per_launch_ms, 4),
                      "launches_per_product": d["launches"] // args.steps,
                      "traffic": NCU_TRAFFIC.get((dom, mode, n))},

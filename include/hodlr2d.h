@@ -42,7 +42,7 @@ extern "C" {
 #define HODLR2D_ERR_OOM (-2)     /* device or host allocation failed             */
 #define HODLR2D_ERR_CUDA (-3)    /* a CUDA runtime call failed                   */
 #define HODLR2D_ERR_NOCONV (-4)  /* an iteration did not reach its tolerance     */
-#define HODLR2D_ERR_TIMEOUT (-5) /* a bounded device-side wait gave up           */
+#define HODLR2D_ERR_TIMEOUT (-5) /* reserved: a bounded device-side wait gave up */
 #define HODLR2D_ERR_DEPTH (-6)   /* no depth <= 14 meets the leaf rule           */
 #define HODLR2D_ERR_STATE (-7)   /* handle not ready (e.g. no factors yet)       */
 
@@ -146,10 +146,14 @@ int hodlr2d_gmres(hodlr2d_t h, const double* b, double* x, double tol);
 
 /* As hodlr2d_gmres with explicit restart length, matvec cap, and outputs
  * (iters: matvecs used, relres: final |b - A x| / |b|; either may be NULL).
- * inner_mode: the hodlr2d_mode of the products inside each cycle; with a mode
- * other than F64 the solver runs iterative refinement: residuals r = b - A x
- * in F64, corrections solved with inner_mode.  Returns HODLR2D_ERR_NOCONV
- * (with x and the outputs filled) when maxit is reached first. */
+ * inner_mode: the hodlr2d_mode of the products inside each cycle.  F64 and
+ * DF32 (binary64-level accuracy) run plain GMRES with that product; F32 and
+ * BF16 run iterative refinement: residuals r = b - A x with the F64 product,
+ * corrections solved with inner_mode to a relative residual of 1e-5 (F32) or
+ * 1e-2 (BF16).  Products of a zero vector are skipped and not counted.  The
+ * Krylov workspace ((restart + 6) n doubles) is kept by the handle until
+ * hodlr2d_free.  Returns HODLR2D_ERR_NOCONV (with x and the outputs filled)
+ * when maxit is reached first. */
 int hodlr2d_gmres_ex(hodlr2d_t h, const double* b, double* x, double tol,
                      int restart, int maxit, int inner_mode, int* iters,
                      double* relres);
@@ -189,8 +193,8 @@ int hodlr2d_get_stats(hodlr2d_t h, hodlr2d_stats* s);
  * kernel running by itself.  hodlr2d_profile(h, 1) resets and starts
  * recording, (h, 0) stops.  hodlr2d_get_profile synchronises the stream and
  * returns, per phase, the summed milliseconds, the number of kernel launches,
- * and the algorithmic bytes one launch moves (arrays of HODLR2D_NPHASE
- * entries; any may be NULL). */
+ * and the summed algorithmic bytes of those launches (arrays of
+ * HODLR2D_NPHASE entries; any may be NULL). */
 #define HODLR2D_NPHASE 10
 int hodlr2d_profile(hodlr2d_t h, int enable);
 int hodlr2d_get_profile(hodlr2d_t h, double* ms, int64_t* launches, int64_t* bytes);

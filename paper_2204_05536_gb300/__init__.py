@@ -196,7 +196,7 @@ class HODLR2D:
         check(self._lib.hodlr2d_profile(self._h, int(bool(enable))), "hodlr2d_profile")
 
     def get_profile(self) -> dict:
-        """Per phase: summed device ms, launches, algorithmic bytes per launch."""
+        """Per phase: summed device ms, launches and algorithmic bytes."""
         ms = np.zeros(_lib.NPHASE)
         nl = np.zeros(_lib.NPHASE, dtype=np.int64)
         by = np.zeros(_lib.NPHASE, dtype=np.int64)

@@ -474,7 +474,8 @@ int aca_build(hodlr2d* h) {
     L.h_foff[np] = tot;
     L.nvalues = tot;
     L.nstored = stored;
-    H2D_CK(cudaMalloc(&L.d_fac, sizeof(double) * std::max<int64_t>(tot, 1)));
+    // 16 bytes of slack: bulk copies widen each column to 16-byte boundaries
+    H2D_CK(cudaMalloc(&L.d_fac, sizeof(double) * (std::max<int64_t>(tot, 1) + 2)));
     H2D_CK(cudaMemcpy(L.d_foff, L.h_foff.data(), sizeof(int64_t) * (np + 1), cudaMemcpyHostToDevice));
     {
       const double** d_src = nullptr;

@@ -127,6 +127,7 @@ static void free_handle(hodlr2d* h) {
   cudaFree(h->d_y);
   cudaFree(h->d_perm);
   cudaFree(h->d_leaf_off);
+  cudaFree(h->d_gm);
   free_modes(h);
   for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) {
     Level& L = h->lev[l];
@@ -480,7 +481,8 @@ int hodlr2d_import_factors(hodlr2d_t h, int64_t npairs, const int32_t* info,
     }
     H2D_CK(cudaMalloc(&L.d_rank, sizeof(int32_t) * (L.npairs + 1)));
     H2D_CK(cudaMalloc(&L.d_foff, sizeof(int64_t) * (L.npairs + 1)));
-    H2D_CK(cudaMalloc(&L.d_fac, sizeof(double) * fac.size()));
+    // 16 bytes of slack: bulk copies widen each column to 16-byte boundaries
+    H2D_CK(cudaMalloc(&L.d_fac, sizeof(double) * (fac.size() + 2)));
     if (L.npairs)
       H2D_CK(cudaMemcpy(L.d_rank, L.h_rank.data(), sizeof(int32_t) * L.npairs,
                         cudaMemcpyHostToDevice));

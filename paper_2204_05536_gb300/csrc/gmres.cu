@@ -4,9 +4,16 @@
 // orthogonalisation is two batched dot-product launches; the (restart+1) x
 // restart Hessenberg matrix and its Givens rotations live on the host (tiny).
 // Dot products reduce in a fixed order (block partials, then one pass), so a
-// solve is bitwise reproducible.  With an inner mode other than F64 the
-// solver runs iterative refinement: r = b - A x with the F64 product, then a
-// GMRES correction with the inner mode's product, until |r| <= tol |b|.
+// solve is bitwise reproducible.  Inner modes:
+//   F64, DF32   plain GMRES with that product (the float-float product keeps
+//               binary64-level accuracy, so it needs no refinement);
+//   F32, BF16   iterative refinement: r = b - A x with the F64 product, then
+//               a GMRES correction with the inner mode's product to a relative
+//               residual a little above that product's own error, until
+//               |r| <= tol |b|.
+// A product whose input is known to be zero (x0 = 0, each fresh correction)
+// is skipped.  The Krylov basis lives in a per-handle workspace that grows
+// on demand and is kept for the next solve.
 #include <math.h>
 
 #include <algorithm>
@@ -105,8 +112,8 @@ struct Work {
 
 // GMRES(restart) on A z = rhs starting from z (device), product `mode`.
 // Stops at |rhs - A z| <= tol_abs or after `budget` products.
-int gmres_core(Work& W, const double* rhs, double* z, double tol_abs, int restart, int budget,
-               int mode, double* Vb, double* w, int* used, double* final_res) {
+int gmres_core(Work& W, const double* rhs, double* z, bool z_zero, double tol_abs, int restart,
+               int budget, int mode, double* Vb, double* w, int* used, double* final_res) {
   const int64_t n = W.n;
   cudaStream_t s = W.s;
   const int m = restart;
@@ -115,11 +122,17 @@ int gmres_core(Work& W, const double* rhs, double* z, double tol_abs, int restar
   int it = 0;
   double beta = 0.0;
   const unsigned gb = (unsigned)((n + 255) / 256);
+  if (z_zero) H2D_CK(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
   while (true) {
-    // r = rhs - A z, into V_0
-    H2D_TRY(W.matvec(z, w, mode));
-    ++it;
-    k_axpby<<<gb, 256, 0, s>>>(1.0, rhs, -1.0, w, Vb, n);
+    // r = rhs - A z, into V_0 (r = rhs while z is still zero)
+    if (z_zero) {
+      H2D_CK(cudaMemcpyAsync(Vb, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      z_zero = false;
+    } else {
+      H2D_TRY(W.matvec(z, w, mode));
+      ++it;
+      k_axpby<<<gb, 256, 0, s>>>(1.0, rhs, -1.0, w, Vb, n);
+    }
     beta = W.norm(Vb);
     if (!isfinite(beta)) return HODLR2D_ERR_CUDA;
     if (beta <= tol_abs || it >= budget) break;
@@ -185,7 +198,6 @@ int gmres_run(hodlr2d* h, const double* b, double* x, double tol, int restart, i
   W.h = h;
   W.n = n;
   W.s = s;
-  double *db = nullptr, *dx = nullptr, *Vb = nullptr, *w = nullptr, *r = nullptr, *d = nullptr;
   const int m = std::min<int>(restart, (int)std::min<int64_t>(n, 1 << 20));
   int rc = HODLR2D_OK;
   auto ck = [&](cudaError_t e) {
@@ -194,66 +206,83 @@ int gmres_run(hodlr2d* h, const double* b, double* x, double tol, int restart, i
       rc = e == cudaErrorMemoryAllocation ? HODLR2D_ERR_OOM : HODLR2D_ERR_CUDA;
     }
   };
-  ck(cudaMalloc(&W.partial, sizeof(double) * kDotBlocks * (m + 2)));
-  ck(cudaMalloc(&W.dvec, sizeof(double) * (m + 2)));
-  ck(cudaMalloc(&Vb, sizeof(double) * n * (m + 1)));
-  ck(cudaMalloc(&w, sizeof(double) * n));
-  ck(cudaMalloc(&r, sizeof(double) * n));
-  ck(cudaMalloc(&d, sizeof(double) * n));
-  if (!bd) ck(cudaMalloc(&db, sizeof(double) * n));
-  if (!xd) ck(cudaMalloc(&dx, sizeof(double) * n));
-  if (rc == HODLR2D_OK) {
-    if (!bd) ck(cudaMemcpyAsync(db, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    if (!xd) ck(cudaMemcpyAsync(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  // workspace: partials, coefficients, basis (m + 1 vectors), w, r, d, b, x
+  const int64_t need = (int64_t)kDotBlocks * (m + 2) + (m + 2) + n * (m + 1) + 5 * n;
+  if (h->gm_values < need) {
+    cudaFree(h->d_gm);
+    h->d_gm = nullptr;
+    h->gm_values = 0;
+    ck(cudaMalloc(&h->d_gm, sizeof(double) * need));
+    if (rc == HODLR2D_OK) h->gm_values = need;
   }
+  if (rc != HODLR2D_OK) return rc;
+  double* p = h->d_gm;
+  auto take = [&](int64_t k) {
+    double* q = p;
+    p += k;
+    return q;
+  };
+  W.partial = take((int64_t)kDotBlocks * (m + 2));
+  W.dvec = take(m + 2);
+  double* Vb = take(n * (m + 1));
+  double* w = take(n);
+  double* r = take(n);
+  double* d = take(n);
+  double* db = bd ? nullptr : take(n);
+  double* dx = xd ? nullptr : take(n);
+  if (!bd) ck(cudaMemcpyAsync(db, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  if (!xd) ck(cudaMemcpyAsync(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
   const double* B = bd ? b : db;
   double* X = xd ? x : dx;
   int used = 0;
-  double res = 0.0, bn = 0.0;
+  double res = 0.0, bn = 0.0, xn = 0.0;
   if (rc == HODLR2D_OK) {
     bn = W.norm(B);
-    if (!isfinite(bn)) rc = HODLR2D_ERR_ARG;
+    xn = W.norm(X);
+    if (!isfinite(bn) || !isfinite(xn)) rc = HODLR2D_ERR_ARG;
   }
   if (rc == HODLR2D_OK && bn == 0.0) {
     ck(cudaMemsetAsync(X, 0, sizeof(double) * n, s));
     res = 0.0;
   } else if (rc == HODLR2D_OK) {
-    if (inner_mode == HODLR2D_MODE_F64) {
-      rc = gmres_core(W, B, X, tol * bn, m, maxit, HODLR2D_MODE_F64, Vb, w, &used, &res);
+    if (inner_mode == HODLR2D_MODE_F64 || inner_mode == HODLR2D_MODE_DF32) {
+      rc = gmres_core(W, B, X, xn == 0.0, tol * bn, m, maxit, inner_mode, Vb, w, &used, &res);
     } else {
-      // iterative refinement: F64 residual, low-precision correction
+      // iterative refinement: F64 residual, low-precision correction solved to
+      // a relative residual just above the inner product's own error
       const unsigned gb = (unsigned)((n + 255) / 256);
-      const double inner_rel = 1e-3;
+      const double inner_rel = inner_mode == HODLR2D_MODE_F32 ? 1e-5 : 1e-2;
+      bool x_zero = xn == 0.0;
       while (rc == HODLR2D_OK) {
-        rc = matvec_mode_device(h, X, w, 1, HODLR2D_MODE_F64);
-        if (rc) break;
-        ++used;
-        k_axpby<<<gb, 256, 0, s>>>(1.0, B, -1.0, w, r, n);
+        if (x_zero) {
+          ck(cudaMemcpyAsync(r, B, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        } else {
+          rc = matvec_mode_device(h, X, w, 1, HODLR2D_MODE_F64);
+          if (rc) break;
+          ++used;
+          k_axpby<<<gb, 256, 0, s>>>(1.0, B, -1.0, w, r, n);
+        }
         res = W.norm(r);
         if (!isfinite(res)) { rc = HODLR2D_ERR_CUDA; break; }
         if (res <= tol * bn || used >= maxit) break;
-        ck(cudaMemsetAsync(d, 0, sizeof(double) * n, s));
         int u2 = 0;
         double r2 = 0.0;
-        rc = gmres_core(W, r, d, inner_rel * res, m, std::max(1, maxit - used), inner_mode, Vb, w,
-                        &u2, &r2);
+        rc = gmres_core(W, r, d, true, std::max(inner_rel * res, 0.5 * tol * bn), m,
+                        std::max(1, maxit - used), inner_mode, Vb, w, &u2, &r2);
         used += u2;
         if (rc) break;
-        k_axpby<<<gb, 256, 0, s>>>(1.0, X, 1.0, d, X, n);
+        if (x_zero) {
+          ck(cudaMemcpyAsync(X, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+          x_zero = false;
+        } else {
+          k_axpby<<<gb, 256, 0, s>>>(1.0, X, 1.0, d, X, n);
+        }
       }
     }
   }
   if (rc == HODLR2D_OK && !xd)
     ck(cudaMemcpyAsync(x, X, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   ck(cudaStreamSynchronize(s));
-  cudaFree(W.partial);
-  cudaFree(W.dvec);
-  cudaFree(Vb);
-  cudaFree(w);
-  cudaFree(r);
-  cudaFree(d);
-  cudaFree(db);
-  cudaFree(dx);
   if (iters) *iters = used;
   if (relres) *relres = bn > 0.0 ? res / bn : 0.0;
   if (rc == HODLR2D_OK && bn > 0.0 && res > tol * bn) rc = HODLR2D_ERR_NOCONV;

@@ -81,6 +81,14 @@ struct ProjTask {
 };
 
 // Plan and scratch of the second-generation product (product.cu).
+// Pair-mode work of one level: (level, pair) of every stored pair of rank > 0,
+// and the largest box of the level.
+struct StageLevel {
+  int2* d_work = nullptr;
+  int64_t nwork = 0;
+  int max_rows = 0;
+};
+
 struct V2Plan {
   bool ready = false;
   int lfuse = 1;   // first level handled by the fused kernel
@@ -92,11 +100,8 @@ struct V2Plan {
   int64_t* d_sideq = nullptr;  // (pair side, column) of each chunk-sum warp
   int lmode[HODLR2D_MAX_LEVELS] = {};  // per level: two-pass, pair or box mode
   int lpair_small = 1 << 20;           // first pair-mode level with 64-thread blocks
-  int2* d_pw_big = nullptr;    // pair-mode work (level, pair), large boxes
-  int2* d_pw_small = nullptr;  // pair-mode work, boxes <= 256 points
   BoxWork* d_bw = nullptr;     // box-mode work, boxes <= 64 points
-  int2* d_bw_big = nullptr;    // box-mode work, boxes of 65..128 points
-  int64_t npw_big = 0, npw_small = 0, nbw = 0, nbw_big = 0;
+  int64_t nbw = 0;
   bool zero_partials = false;
   int64_t pstride = 1;
   int32_t* d_leaf_of = nullptr;
@@ -112,6 +117,7 @@ struct V2Plan {
   void* d_x32 = nullptr;  // binary32 coordinates (F32 / BF16 modes)
   void* d_y32 = nullptr;
   KernelF32 kf32{};
+  StageLevel stg[HODLR2D_MAX_LEVELS];
   // side streams: near field, and the single-read far-field levels
   cudaStream_t s_near = nullptr, s_far = nullptr;
   cudaEvent_t ev_in = nullptr, ev_near = nullptr, ev_far = nullptr;
@@ -160,6 +166,8 @@ struct hodlr2d {
   double* d_t = nullptr;       // t_total x nrhs
   double* d_io = nullptr;      // staging for host x / y (n x nrhs each)
   int io_nrhs = 0;
+  double* d_gm = nullptr;      // GMRES workspace (Krylov basis and vectors)
+  int64_t gm_values = 0;
 
   hodlr2d_stats st{};
 
@@ -186,7 +194,7 @@ struct PhaseScope {
   PhaseScope(hodlr2d* h_, int phase_, int nlaunch_, int64_t bytes, cudaStream_t s_)
       : h(h_), phase(phase_), nlaunch(nlaunch_), st(s_) {
     if (!h->prof_on) return;
-    h->prof_bytes[phase] = bytes;
+    h->prof_bytes[phase] += bytes;
     if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
       cudaEventRecord(a, st);
   }

@@ -1,20 +1,25 @@
-// The HODLR2D product (Alg. 2), second generation: native FP64 (F64A) or
-// float-float (DF32A) arithmetic over the same factor layout.
+// The HODLR2D product (Alg. 2) over one factor layout, in four arithmetic
+// policies: binary64 (F64A), float-float (DF32A), binary32 (F32A) and
+// binary32 sums over bfloat16 factors (BF16A).
 //
-// Far field, levels whose boxes hold <= kFuseRows points ("fused" levels):
-// one thread block per row box X reads each stored pair (X,Y), Y > X, once:
-//   t1 = V^T x_Y and t2 = U^T x_X      (one warp per column, shuffle sums)
-//   y_X += U t1                         (one thread per row, kept on chip)
-//   partial_(X,Y) = V t2                (one thread per row of Y, to HBM)
-// The pair is staged in shared memory while it is read when it fits, so the
-// expansions re-read it from there.  Each box's own sum goes to its level
-// slab; the partials are added by the combine pass in a fixed order.
-// Coarser levels (huge boxes) use a projection pass over row chunks, a fixed-
-// order sum of the chunk partials, and an expansion pass.
+// Far field, by level (the level mode is fixed by the plan):
+//   two-pass (boxes > kFuseRows points): a projection pass t = V^T x over row
+//     chunks, a fixed-order sum of the chunk partials, and an expansion pass
+//     y_X += U t per row box into the level's slab;
+//   pair (boxes of kBoxRows..kFuseRows points): one block per stored pair
+//     (X,Y) computes t1 = V^T x_Y, t2 = U^T x_X and writes the partial
+//     results U t1 (rows of X) and V t2 (rows of Y); one right-hand side uses
+//     k_pairg (each factor value read once, kept in registers between the two
+//     uses), binary64 or several right-hand sides use k_pair;
+//   box (boxes of <= kBoxRows points): one warp per row box, the box's pairs
+//     staged in shared memory; own sums to the slab, partials for the column
+//     side.
 // Near field: every leaf against itself and its edge sharers, entries
-// evaluated from the points.
+// evaluated from the points.  The combine pass adds the near field, the
+// slabs and the partials of each point in a fixed order.
 // No atomics anywhere: a product is bitwise reproducible.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "arith.cuh"
@@ -25,16 +30,10 @@ namespace h2d {
 #ifndef H2D_FUSE_ROWS
 #define H2D_FUSE_ROWS 2048
 #endif
-#ifndef H2D_PAIR_SMEM
-#define H2D_PAIR_SMEM 0
-#endif
 #ifndef H2D_BOX_STAGE
 #define H2D_BOX_STAGE 1024
 #endif
 constexpr int kFuseRows = H2D_FUSE_ROWS;  // largest box handled by the single-read kernels
-// dynamic shared memory reserved by each large pair block; limits how many
-// pairs are in flight per SM, so that the second read of a pair hits L2
-constexpr int kPairSmem = H2D_PAIR_SMEM;
 constexpr int kSmallPair = 256;   // boxes up to this size: 64-thread pair blocks
 constexpr int kChunk2 = 256;      // row chunk of the two-pass levels (8 rows per lane)
 constexpr int kNearRhs = 4;       // right-hand sides per near-field pass
@@ -82,6 +81,15 @@ __device__ __forceinline__ float shfl_val(float v, int o) {
 }
 __device__ __forceinline__ float2 shfl_val(float2 v, int o) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ double shfl_idx(double v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ float shfl_idx(float v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ float2 shfl_idx(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
 // ---------------------------------------------------------------------------
@@ -212,8 +220,8 @@ __global__ void __launch_bounds__(32 * kNearWarps)
 // pair mode (mid levels): one block per stored pair (X,Y).  Phase 1: one warp
 // per column computes t1 = V^T x_Y and t2 = U^T x_X (rows over lanes, shuffle
 // sum).  Phase 2: one thread per row writes U t1 (rows of X) and V t2 (rows of
-// Y) as partial results; its reads of U and V hit L2, which still holds the
-// pair from phase 1.
+// Y) as partial results.  Phase 2 re-reads U and V: from L2 when the pairs in
+// flight fit it (small boxes), else from HBM.
 // ---------------------------------------------------------------------------
 constexpr int kPairKmax = 256;
 
@@ -281,6 +289,156 @@ __global__ void __launch_bounds__(T)
       (own ? outx : outy)[i] = A::fin(a);
     }
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// register pair mode: one block of T threads per stored pair (X,Y), one
+// right-hand side.  Thread t owns rows t, t + T, ... (at most RM) of X and of
+// Y and keeps x, and the partial results y, of those rows in registers.  The
+// columns are visited in groups of G: the group's values of U and V are
+// loaded once into registers, the block sums
+//   t1_q = sum over Y rows of V(r,q) x(r),   t2_q = sum over X rows of U(r,q) x(r)
+// are formed (below), and the same registers are then used for y_X += U t1
+// and y_Y += V t2.  Every factor value is read from HBM exactly once.
+//
+// The 2G sums of a warp are reduced by halving exchanges: at each of the
+// first log2(2G) steps a lane keeps half of its values and adds the other
+// half received from its partner, so that after them lane L holds one
+// column's partial (column L >> (5 - log2 2G)); the remaining steps are plain
+// butterflies.  Warps then combine through shared memory in warp order.
+// ---------------------------------------------------------------------------
+template <class F>
+__device__ __forceinline__ F fac_zero();
+template <>
+__device__ __forceinline__ double fac_zero<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ float fac_zero<float>() { return 0.f; }
+template <>
+__device__ __forceinline__ float2 fac_zero<float2>() { return make_float2(0.f, 0.f); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 fac_zero<__nv_bfloat16>() {
+  return __float2bfloat16_rn(0.f);
+}
+
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
+// v[NV] per lane -> the warp total of column (lane >> (5 - log2 NV)), returned
+template <class A, int NV>
+__device__ __forceinline__ typename A::val warp_reduce_scatter(typename A::val (&v)[NV],
+                                                               int lane) {
+  using V = typename A::val;
+  constexpr int LG = ilog2c(NV);
+#pragma unroll
+  for (int st = 0; st < LG; ++st) {
+    const int o = 16 >> st;
+    const int M = NV >> st;  // values still held
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < M / 2; ++j) {
+      const V mine = up ? v[j + M / 2] : v[j];
+      const V other = up ? v[j] : v[j + M / 2];
+      v[j] = A::add(mine, shfl_val(other, o));
+    }
+  }
+  V r = v[0];
+#pragma unroll
+  for (int o = 16 >> LG; o > 0; o >>= 1) r = A::add(r, shfl_val(r, o));
+  return r;
+}
+
+template <class A, int T, int RM, int G>
+__global__ void __launch_bounds__(T)
+    k_pairg(ArgsV2 P, const int2* __restrict__ work, const typename A::val* __restrict__ xt,
+            typename A::val* __restrict__ ppart) {
+  using V = typename A::val;
+  using F = typename A::fac;
+  using Acc = typename A::acc;
+  constexpr int NW = T / 32;
+  constexpr int NV = 2 * G;              // sums per group (power of two)
+  constexpr int SH = 5 - ilog2c(NV);     // lane >> SH = column held after the scatter
+  __shared__ V red[2][NW > 1 ? NW : 1][NV];
+  __shared__ V tot[2][NV];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int2 wk = work[blockIdx.x];
+  const LevelV2& L = P.lev[wk.x];
+  const PairMeta PM = L.meta[wk.y];
+  const int m = PM.m, n = PM.n, k = PM.k;
+  const int64_t lm = ldpad(m), ln = ldpad(n);
+  const F* Ug = reinterpret_cast<const F*>(L.fac) + PM.foff;
+  const F* Vg = Ug + lm * k;
+  V xX[RM], xY[RM];
+  Acc yX[RM], yY[RM];
+#pragma unroll
+  for (int a = 0; a < RM; ++a) {
+    const int i = tid + a * T;
+    xX[a] = i < m ? xt[PM.xs + i] : A::vzero();
+    xY[a] = i < n ? xt[PM.ys + i] : A::vzero();
+    yX[a] = A::zero();
+    yY[a] = A::zero();
+  }
+  int par = 0;
+  for (int q0 = 0; q0 < k; q0 += G) {
+    F u[RM][G], v[RM][G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const bool qok = q0 + g < k;
+      const F* uc = Ug + (int64_t)(q0 + g) * lm;
+      const F* vc = Vg + (int64_t)(q0 + g) * ln;
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        const int i = tid + a * T;
+        u[a][g] = (qok && i < m) ? uc[i] : fac_zero<F>();
+        v[a][g] = (qok && i < n) ? vc[i] : fac_zero<F>();
+      }
+    }
+    // s[g] = partial t1_{q0+g} (V), s[G+g] = partial t2_{q0+g} (U)
+    V s[NV];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      Acc a1 = A::zero(), a2 = A::zero();
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        A::fma(a1, A::ld(v[a][g]), xY[a]);
+        A::fma(a2, A::ld(u[a][g]), xX[a]);
+      }
+      s[g] = A::fin(a1);
+      s[G + g] = A::fin(a2);
+    }
+    const V mine = warp_reduce_scatter<A, NV>(s, lane);
+    V t[NV];
+    if (NW == 1) {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) t[c] = shfl_idx(mine, c << SH);
+    } else {
+      if ((lane & ((1 << SH) - 1)) == 0) red[par][warp][lane >> SH] = mine;
+      __syncthreads();
+      if (tid < NV) {
+        V acc = red[par][0][tid];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) acc = A::add(acc, red[par][w][tid]);
+        tot[par][tid] = acc;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < NV; ++c) t[c] = tot[par][c];
+      par ^= 1;
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        A::fma(yX[a], A::ld(u[a][g]), t[g]);      // U with t1
+        A::fma(yY[a], A::ld(v[a][g]), t[G + g]);  // V with t2
+      }
+  }
+  V* outx = ppart + PM.ppx;
+  V* outy = ppart + PM.ppy;
+#pragma unroll
+  for (int a = 0; a < RM; ++a) {
+    const int i = tid + a * T;
+    if (i < m) outx[i] = A::fin(yX[a]);
+    if (i < n) outy[i] = A::fin(yY[a]);
   }
 }
 
@@ -730,7 +888,6 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMemcpy(V.d_red, red.data(), sizeof(int64_t) * red.size(), cudaMemcpyHostToDevice));
   // single-read levels: pair mode (one block per pair, partials for both
   // sides) or box mode (one warp per row box, partials for the column side)
-  std::vector<int2> pw_big, pw_small, bw_big;
   std::vector<BoxWork> bw;
   int64_t pbase = 0;
   for (int l = 1; l <= kappa; ++l) V.lmode[l] = l < V.lfuse ? LMODE_TWO : LMODE_PAIR;
@@ -761,8 +918,6 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMemcpy(L.d_ppoff, pp.data(), sizeof(int64_t) * (2 * np + 2), cudaMemcpyHostToDevice));
     if (V.lmode[l] == LMODE_PAIR) {
       if (mc <= kSmallPair) V.lpair_small = std::min(V.lpair_small, l);
-      for (int64_t p = 0; p < np; ++p)
-        if (L.h_rank[p] > 0) (mc <= kSmallPair ? pw_small : pw_big).push_back(make_int2(l, (int)p));
     } else {
       std::vector<int64_t> prow(((int64_t)1 << (2 * l)) + 1);
       H2D_CK(cudaMemcpy(prow.data(), L.d_prow, sizeof(int64_t) * prow.size(),
@@ -807,21 +962,34 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMalloc(&L.d_meta, sizeof(PairMeta) * np));
     H2D_CK(cudaMemcpy(L.d_meta, meta.data(), sizeof(PairMeta) * np, cudaMemcpyHostToDevice));
   }
-  V.npw_big = (int64_t)pw_big.size();
-  V.npw_small = (int64_t)pw_small.size();
+  // pair-mode work lists, one per level
+  for (int l = V.lfuse; l <= kappa; ++l) {
+    if (V.lmode[l] != LMODE_PAIR) continue;
+    Level& L = h->lev[l];
+    StageLevel& G = V.stg[l];
+    const int64_t np = L.npairs;
+    const int sh = 2 * (kappa - l);
+    std::vector<int32_t> px(np), py(np);
+    if (np) {
+      H2D_CK(cudaMemcpy(px.data(), L.d_px, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
+      H2D_CK(cudaMemcpy(py.data(), L.d_py, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
+    }
+    auto cnt = [&](int32_t b) {
+      return h->h_leaf_off[(int64_t)(b + 1) << sh] - h->h_leaf_off[(int64_t)b << sh];
+    };
+    std::vector<int2> wl;
+    for (int64_t p = 0; p < np; ++p) {
+      if (L.h_rank[p] <= 0) continue;
+      wl.push_back(make_int2(l, (int)p));
+      G.max_rows = (int)std::max<int64_t>(G.max_rows, std::max(cnt(px[p]), cnt(py[p])));
+    }
+    G.nwork = (int64_t)wl.size();
+    H2D_CK(cudaMalloc(&G.d_work, sizeof(int2) * std::max<int64_t>(G.nwork, 1)));
+    if (G.nwork)
+      H2D_CK(cudaMemcpy(G.d_work, wl.data(), sizeof(int2) * G.nwork, cudaMemcpyHostToDevice));
+  }
   V.nbw = (int64_t)bw.size();
-  V.nbw_big = (int64_t)bw_big.size();
-  H2D_CK(cudaMalloc(&V.d_bw_big, sizeof(int2) * std::max<int64_t>(V.nbw_big, 1)));
-  if (V.nbw_big)
-    H2D_CK(cudaMemcpy(V.d_bw_big, bw_big.data(), sizeof(int2) * V.nbw_big, cudaMemcpyHostToDevice));
-  H2D_CK(cudaMalloc(&V.d_pw_big, sizeof(int2) * std::max<int64_t>(V.npw_big, 1)));
-  H2D_CK(cudaMalloc(&V.d_pw_small, sizeof(int2) * std::max<int64_t>(V.npw_small, 1)));
   H2D_CK(cudaMalloc(&V.d_bw, sizeof(BoxWork) * std::max<int64_t>(V.nbw, 1)));
-  if (V.npw_big)
-    H2D_CK(cudaMemcpy(V.d_pw_big, pw_big.data(), sizeof(int2) * V.npw_big, cudaMemcpyHostToDevice));
-  if (V.npw_small)
-    H2D_CK(cudaMemcpy(V.d_pw_small, pw_small.data(), sizeof(int2) * V.npw_small,
-                      cudaMemcpyHostToDevice));
   if (V.nbw) H2D_CK(cudaMemcpy(V.d_bw, bw.data(), sizeof(BoxWork) * V.nbw, cudaMemcpyHostToDevice));
   // pair-mode values of partial results need zero for pairs of rank 0
   V.zero_partials = false;
@@ -856,13 +1024,61 @@ int scratch_v2(hodlr2d* h, int nrhs) {
   V.scratch_nrhs = 0;
   const int64_t n = h->n;
   // every element is 8 bytes (double, or a float pair)
-  H2D_CK(cudaMalloc(&V.d_xt, 8 * n * nrhs));
+  H2D_CK(cudaMalloc(&V.d_xt, 8 * n * nrhs + 16));  // + bulk-copy slack
   H2D_CK(cudaMalloc(&V.d_yl, 8 * n * nrhs * (h->kappa + 1)));
   H2D_CK(cudaMalloc(&V.d_ppart, 8 * V.pstride * nrhs));
   H2D_CK(cudaMalloc(&V.d_part, 8 * std::max<int64_t>(V.proj_partials, 1) * nrhs));
   H2D_CK(cudaMalloc(&V.d_t, 8 * std::max<int64_t>(h->t_total, 1) * nrhs));
   V.scratch_nrhs = nrhs;
   return HODLR2D_OK;
+}
+
+// Launchers of the pair-mode levels: k_pairg (each factor value read once)
+// for one right-hand side, block size by the level's largest box; k_pair for
+// binary64 sums (its shuffle-free second phase suits the slow binary64 pipe)
+// and for several right-hand sides.
+template <class A>
+static int launch_pair_plain(const StageLevel& G, const ArgsV2& P, const typename A::val* xt,
+                             typename A::val* ppart, cudaStream_t st) {
+  if (G.max_rows <= kSmallPair)
+    k_pair<A, 64><<<(unsigned)G.nwork, 64, 0, st>>>(P, G.d_work, xt, ppart);
+  else
+    k_pair<A, 256><<<(unsigned)G.nwork, 256, 0, st>>>(P, G.d_work, xt, ppart);
+  H2D_CK(cudaGetLastError());
+  return HODLR2D_OK;
+}
+
+template <class A>
+static int launch_pair_reg(const StageLevel& G, const ArgsV2& P, const typename A::val* xt,
+                           typename A::val* ppart, cudaStream_t st) {
+  const int mr = G.max_rows;
+  const unsigned nb = (unsigned)G.nwork;
+  if (mr <= 128)
+    k_pairg<A, 32, 4, 4><<<nb, 32, 0, st>>>(P, G.d_work, xt, ppart);
+  else if (mr <= 256)
+    k_pairg<A, 64, 4, 4><<<nb, 64, 0, st>>>(P, G.d_work, xt, ppart);
+  else if (mr <= 384)
+    k_pairg<A, 128, 3, 4><<<nb, 128, 0, st>>>(P, G.d_work, xt, ppart);
+  else if (mr <= 1280)
+    k_pairg<A, 256, 5, 2><<<nb, 256, 0, st>>>(P, G.d_work, xt, ppart);
+  else if (mr <= 2560)
+    k_pairg<A, 512, 5, 2><<<nb, 512, 0, st>>>(P, G.d_work, xt, ppart);
+  else
+    return launch_pair_plain<A>(G, P, xt, ppart, st);
+  H2D_CK(cudaGetLastError());
+  return HODLR2D_OK;
+}
+
+template <class A>
+static int launch_pairs(hodlr2d* h, int l, const ArgsV2& P, const typename A::val* xt,
+                        typename A::val* ppart, cudaStream_t st) {
+  const StageLevel& G = h->v2.stg[l];
+  if constexpr (std::is_same<typename A::acc, double>::value)
+    return launch_pair_plain<A>(G, P, xt, ppart, st);
+  else if (P.nrhs == 1)
+    return launch_pair_reg<A>(G, P, xt, ppart, st);
+  else
+    return launch_pair_plain<A>(G, P, xt, ppart, st);
 }
 
 template <class A>
@@ -938,28 +1154,16 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   }
   H2D_CK(cudaEventRecord(V.ev_near, sn));
   if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, sf));
-  if (V.npw_big) {
-    int64_t vals = 0;
-    for (int l = V.lfuse; l <= h->kappa; ++l)
-      if (V.lmode[l] == LMODE_PAIR && l < V.lpair_small) vals += h->lev[l].nstored;
-    PhaseScope ps(h, 6, 1, fs * vals, sf);
-    if (kPairSmem > 48 * 1024)
-      H2D_CK(cudaFuncSetAttribute(k_pair<A, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kPairSmem));
-    k_pair<A, 256><<<(unsigned)V.npw_big, 256, kPairSmem, sf>>>(P, V.d_pw_big, xt, ppart);
+  for (int l = V.lfuse; l <= h->kappa; ++l) {
+    if (V.lmode[l] != LMODE_PAIR || V.stg[l].nwork == 0) continue;
+    PhaseScope ps(h, l < V.lpair_small ? 6 : 8, 1, fs * h->lev[l].nstored, sf);
+    H2D_TRY(launch_pairs<A>(h, l, P, xt, ppart, sf));
   }
-  if (V.npw_small) {
-    int64_t vals = 0;
-    for (int l = V.lfuse; l <= h->kappa; ++l)
-      if (V.lmode[l] == LMODE_PAIR && l >= V.lpair_small) vals += h->lev[l].nstored;
-    PhaseScope ps(h, 8, 1, fs * vals, sf);
-    k_pair<A, 64><<<(unsigned)V.npw_small, 64, 0, sf>>>(P, V.d_pw_small, xt, ppart);
-  }
-  if (V.nbw || V.nbw_big) {
+  if (V.nbw) {
     int64_t vals = 0;
     for (int l = V.lfuse; l <= h->kappa; ++l)
       if (V.lmode[l] == LMODE_BOX) vals += h->lev[l].nstored;
-    PhaseScope ps(h, 7, (V.nbw ? 1 : 0) + (V.nbw_big ? 1 : 0), fs * vals, sf);
+    PhaseScope ps(h, 7, 1, fs * vals, sf);
     if (V.nbw)
       k_box<A><<<(unsigned)((V.nbw + kBoxWarps - 1) / kBoxWarps), 32 * kBoxWarps, 0, sf>>>(
           P, V.d_bw, V.nbw, xt, yl, ppart);
@@ -993,7 +1197,7 @@ int prepare_df32(hodlr2d* h) {
     Level& L = h->lev[l];
     if (L.d_fac_mode[HODLR2D_MODE_DF32]) continue;
     const int64_t nv = std::max<int64_t>(L.nvalues, 1);
-    H2D_CK(cudaMalloc(&L.d_fac_mode[HODLR2D_MODE_DF32], 8 * nv));
+    H2D_CK(cudaMalloc(&L.d_fac_mode[HODLR2D_MODE_DF32], 8 * nv + 16));  // + bulk-copy slack
     if (L.nvalues)
       k_to_ff<<<(unsigned)((L.nvalues + 255) / 256), 256, 0, h->stream>>>(
           L.d_fac, reinterpret_cast<float2*>(L.d_fac_mode[HODLR2D_MODE_DF32]), L.nvalues);
@@ -1038,7 +1242,7 @@ int prepare_low(hodlr2d* h, int mode) {
     if (L.d_fac_mode[mode]) continue;
     const int64_t nv = std::max<int64_t>(L.nvalues, 1);
     const int64_t es = mode == HODLR2D_MODE_F32 ? 4 : 2;
-    H2D_CK(cudaMalloc(&L.d_fac_mode[mode], es * nv));
+    H2D_CK(cudaMalloc(&L.d_fac_mode[mode], es * nv + 16));  // + bulk-copy slack
     if (!L.nvalues) continue;
     const unsigned g = (unsigned)((L.nvalues + 255) / 256);
     if (mode == HODLR2D_MODE_F32)
@@ -1074,10 +1278,7 @@ void free_v2(hodlr2d* h) {
   cudaFree(V.d_red);
   cudaFree(V.d_wtask);
   cudaFree(V.d_sideq);
-  cudaFree(V.d_pw_big);
-  cudaFree(V.d_pw_small);
   cudaFree(V.d_bw);
-  cudaFree(V.d_bw_big);
   cudaFree(V.d_leaf_of);
   cudaFree(V.d_xt);
   cudaFree(V.d_yl);
@@ -1088,6 +1289,7 @@ void free_v2(hodlr2d* h) {
   cudaFree(V.d_yf);
   cudaFree(V.d_x32);
   cudaFree(V.d_y32);
+  for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) cudaFree(V.stg[l].d_work);
   if (V.s_near) cudaStreamDestroy(V.s_near);
   if (V.s_far) cudaStreamDestroy(V.s_far);
   if (V.ev_in) cudaEventDestroy(V.ev_in);

@@ -253,15 +253,17 @@ def test_full_size_sampled_rows(h2d, oracle):
 
 
 @pytest.mark.parametrize("name,n,kind,a,leaf,eps", CASES)
-def test_p1_df32_same_factors(h2d, oracle, name, n, kind, a, leaf, eps):
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_p1_df32_same_factors(h2d, oracle, name, n, kind, a, leaf, eps, nrhs):
     """The float-float product on the oracle's factors equals the oracle's
-    Alg. 2 product to <= 1e-12 (binary64-level accuracy)."""
+    Alg. 2 product to <= 1e-12 (binary64-level accuracy).  One right-hand
+    side runs the register pair kernel, two the two-read pair kernel."""
     pts = inputs.uniform(n, seed=0)
     o = oracle.Oracle(pts, oracle.kernel(kind, a), leaf, eps)
     g = h2d.HODLR2D(pts, h2d.kernel(kind, a), leaf, eps, compress=False)
     g.import_factors(*o.export_factors())
     g.prepare("df32")
-    x = inputs.rhs(n, 2, seed=1)
+    x = inputs.rhs(n, nrhs, seed=1)
     y_o = o.matvec(x)
     y_g = g.matvec(torch.from_numpy(np.ascontiguousarray(x)).cuda(), mode="df32").cpu().numpy()
     assert rel(y_g, y_o) <= 1e-12
@@ -280,6 +282,33 @@ def test_df32_f64_agree_and_deterministic(h2d):
     assert rel(a.cpu().numpy(), c.cpu().numpy()) <= 1e-12
 
 
+@pytest.mark.parametrize("n", [6000, 20000, 65536])
+def test_register_pair_kernel_block_sizes(h2d, oracle, n):
+    """One right-hand side in the float-float, binary32 and bfloat16 modes
+    runs the register pair kernel; these sizes give pair-mode levels whose
+    largest boxes select its 512-, 256-, 128- and 32-thread forms.  Checked
+    against the oracle's product on the same factors (P1) and against the
+    same mode with two equal right-hand sides, which takes the two-read
+    pair kernel."""
+    pts = inputs.uniform(n, seed=3)
+    kind, a, leaf, eps = "imq", 1.0 / np.sqrt(n), 64, 1e-10
+    o = oracle.Oracle(pts, oracle.kernel(kind, a), leaf, eps)
+    g = h2d.HODLR2D(pts, h2d.kernel(kind, a), leaf, eps, compress=False)
+    g.import_factors(*o.export_factors())
+    x = inputs.rhs(n, seed=4)
+    y_o = o.matvec(x)
+    xd = torch.from_numpy(x).cuda()
+    x2 = torch.stack([xd, xd], dim=1)
+    for mode, bound, bound2 in (("df32", 1e-12, 1e-13), ("f32", 5e-6, 1e-6), ("bf16", 2e-2, 1e-6)):
+        g.prepare(mode)
+        y1 = g.matvec(xd, mode=mode)
+        y2 = g.matvec(x2, mode=mode)
+        assert rel(y1.cpu().numpy(), y_o) <= bound, mode
+        assert torch.equal(y2[:, 0], y2[:, 1])
+        assert rel(y1.cpu().numpy(), y2[:, 0].cpu().numpy()) <= bound2, mode
+        assert torch.equal(y1, g.matvec(xd, mode=mode))  # deterministic
+
+
 def test_df32_full_size_sampled_rows(h2d, oracle):
     n, eps = 1 << 20, 1e-8
     pts = inputs.uniform(n, seed=0)
@@ -295,8 +324,9 @@ def test_df32_full_size_sampled_rows(h2d, oracle):
     assert rel(y[rows], yd) <= 50 * eps
 
 
-def test_gmres_df32_refinement(h2d, oracle):
-    """Iterative refinement: F64 residuals, float-float inner products."""
+def test_gmres_df32(h2d, oracle):
+    """GMRES with float-float products (binary64-level accuracy, no
+    refinement loop); restarting from the solution costs one product."""
     n = 3000
     pts = inputs.uniform(n, seed=2)
     lam = inputs.rhs(n, seed=9)
@@ -307,6 +337,8 @@ def test_gmres_df32_refinement(h2d, oracle):
     x, it, rr, code = g.gmres(torch.from_numpy(f).cuda(), tol=1e-10, inner_mode="df32")
     assert code == 0 and rr <= 1e-10
     assert rel(x.cpu().numpy(), lam) <= 1e-8
+    x2, it2, rr2, code2 = g.gmres(torch.from_numpy(f).cuda(), x0=x, tol=1e-10, inner_mode="df32")
+    assert code2 == 0 and it2 == 1 and torch.equal(x2, x)
 
 
 @pytest.mark.parametrize("mode,bound", [("f32", 5e-6), ("bf16", 2e-2)])
