@@ -35,7 +35,8 @@ namespace h2d {
 #endif
 constexpr int kFuseRows = H2D_FUSE_ROWS;  // largest box handled by the single-read kernels
 constexpr int kSmallPair = 256;   // boxes up to this size: 64-thread pair blocks
-constexpr int kChunk2 = 256;      // row chunk of the two-pass levels (8 rows per lane)
+constexpr int kChunk2 = 256;      // rows of one expansion task of the two-pass levels
+constexpr int kChunkP = 512;      // rows of one projection task (16 per lane)
 constexpr int kNearRhs = 4;       // right-hand sides per near-field pass
 
 struct LevelV2 {
@@ -323,15 +324,17 @@ __device__ __forceinline__ __nv_bfloat16 fac_zero<__nv_bfloat16>() {
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
 
-// v[NV] per lane -> the warp total of column (lane >> (5 - log2 NV)), returned
-template <class A, int NV>
+// v[NV] per lane -> the total over the W-lane group (W a power of two, W >=
+// NV) of column ((lane % W) >> (log2 W - log2 NV)), returned
+template <class A, int NV, int W = 32>
 __device__ __forceinline__ typename A::val warp_reduce_scatter(typename A::val (&v)[NV],
                                                                int lane) {
   using V = typename A::val;
   constexpr int LG = ilog2c(NV);
+  static_assert(NV <= W, "one value per lane at least");
 #pragma unroll
   for (int st = 0; st < LG; ++st) {
-    const int o = 16 >> st;
+    const int o = (W / 2) >> st;
     const int M = NV >> st;  // values still held
     const bool up = (lane & o) != 0;
 #pragma unroll
@@ -343,7 +346,7 @@ __device__ __forceinline__ typename A::val warp_reduce_scatter(typename A::val (
   }
   V r = v[0];
 #pragma unroll
-  for (int o = 16 >> LG; o > 0; o >>= 1) r = A::add(r, shfl_val(r, o));
+  for (int o = (W / 2) >> LG; o > 0; o >>= 1) r = A::add(r, shfl_val(r, o));
   return r;
 }
 
@@ -367,6 +370,7 @@ __global__ void __launch_bounds__(T)
   const int64_t lm = ldpad(m), ln = ldpad(n);
   const F* Ug = reinterpret_cast<const F*>(L.fac) + PM.foff;
   const F* Vg = Ug + lm * k;
+  const int mn = max(m, n);
   V xX[RM], xY[RM];
   Acc yX[RM], yY[RM];
 #pragma unroll
@@ -398,10 +402,11 @@ __global__ void __launch_bounds__(T)
     for (int g = 0; g < G; ++g) {
       Acc a1 = A::zero(), a2 = A::zero();
 #pragma unroll
-      for (int a = 0; a < RM; ++a) {
-        A::fma(a1, A::ld(v[a][g]), xY[a]);
-        A::fma(a2, A::ld(u[a][g]), xX[a]);
-      }
+      for (int a = 0; a < RM; ++a)  // row groups past the box are skipped (block-uniform)
+        if (a * T < mn) {
+          A::fma(a1, A::ld(v[a][g]), xY[a]);
+          A::fma(a2, A::ld(u[a][g]), xX[a]);
+        }
       s[g] = A::fin(a1);
       s[G + g] = A::fin(a2);
     }
@@ -427,16 +432,111 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
     for (int g = 0; g < G; ++g)
 #pragma unroll
-      for (int a = 0; a < RM; ++a) {
-        A::fma(yX[a], A::ld(u[a][g]), t[g]);      // U with t1
-        A::fma(yY[a], A::ld(v[a][g]), t[G + g]);  // V with t2
-      }
+      for (int a = 0; a < RM; ++a)
+        if (a * T < mn) {
+          A::fma(yX[a], A::ld(u[a][g]), t[g]);      // U with t1
+          A::fma(yY[a], A::ld(v[a][g]), t[G + g]);  // V with t2
+        }
   }
   V* outx = ppart + PM.ppx;
   V* outy = ppart + PM.ppy;
 #pragma unroll
   for (int a = 0; a < RM; ++a) {
     const int i = tid + a * T;
+    if (i < m) outx[i] = A::fin(yX[a]);
+    if (i < n) outy[i] = A::fin(yY[a]);
+  }
+}
+
+// Sub-warp form of k_pairg for the finest levels (boxes of <= kBoxRows
+// points): S lanes per pair, 32 / S pairs per warp, rows t, t + S, ... (at
+// most RM) of X and Y per lane.  The column loop runs to the largest rank of
+// the warp's pairs; the sums reduce within each S-lane group.
+template <class A, int S, int RM, int G>
+__global__ void __launch_bounds__(128)
+    k_pairs(ArgsV2 P, const int2* __restrict__ work, int64_t nwork,
+            const typename A::val* __restrict__ xt, typename A::val* __restrict__ ppart) {
+  using V = typename A::val;
+  using F = typename A::fac;
+  using Acc = typename A::acc;
+  constexpr int NV = 2 * G;
+  constexpr int SH = ilog2c(S) - ilog2c(NV);  // (lane % S) >> SH = column after the scatter
+  const int lane = threadIdx.x & 31;
+  const int sl = lane & (S - 1), gb = lane & ~(S - 1);
+  const int64_t w = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / S) +
+                    lane / S;
+  int m = 0, n = 0, k = 0;
+  PairMeta PM{};
+  const F* Ug = nullptr;
+  if (w < nwork) {
+    const int2 wk = work[w];
+    const LevelV2& L = P.lev[wk.x];
+    PM = L.meta[wk.y];
+    m = PM.m;
+    n = PM.n;
+    k = PM.k;
+    Ug = reinterpret_cast<const F*>(L.fac) + PM.foff;
+  }
+  const int kw = __reduce_max_sync(0xffffffffu, k);  // columns the warp visits
+  const int mnw = __reduce_max_sync(0xffffffffu, max(m, n));  // rows the warp visits
+  const int64_t lm = ldpad(m), ln = ldpad(n);
+  const F* Vg = Ug + lm * k;
+  V xX[RM], xY[RM];
+  Acc yX[RM], yY[RM];
+#pragma unroll
+  for (int a = 0; a < RM; ++a) {
+    const int i = sl + a * S;
+    xX[a] = i < m ? xt[PM.xs + i] : A::vzero();
+    xY[a] = i < n ? xt[PM.ys + i] : A::vzero();
+    yX[a] = A::zero();
+    yY[a] = A::zero();
+  }
+  for (int q0 = 0; q0 < kw; q0 += G) {
+    F u[RM][G], v[RM][G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const bool qok = q0 + g < k;
+      const F* uc = Ug + (int64_t)(q0 + g) * lm;
+      const F* vc = Vg + (int64_t)(q0 + g) * ln;
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        const int i = sl + a * S;
+        u[a][g] = (qok && i < m) ? uc[i] : fac_zero<F>();
+        v[a][g] = (qok && i < n) ? vc[i] : fac_zero<F>();
+      }
+    }
+    V s[NV];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      Acc a1 = A::zero(), a2 = A::zero();
+#pragma unroll
+      for (int a = 0; a < RM; ++a)  // row groups past the warp's boxes are skipped
+        if (a * S < mnw) {
+          A::fma(a1, A::ld(v[a][g]), xY[a]);
+          A::fma(a2, A::ld(u[a][g]), xX[a]);
+        }
+      s[g] = A::fin(a1);
+      s[G + g] = A::fin(a2);
+    }
+    const V mine = warp_reduce_scatter<A, NV, S>(s, lane);
+    V t[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) t[c] = shfl_idx(mine, gb + (c << SH));
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+      for (int a = 0; a < RM; ++a)
+        if (a * S < mnw) {
+          A::fma(yX[a], A::ld(u[a][g]), t[g]);      // U with t1
+          A::fma(yY[a], A::ld(v[a][g]), t[G + g]);  // V with t2
+        }
+  }
+  if (w >= nwork) return;
+  V* outx = ppart + PM.ppx;
+  V* outy = ppart + PM.ppy;
+#pragma unroll
+  for (int a = 0; a < RM; ++a) {
+    const int i = sl + a * S;
     if (i < m) outx[i] = A::fin(yX[a]);
     if (i < n) outy[i] = A::fin(yY[a]);
   }
@@ -482,6 +582,7 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
   PairMeta* pm = pm_all[warp];
   const BoxWork wk = work[wid];
   const int l = wk.level;
+  if (P.lmode[l] != LMODE_BOX) return;  // this level runs as pairs in this product
   const LevelV2& L = P.lev[l];
   const int32_t xs = wk.xs, m = wk.m;
   const int64_t lm = ldpad(m);
@@ -592,7 +693,7 @@ __global__ void __launch_bounds__(256)
             typename A::val* __restrict__ part) {
   using V = typename A::val;
   using Acc = typename A::acc;
-  constexpr int R = kChunk2 / 32;
+  constexpr int R = kChunkP / 32;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= nwarps) return;
@@ -766,6 +867,15 @@ __global__ void k_near_f64(const double* __restrict__ xs, const double* __restri
                            int kappa, KernelParams kp, const double* __restrict__ xt, int64_t n,
                            int nrhs, double* __restrict__ yout);
 
+// A box level runs as pairs (sub-warp register kernel) for one right-hand
+// side in the binary32 and bfloat16 modes, and in float-float when its boxes
+// exceed 48 points (below that the box kernel is faster there); else with
+// the box kernel.
+static bool box_as_pairs(const hodlr2d* h, int l, int nrhs, int mode) {
+  if (nrhs != 1 || mode == HODLR2D_MODE_F64) return false;
+  return mode != HODLR2D_MODE_DF32 || h->v2.stg[l].max_rows > 48;
+}
+
 static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
   ArgsV2 P;
   for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) {
@@ -774,7 +884,10 @@ static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
     P.lev[l] = LevelV2{L.d_px, L.d_py, L.d_rank, L.d_foff, L.d_prow, L.d_ppoff,
                        L.d_toff, L.d_ent_off, L.d_ent, fac, L.d_meta};
   }
-  for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) P.lmode[l] = h->v2.lmode[l];
+  for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) {
+    P.lmode[l] = h->v2.lmode[l];
+    if (P.lmode[l] == LMODE_BOX && box_as_pairs(h, l, nrhs, mode)) P.lmode[l] = LMODE_PAIR;
+  }
   P.leaf_off = h->d_leaf_off;
   P.kappa = h->kappa;
   P.lfuse = h->v2.lfuse;
@@ -824,13 +937,13 @@ int plan_v2(hodlr2d* h) {
         const int32_t rows = side == 0 ? cnt(py[p]) : cnt(px[p]);
         const int64_t first = (int64_t)proj.size();
         if (k > 0)
-          for (int32_t r0 = 0; r0 < rows; r0 += kChunk2) {
+          for (int32_t r0 = 0; r0 < rows; r0 += kChunkP) {
             ProjTask T;
             T.level = l;
             T.side = side;
             T.pair = p;
             T.r0 = r0;
-            T.nr = std::min(kChunk2, rows - r0);
+            T.nr = std::min(kChunkP, rows - r0);
             T.out = out;
             T.mat = L.h_foff[p] + (side == 0 ? ldpad(cnt(px[p])) * k : 0);
             T.ld = (int32_t)ldpad(rows);
@@ -908,8 +1021,8 @@ int plan_v2(hodlr2d* h) {
     };
     std::vector<int64_t> pp(2 * np + 2);
     for (int64_t p = 0; p < np; ++p) {
-      pp[2 * p] = pbase;
-      if (V.lmode[l] == LMODE_PAIR) pbase += cnt(px[p]);
+      pp[2 * p] = pbase;  // pair layout also for box levels (they may run as pairs)
+      pbase += cnt(px[p]);
       pp[2 * p + 1] = pbase;
       pbase += cnt(py[p]);
     }
@@ -962,9 +1075,8 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMalloc(&L.d_meta, sizeof(PairMeta) * np));
     H2D_CK(cudaMemcpy(L.d_meta, meta.data(), sizeof(PairMeta) * np, cudaMemcpyHostToDevice));
   }
-  // pair-mode work lists, one per level
+  // pair work lists, one per single-read level
   for (int l = V.lfuse; l <= kappa; ++l) {
-    if (V.lmode[l] != LMODE_PAIR) continue;
     Level& L = h->lev[l];
     StageLevel& G = V.stg[l];
     const int64_t np = L.npairs;
@@ -994,9 +1106,8 @@ int plan_v2(hodlr2d* h) {
   // pair-mode values of partial results need zero for pairs of rank 0
   V.zero_partials = false;
   for (int l = V.lfuse; l <= kappa; ++l)
-    if (V.lmode[l] == LMODE_PAIR)
-      for (int64_t p = 0; p < h->lev[l].npairs; ++p)
-        if (h->lev[l].h_rank[p] == 0) V.zero_partials = true;
+    for (int64_t p = 0; p < h->lev[l].npairs; ++p)
+      if (h->lev[l].h_rank[p] == 0) V.zero_partials = true;
   // leaf of every tree position
   const int64_t nleaf = (int64_t)1 << (2 * kappa);
   H2D_CK(cudaMalloc(&V.d_leaf_of, sizeof(int32_t) * h->n));
@@ -1053,7 +1164,13 @@ static int launch_pair_reg(const StageLevel& G, const ArgsV2& P, const typename 
                            typename A::val* ppart, cudaStream_t st) {
   const int mr = G.max_rows;
   const unsigned nb = (unsigned)G.nwork;
-  if (mr <= 128)
+  if (mr <= 48)  // 16 pairs per 128-thread block
+    k_pairs<A, 8, 6, 4><<<(unsigned)((G.nwork + 15) / 16), 128, 0, st>>>(P, G.d_work, G.nwork,
+                                                                         xt, ppart);
+  else if (mr <= 64)  // 8 pairs per block
+    k_pairs<A, 16, 4, 4><<<(unsigned)((G.nwork + 7) / 8), 128, 0, st>>>(P, G.d_work, G.nwork,
+                                                                        xt, ppart);
+  else if (mr <= 128)
     k_pairg<A, 32, 4, 4><<<nb, 32, 0, st>>>(P, G.d_work, xt, ppart);
   else if (mr <= 256)
     k_pairg<A, 64, 4, 4><<<nb, 64, 0, st>>>(P, G.d_work, xt, ppart);
@@ -1155,18 +1272,18 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   H2D_CK(cudaEventRecord(V.ev_near, sn));
   if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, sf));
   for (int l = V.lfuse; l <= h->kappa; ++l) {
-    if (V.lmode[l] != LMODE_PAIR || V.stg[l].nwork == 0) continue;
-    PhaseScope ps(h, l < V.lpair_small ? 6 : 8, 1, fs * h->lev[l].nstored, sf);
+    if (P.lmode[l] != LMODE_PAIR || V.stg[l].nwork == 0) continue;
+    const int phase = V.lmode[l] == LMODE_BOX ? 7 : l < V.lpair_small ? 6 : 8;
+    PhaseScope ps(h, phase, 1, fs * h->lev[l].nstored, sf);
     H2D_TRY(launch_pairs<A>(h, l, P, xt, ppart, sf));
   }
-  if (V.nbw) {
-    int64_t vals = 0;
-    for (int l = V.lfuse; l <= h->kappa; ++l)
-      if (V.lmode[l] == LMODE_BOX) vals += h->lev[l].nstored;
-    PhaseScope ps(h, 7, 1, fs * vals, sf);
-    if (V.nbw)
-      k_box<A><<<(unsigned)((V.nbw + kBoxWarps - 1) / kBoxWarps), 32 * kBoxWarps, 0, sf>>>(
-          P, V.d_bw, V.nbw, xt, yl, ppart);
+  int64_t box_vals = 0;  // levels left to the box kernel in this product
+  for (int l = V.lfuse; l <= h->kappa; ++l)
+    if (P.lmode[l] == LMODE_BOX) box_vals += h->lev[l].nstored;
+  if (V.nbw && box_vals) {
+    PhaseScope ps(h, 7, 1, fs * box_vals, sf);
+    k_box<A><<<(unsigned)((V.nbw + kBoxWarps - 1) / kBoxWarps), 32 * kBoxWarps, 0, sf>>>(
+        P, V.d_bw, V.nbw, xt, yl, ppart);
   }
   H2D_CK(cudaEventRecord(V.ev_far, sf));
   H2D_CK(cudaStreamWaitEvent(s, V.ev_near, 0));
