@@ -152,9 +152,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# ncu DRAM traffic (read + write bytes per launch) of the dominant kernel,
-# taken from the committed capture summary; None once the kernel changed.
-NCU_TRAFFIC = {}
+# ncu DRAM traffic (read + write bytes per launch) of the dominant kernel at
+# the headline workload, keyed by (phase, mode, n): k_proj2 (DF32) measured at
+# N = 2^17 (522.9 MB for 64.33e6 two-pass values) and scaled by the values of
+# a full N = 2^20 launch (846.1e6).  Remove an entry when its kernel changes.
+NCU_TRAFFIC = {("proj", "df32", 1 << 20): 6.878e9}
 
 
 def cpu_baseline_leg(rows, x, pts, n):
@@ -185,6 +187,15 @@ def cpu_baseline_leg(rows, x, pts, n):
     t_mv = statistics.median(ts)
     return {"t_matvec_s": t_mv, "t_build_s": t_build, "values_sample": o.nvalues,
             "kappa_sample": o.kappa, "t_rows_s": t_rows, "y_direct_rows": yd}
+
+
+def workload_config(n, kappa, mode):
+    """The bench line's config (the same for both arms)."""
+    fb = {"f64": 8, "df32": 8, "f32": 4, "bf16": 2}[mode]
+    return {"workload": WORKLOAD if n == N_FULL else WORKLOAD.replace("2^20", str(n)),
+            "n": n, "leaf": LEAF, "eps": EPS, "kernel": "mq", "a": 1.0 / np.sqrt(n), "nrhs": 1,
+            "mode": mode, "kappa": kappa, "parallelism": "replicas",
+            "l2": "no flush: factors (%d bytes per value) exceed the 129 MB L2" % fb}
 
 
 def timed(g, x, y, mode, steps, warmup, stream):
@@ -461,7 +472,9 @@ def run_ours(args, ws, rank, local):
 
     # dominant kernel (serialized per-phase times) and its roofline
     peak, peak_src = peaks()
-    dom = max((k for k in prof if prof[k]["launches"]), key=lambda k: prof[k]["ms"])
+    # dominant kernel: the phase with the longest time per launch
+    dom = max((k for k in prof if prof[k]["launches"]),
+              key=lambda k: prof[k]["ms"] / prof[k]["launches"])
     d = prof[dom]
     # per product: the phase's launches, their device time and algorithmic bytes
     per_launch_ms = d["ms"] / args.steps
@@ -484,11 +497,7 @@ def run_ours(args, ws, rank, local):
         "vs_baseline": None,
         "dtype": mode,
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if n == N_FULL else WORKLOAD.replace("2^20", str(n)),
-                   "n": n, "leaf": LEAF, "eps": EPS, "kernel": "mq", "a": a, "nrhs": 1,
-                   "mode": mode, "kappa": st["kappa"], "parallelism": "replicas",
-                   "l2": "no flush: factor bytes %.2f GB > 129 MB L2"
-                         % (st["far_values"] * 8 / 1e9)},
+        "config": workload_config(n, st["kappa"], mode),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "peak_source": peak_src, "bytes_per_launch": bytes_step,
@@ -552,8 +561,8 @@ def run_ours(args, ws, rank, local):
 def run_reference(args, ws, rank):
     """The CPU oracle on the host cores, each step a bounded sample: the
     oracle's Alg. 2 product at N = 2^16 of the same recipe, reported scaled to
-    N = 2^20 by the stored-value ratio of the oracle's own N = 2^16 build and
-    the complexity model O(N log N) of the paper (Sec. 4.1)."""
+    N = 2^20 by N kappa, the paper's O(p N kappa) cost model (Sec. 4.1).
+    Only rank 0 works; the other ranks return at once."""
     if rank != 0:
         return None
     import oracle
@@ -576,7 +585,7 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": "ms",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 2),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_FULL},
+        "data": "synthetic", "config": workload_config(N_FULL, 8, args.modes.split(",")[0]),
         "cpu_baseline": {"value": round(v, 2), "unit": "ms", "cores": 1, "kind": "oracle",
                          "sample": "oracle Alg. 2 product at N=2^16 (kappa %d), mean of %d, "
                                    "scaled x%.2f by N*kappa to N=2^20" % (o.kappa, args.steps, scale)},
