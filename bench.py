@@ -232,6 +232,7 @@ def extra_gmres_nrhs(pkg, inputs, n, stream):
     lam = torch.from_numpy(inputs.rhs(n, seed=2)).cuda()
     f = g.matvec(lam, mode="f64")
     gm = {}
+    g.gmres(f, tol=1e-2, restart=50, maxit=50)  # allocates the Krylov workspace (untimed)
     for mode in ("f64", "f32", "bf16", "df32"):
         if mode != "f64":
             g.prepare(mode)
@@ -396,12 +397,107 @@ def extra_learned(pkg, inputs, stream, n_big):
     return res
 
 
+def direct_rows_gpu(pts, kind, a, diag, x, rows, chunk=1024):
+    """Exact product rows (binary64, plain torch on the GPU) for the error
+    checks of the paper replays: phi of Sec. 5.1 / Eq. ker, diagonal diag."""
+    import torch
+    P = torch.from_numpy(pts).cuda()
+    X = torch.from_numpy(x).cuda()
+    out = torch.empty(len(rows), dtype=torch.float64, device="cuda")
+    rows_t = torch.from_numpy(np.asarray(rows)).cuda()
+    for c0 in range(0, len(rows), chunk):
+        ri = rows_t[c0:c0 + chunk]
+        dx = P[ri, 0:1] - P[:, 0]
+        dy = P[ri, 1:2] - P[:, 1]
+        r = torch.sqrt(dx * dx + dy * dy)
+        del dx, dy
+        if kind == "inv_r":
+            K = 1.0 / r
+        elif kind == "phi1":
+            K = torch.where(r >= a, torch.log(r) / np.log(a), (r * torch.log(r) - 1.0) /
+                            (a * np.log(a) - 1.0))
+        else:  # phi2
+            K = torch.where(r >= a, a / r, r / a)
+        K[torch.arange(len(ri), device="cuda"), ri] = diag
+        out[c0:c0 + chunk] = K @ X
+    return out.cpu().numpy()
+
+
+def extra_paper_replay(pkg, inputs, stream):
+    """The paper's own workloads on the GPU, next to its printed tables
+    (context): Sec. 5.1 (1/r, Chebyshev grid, N_max 500, eps 1e-12; r_m,
+    stored GB, build time, product time, max componentwise error over 2048
+    sampled rows) and Sec. 5.2 (phi_1 and phi_2, a = 0.001, beta = N, GMRES
+    to 1e-10; build, solve time, solution error)."""
+    import torch
+    out = {"sec51_inv_r": {}, "sec52_rbf": {}}
+    rng = np.random.default_rng(11)
+    for m in (100, 300, 500):
+        n = m * m
+        pts = inputs.chebyshev_grid(m)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = pkg.HODLR2D(pts, pkg.kernel("inv_r"), 500, 1e-12, root=ROOT_BOX)
+        torch.cuda.synchronize()
+        t_i = time.perf_counter() - t0
+        g.set_stream(stream)
+        g.prepare("df32")
+        st = g.stats()
+        psi = rng.uniform(0.0, 1.0, n)
+        rows = np.sort(rng.choice(n, min(n, 2048), replace=False))
+        b = direct_rows_gpu(pts, "inv_r", 0.0, 0.0, psi, rows)
+        xd = torch.from_numpy(psi).cuda()
+        res = {"kappa": st["kappa"], "r_m": st["max_rank"],
+               "stored_gb": round((st["far_values"] + st["near_entries"]) * 8 / 1e9, 3),
+               "factor_gb": round(st["far_values"] * 8 / 1e9, 3),
+               "cr": round(st["compression_ratio"], 4), "t_i_s": round(t_i, 3)}
+        for mode in ("f64", "df32"):
+            y = torch.empty_like(xd)
+            ms = timed(g, xd, y, mode, 5, 2, stream)
+            yb = y.cpu().numpy()[rows]
+            res[mode] = {"ms": round(ms, 3),
+                         "eps_r": float(np.max(np.abs(yb - b) / np.abs(b)))}
+        out["sec51_inv_r"][str(n)] = res
+        g.close()
+    m = 500
+    n = m * m
+    pts = inputs.chebyshev_grid(m)
+    lam = rng.standard_normal(n)
+    for kind in ("phi1", "phi2"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = pkg.HODLR2D(pts, pkg.kernel(kind, 0.001, diag=float(n)), 500, 1e-12, root=ROOT_BOX)
+        torch.cuda.synchronize()
+        t_i = time.perf_counter() - t0
+        g.set_stream(stream)
+        g.prepare("df32")
+        st = g.stats()
+        f = torch.from_numpy(direct_rows_gpu(pts, kind, 0.001, float(n), lam,
+                                             np.arange(n))).cuda()
+        res = {"kappa": st["kappa"], "r_m": st["max_rank"], "cr": round(st["compression_ratio"], 4),
+               "t_i_s": round(t_i, 3)}
+        g.gmres(f, tol=1e-2, restart=50, maxit=50)  # Krylov workspace (untimed)
+        for mode in ("f64", "df32"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xs, it, rr, code = g.gmres(f, tol=1e-10, restart=50, maxit=2000, inner_mode=mode)
+            torch.cuda.synchronize()
+            res[mode] = {"t_g_s": round(time.perf_counter() - t0, 4), "products": it,
+                         "relres": rr, "converged": code == 0,
+                         "rel_err_solution": float(np.linalg.norm(xs.cpu().numpy() - lam)
+                                                   / np.linalg.norm(lam))}
+        out["sec52_rbf"][kind + "_n" + str(n)] = res
+        g.close()
+    return out
+
+
 def extras(pkg, inputs, n, n_learned):
     """Secondary measurements on one GPU (each section timed on its own)."""
     import torch
     stream = torch.cuda.current_stream()
     out = {}
     for name, fn in (("rbf_system", lambda: extra_gmres_nrhs(pkg, inputs, n, stream)),
+                     ("paper_replay", lambda: extra_paper_replay(pkg, inputs, stream)),
                      ("batch_point_sets", lambda: extra_batch(pkg, inputs, stream)),
                      ("learned_rank_log", lambda: extra_learned(pkg, inputs, stream, n_learned))):
         t0 = time.perf_counter()
