@@ -91,7 +91,10 @@ struct StageLevel {
 
 struct V2Plan {
   bool ready = false;
-  int lfuse = 1;   // first level handled by the fused kernel
+  int lfuse = 1;   // first single-read level
+  int ldual = 1;   // first two-pass level that also has a pair plan (<= lfuse)
+  // two-pass task counts of the levels below ldual (prefixes of the lists)
+  int64_t nproj_pre = 0, nexp_pre = 0, proj_partials_pre = 0, ntsum_pre = 0;
   ProjTask* d_proj = nullptr;
   ExpTask* d_exp = nullptr;
   int64_t* d_red = nullptr;

@@ -37,6 +37,10 @@ constexpr int kFuseRows = H2D_FUSE_ROWS;  // largest box handled by the single-r
 constexpr int kSmallPair = 256;   // boxes up to this size: 64-thread pair blocks
 constexpr int kChunk2 = 256;      // rows of one expansion task of the two-pass levels
 constexpr int kChunkP = 512;      // rows of one projection task (16 per lane)
+// Two-pass levels whose boxes hold at most kDualRows points also get a pair
+// plan; binary32 / bfloat16 products with one right-hand side run them as
+// pairs (each factor value read once) instead of in two passes.
+constexpr int kDualRows = 512 * 9;
 constexpr int kNearRhs = 4;       // right-hand sides per near-field pass
 
 struct LevelV2 {
@@ -876,6 +880,13 @@ static bool box_as_pairs(const hodlr2d* h, int l, int nrhs, int mode) {
   return mode != HODLR2D_MODE_DF32 || h->v2.stg[l].max_rows > 48;
 }
 
+// The dual levels [ldual, lfuse) run as pairs for one right-hand side in the
+// binary32 and bfloat16 modes (the 512 x 9 register form holds their boxes),
+// else in two passes.
+static bool dual_as_pairs(int nrhs, int mode) {
+  return nrhs == 1 && (mode == HODLR2D_MODE_F32 || mode == HODLR2D_MODE_BF16);
+}
+
 static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
   ArgsV2 P;
   for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) {
@@ -887,6 +898,7 @@ static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
   for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) {
     P.lmode[l] = h->v2.lmode[l];
     if (P.lmode[l] == LMODE_BOX && box_as_pairs(h, l, nrhs, mode)) P.lmode[l] = LMODE_PAIR;
+    if (l >= h->v2.ldual && l < h->v2.lfuse && dual_as_pairs(nrhs, mode)) P.lmode[l] = LMODE_PAIR;
   }
   P.leaf_off = h->d_leaf_off;
   P.kappa = h->kappa;
@@ -914,12 +926,22 @@ int plan_v2(hodlr2d* h) {
     if (maxcount(l) <= kFuseRows) { V.lfuse = l; break; }
   for (int l = V.lfuse; l <= kappa; ++l)  // the pair kernel holds at most kPairKmax terms
     if (h->lev[l].max_rank > kPairKmax) V.lfuse = l + 1;
+  V.ldual = V.lfuse;  // two-pass levels that may also run as pairs: [ldual, lfuse)
+  while (V.ldual > 1 && maxcount(V.ldual - 1) <= kDualRows &&
+         h->lev[V.ldual - 1].max_rank <= kPairKmax)
+    --V.ldual;
   // two-pass task lists for levels < lfuse
   std::vector<ProjTask> proj;
   std::vector<ExpTask> exps;
   std::vector<int64_t> red;
-  int64_t out = 0;
+  int64_t out = 0, sides_pre = 0;
   for (int l = 1; l < V.lfuse; ++l) {
+    if (l == V.ldual) {  // the task lists are level-ordered: record the prefix below ldual
+      V.nproj_pre = (int64_t)proj.size();
+      V.nexp_pre = (int64_t)exps.size();
+      V.proj_partials_pre = out;
+      sides_pre = (int64_t)red.size() / 2;
+    }
     Level& L = h->lev[l];
     const int64_t np = L.npairs;
     const int sh = 2 * (kappa - l);
@@ -965,6 +987,12 @@ int plan_v2(hodlr2d* h) {
   }
   V.nproj = (int64_t)proj.size();
   V.nexp = (int64_t)exps.size();
+  if (V.ldual == V.lfuse) {
+    V.nproj_pre = V.nproj;
+    V.nexp_pre = V.nexp;
+    V.proj_partials_pre = out;
+    sides_pre = (int64_t)red.size() / 2;
+  }
   {
     std::vector<int32_t> wt(std::max<int64_t>(out, 1));
     for (int64_t t = 0; t < V.nproj; ++t) {
@@ -972,7 +1000,9 @@ int plan_v2(hodlr2d* h) {
       for (int q = 0; q < k; ++q) wt[proj[t].out + q] = (int32_t)t;
     }
     std::vector<int64_t> sq;
+    V.ntsum_pre = -1;
     for (int64_t sd = 0; sd < (int64_t)red.size() / 2; ++sd) {
+      if (sd == sides_pre) V.ntsum_pre = (int64_t)sq.size() / 2;
       if (red[2 * sd + 1] == 0) continue;
       const ProjTask& T0 = proj[red[2 * sd]];
       const int k = h->lev[T0.level].h_rank[T0.pair];
@@ -982,6 +1012,7 @@ int plan_v2(hodlr2d* h) {
       }
     }
     V.ntsum = (int64_t)sq.size() / 2;
+    if (V.ntsum_pre < 0) V.ntsum_pre = V.ntsum;
     H2D_CK(cudaMalloc(&V.d_wtask, sizeof(int32_t) * wt.size()));
     H2D_CK(cudaMemcpy(V.d_wtask, wt.data(), sizeof(int32_t) * wt.size(), cudaMemcpyHostToDevice));
     H2D_CK(cudaMalloc(&V.d_sideq, sizeof(int64_t) * std::max<size_t>(sq.size(), 2)));
@@ -1005,12 +1036,12 @@ int plan_v2(hodlr2d* h) {
   int64_t pbase = 0;
   for (int l = 1; l <= kappa; ++l) V.lmode[l] = l < V.lfuse ? LMODE_TWO : LMODE_PAIR;
   V.lpair_small = kappa + 1;
-  for (int l = V.lfuse; l <= kappa; ++l) {
+  for (int l = V.ldual; l <= kappa; ++l) {
     Level& L = h->lev[l];
     const int64_t np = L.npairs;
     const int sh = 2 * (kappa - l);
     const int64_t mc = maxcount(l);
-    V.lmode[l] = mc <= kBoxRows ? LMODE_BOX : LMODE_PAIR;
+    if (l >= V.lfuse) V.lmode[l] = mc <= kBoxRows ? LMODE_BOX : LMODE_PAIR;
     std::vector<int32_t> px(np), py(np);
     if (np) {
       H2D_CK(cudaMemcpy(px.data(), L.d_px, sizeof(int32_t) * np, cudaMemcpyDeviceToHost));
@@ -1029,7 +1060,9 @@ int plan_v2(hodlr2d* h) {
     pp[2 * np] = pp[2 * np + 1] = pbase;
     H2D_CK(cudaMalloc(&L.d_ppoff, sizeof(int64_t) * (2 * np + 2)));
     H2D_CK(cudaMemcpy(L.d_ppoff, pp.data(), sizeof(int64_t) * (2 * np + 2), cudaMemcpyHostToDevice));
-    if (V.lmode[l] == LMODE_PAIR) {
+    if (V.lmode[l] == LMODE_TWO) {
+      // dual level: pair plan only
+    } else if (V.lmode[l] == LMODE_PAIR) {
       if (mc <= kSmallPair) V.lpair_small = std::min(V.lpair_small, l);
     } else {
       std::vector<int64_t> prow(((int64_t)1 << (2 * l)) + 1);
@@ -1075,8 +1108,8 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMalloc(&L.d_meta, sizeof(PairMeta) * np));
     H2D_CK(cudaMemcpy(L.d_meta, meta.data(), sizeof(PairMeta) * np, cudaMemcpyHostToDevice));
   }
-  // pair work lists, one per single-read level
-  for (int l = V.lfuse; l <= kappa; ++l) {
+  // pair work lists, one per single-read or dual level
+  for (int l = V.ldual; l <= kappa; ++l) {
     Level& L = h->lev[l];
     StageLevel& G = V.stg[l];
     const int64_t np = L.npairs;
@@ -1105,7 +1138,7 @@ int plan_v2(hodlr2d* h) {
   if (V.nbw) H2D_CK(cudaMemcpy(V.d_bw, bw.data(), sizeof(BoxWork) * V.nbw, cudaMemcpyHostToDevice));
   // pair-mode values of partial results need zero for pairs of rank 0
   V.zero_partials = false;
-  for (int l = V.lfuse; l <= kappa; ++l)
+  for (int l = V.ldual; l <= kappa; ++l)
     for (int64_t p = 0; p < h->lev[l].npairs; ++p)
       if (h->lev[l].h_rank[p] == 0) V.zero_partials = true;
   // leaf of every tree position
@@ -1162,24 +1195,29 @@ static int launch_pair_plain(const StageLevel& G, const ArgsV2& P, const typenam
 template <class A>
 static int launch_pair_reg(const StageLevel& G, const ArgsV2& P, const typename A::val* xt,
                            typename A::val* ppart, cudaStream_t st) {
+  // column group of the small-box forms: 4, or 2 for float-float (registers)
+  constexpr bool b32 = sizeof(typename A::acc) == 4;
+  constexpr int GS = b32 ? 4 : 2;
   const int mr = G.max_rows;
   const unsigned nb = (unsigned)G.nwork;
   if (mr <= 48)  // 16 pairs per 128-thread block
-    k_pairs<A, 8, 6, 4><<<(unsigned)((G.nwork + 15) / 16), 128, 0, st>>>(P, G.d_work, G.nwork,
-                                                                         xt, ppart);
+    k_pairs<A, 8, 6, GS><<<(unsigned)((G.nwork + 15) / 16), 128, 0, st>>>(P, G.d_work, G.nwork,
+                                                                          xt, ppart);
   else if (mr <= 64)  // 8 pairs per block
-    k_pairs<A, 16, 4, 4><<<(unsigned)((G.nwork + 7) / 8), 128, 0, st>>>(P, G.d_work, G.nwork,
-                                                                        xt, ppart);
+    k_pairs<A, 16, 4, GS><<<(unsigned)((G.nwork + 7) / 8), 128, 0, st>>>(P, G.d_work, G.nwork,
+                                                                         xt, ppart);
   else if (mr <= 128)
-    k_pairg<A, 32, 4, 4><<<nb, 32, 0, st>>>(P, G.d_work, xt, ppart);
+    k_pairg<A, 32, 4, GS><<<nb, 32, 0, st>>>(P, G.d_work, xt, ppart);
   else if (mr <= 256)
-    k_pairg<A, 64, 4, 4><<<nb, 64, 0, st>>>(P, G.d_work, xt, ppart);
+    k_pairg<A, 64, 4, GS><<<nb, 64, 0, st>>>(P, G.d_work, xt, ppart);
   else if (mr <= 384)
-    k_pairg<A, 128, 3, 4><<<nb, 128, 0, st>>>(P, G.d_work, xt, ppart);
+    k_pairg<A, 128, 3, GS><<<nb, 128, 0, st>>>(P, G.d_work, xt, ppart);
   else if (mr <= 1280)
     k_pairg<A, 256, 5, 2><<<nb, 256, 0, st>>>(P, G.d_work, xt, ppart);
   else if (mr <= 2560)
     k_pairg<A, 512, 5, 2><<<nb, 512, 0, st>>>(P, G.d_work, xt, ppart);
+  else if (b32 && mr <= kDualRows)
+    k_pairg<A, 512, 9, 2><<<nb, 512, 0, st>>>(P, G.d_work, xt, ppart);
   else
     return launch_pair_plain<A>(G, P, xt, ppart, st);
   H2D_CK(cudaGetLastError());
@@ -1245,33 +1283,38 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
           h->d_perm, h->d_leaf_off, h->kappa, (int64_t)nleaf, V.kf32,
           reinterpret_cast<const float*>(xt), n, nrhs, reinterpret_cast<float*>(yl));
   }
+  // two-pass levels: all of [1, lfuse), or only [1, ldual) when the dual
+  // levels run as pairs (the task lists are level-ordered prefixes)
+  const bool dual = dual_as_pairs(nrhs, mode);
+  const int l2end = dual ? V.ldual : V.lfuse;
+  const int64_t nproj = dual ? V.nproj_pre : V.nproj;
+  const int64_t npart = dual ? V.proj_partials_pre : V.proj_partials;
+  const int64_t ntsum = dual ? V.ntsum_pre : V.ntsum;
+  const int64_t nexp = dual ? V.nexp_pre : V.nexp;
   int64_t two_pass_vals = 0;
-  for (int l = 1; l < V.lfuse; ++l) two_pass_vals += h->lev[l].nstored;
-  if (V.nproj) {
+  for (int l = 1; l < l2end; ++l) two_pass_vals += h->lev[l].nstored;
+  if (nproj) {
     {
-      PhaseScope ps(h, 2, 1, fs * two_pass_vals + vs * V.proj_partials * nrhs);
-      const int64_t thr = V.proj_partials * 32;  // one warp per (task, column)
+      PhaseScope ps(h, 2, 1, fs * two_pass_vals + vs * npart * nrhs);
+      const int64_t thr = npart * 32;  // one warp per (task, column)
       k_proj2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
-          P, V.d_proj, V.d_wtask, V.proj_partials, xt, reinterpret_cast<Val*>(V.d_part));
+          P, V.d_proj, V.d_wtask, npart, xt, reinterpret_cast<Val*>(V.d_part));
     }
     {
-      PhaseScope ps(h, 3, 1, vs * (V.proj_partials + h->t_total) * nrhs);
-      const int64_t thr = V.ntsum * 32;
+      PhaseScope ps(h, 3, 1, vs * (npart + h->t_total) * nrhs);
+      const int64_t thr = ntsum * 32;
       k_tsum2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
-          P, V.d_proj, V.d_red, V.d_sideq, V.ntsum, reinterpret_cast<const Val*>(V.d_part),
+          P, V.d_proj, V.d_red, V.d_sideq, ntsum, reinterpret_cast<const Val*>(V.d_part),
           reinterpret_cast<Val*>(V.d_t));
     }
   }
-  if (V.lfuse > 1) {
-    {
-      PhaseScope ps(h, 4, 1, fs * two_pass_vals + vb * (V.lfuse - 1));
-      k_exp2<A><<<(unsigned)V.nexp, 256, 0, s>>>(P, V.d_exp, reinterpret_cast<const Val*>(V.d_t),
-                                                 yl);
-    }
+  if (nexp) {
+    PhaseScope ps(h, 4, 1, fs * two_pass_vals + vb * (l2end - 1));
+    k_exp2<A><<<(unsigned)nexp, 256, 0, s>>>(P, V.d_exp, reinterpret_cast<const Val*>(V.d_t), yl);
   }
   H2D_CK(cudaEventRecord(V.ev_near, sn));
   if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, sf));
-  for (int l = V.lfuse; l <= h->kappa; ++l) {
+  for (int l = V.ldual; l <= h->kappa; ++l) {
     if (P.lmode[l] != LMODE_PAIR || V.stg[l].nwork == 0) continue;
     const int phase = V.lmode[l] == LMODE_BOX ? 7 : l < V.lpair_small ? 6 : 8;
     PhaseScope ps(h, phase, 1, fs * h->lev[l].nstored, sf);

@@ -30,15 +30,16 @@ def torchrun(args, timeout=300):
 def test_max_over_ranks_and_barrier(tmp_path):
     script = tmp_path / "ranks.py"
     script.write_text(
+        "import sys\n"
         "import bench\n"
         "ws, rank, local = bench.dist_setup()\n"
         "v = bench.max_over_ranks(10.0 * (rank + 1), ws)\n"
         "bench.barrier(ws)\n"
-        "print('RANK', rank, ws, v, flush=True)\n")
-    r = torchrun([str(script)])
+        "open(sys.argv[1] + '/rank%d.txt' % rank, 'w').write('%d %d %s' % (rank, ws, v))\n")
+    r = torchrun([str(script), str(tmp_path)])
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = sorted(l for l in r.stdout.splitlines() if l.startswith("RANK"))
-    assert lines == ["RANK 0 2 20.0", "RANK 1 2 20.0"]
+    got = sorted((tmp_path / ("rank%d.txt" % i)).read_text() for i in range(2))
+    assert got == ["0 2 20.0", "1 2 20.0"]
 
 
 def test_reference_arm_prints_once():
