@@ -177,6 +177,8 @@ struct KernelFF {
   KernelParams p64;
 };
 
+// Entry phi(|x_i - x_j|) of the kernel; gi and gj identify the two points
+// (any bijection of the original index) and decide the diagonal.
 __device__ __forceinline__ float2 entry_ff(const KernelFF& k, float2 xi, float2 yi, int64_t gi,
                                            float2 xj, float2 yj, int64_t gj) {
   if (gi == gj) return k.diag;

@@ -137,10 +137,12 @@ struct NearF32 {  // binary32 points, entries and sums (mixed form)
   }
 };
 
+// at least 10 blocks (40 warps) per SM: the float-float entry chains need
+// the occupancy more than registers (measured 0.85 -> 0.68 ms at N = 2^20)
 template <class NP>
-__global__ void __launch_bounds__(32 * kNearWarps)
+__global__ void __launch_bounds__(32 * kNearWarps, 10)
     k_near_warp(const typename NP::pt* __restrict__ xf, const typename NP::pt* __restrict__ yf,
-                const int64_t* __restrict__ perm, const int32_t* __restrict__ leaf_off, int kappa,
+                const int32_t* __restrict__ leaf_off, int kappa,
                 int64_t nleaf, typename NP::K kp, const typename NP::A::val* __restrict__ xt,
                 int64_t n, int nrhs, typename NP::A::val* __restrict__ yout) {
   using A = typename NP::A;
@@ -187,7 +189,6 @@ __global__ void __launch_bounds__(32 * kNearWarps)
     const bool act = t < m;
     const int64_t it = s0 + (act ? t : 0);
     const Pt xi = xf[it], yi = yf[it];
-    const int64_t gi = perm[it];
     for (int c0 = 0; c0 < nrhs; c0 += kNearRhs) {
       const int nc = min(kNearRhs, nrhs - c0);
       typename A::acc acc[kNearRhs];
@@ -199,9 +200,11 @@ __global__ void __launch_bounds__(32 * kNearWarps)
         // first source of this box whose running index is = h (mod G)
         int j = (h - sidx) % G;
         if (j < 0) j += G;
+        // the diagonal is found by tree position, a bijection of the
+        // original index
         for (; j < len; j += G) {
           const int64_t js = sb[q] + j;
-          const Val kij = NP::entry(kp, xi, yi, gi, xf[js], yf[js], perm[js]);
+          const Val kij = NP::entry(kp, xi, yi, it, xf[js], yf[js], js);
 #pragma unroll
           for (int r = 0; r < kNearRhs; ++r)
             if (r < nc) A::fma(acc[r], kij, xt[(int64_t)(c0 + r) * n + js]);
@@ -1216,9 +1219,9 @@ static int launch_pair_reg(const StageLevel& G, const ArgsV2& P, const typename 
     k_pairg<A, 256, 5, 2><<<nb, 256, 0, st>>>(P, G.d_work, xt, ppart);
   else if (mr <= 2560)
     k_pairg<A, 512, 5, 2><<<nb, 512, 0, st>>>(P, G.d_work, xt, ppart);
-  else if (b32 && mr <= kDualRows)
-    k_pairg<A, 512, 9, 2><<<nb, 512, 0, st>>>(P, G.d_work, xt, ppart);
-  else
+  else if (mr <= kDualRows && b32) {
+    if constexpr (b32) k_pairg<A, 512, 9, 2><<<nb, 512, 0, st>>>(P, G.d_work, xt, ppart);
+  } else
     return launch_pair_plain<A>(G, P, xt, ppart, st);
   H2D_CK(cudaGetLastError());
   return HODLR2D_OK;
@@ -1274,13 +1277,13 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
       k_near_warp<NearDF32><<<(unsigned)((nleaf + kNearWarps - 1) / kNearWarps), 32 * kNearWarps,
                               0, sn>>>(
           reinterpret_cast<const float2*>(V.d_xf), reinterpret_cast<const float2*>(V.d_yf),
-          h->d_perm, h->d_leaf_off, h->kappa, (int64_t)nleaf, V.kff,
+          h->d_leaf_off, h->kappa, (int64_t)nleaf, V.kff,
           reinterpret_cast<const float2*>(xt), n, nrhs, reinterpret_cast<float2*>(yl));
     else
       k_near_warp<NearF32><<<(unsigned)((nleaf + kNearWarps - 1) / kNearWarps), 32 * kNearWarps,
                              0, sn>>>(
           reinterpret_cast<const float*>(V.d_x32), reinterpret_cast<const float*>(V.d_y32),
-          h->d_perm, h->d_leaf_off, h->kappa, (int64_t)nleaf, V.kf32,
+          h->d_leaf_off, h->kappa, (int64_t)nleaf, V.kf32,
           reinterpret_cast<const float*>(xt), n, nrhs, reinterpret_cast<float*>(yl));
   }
   // two-pass levels: all of [1, lfuse), or only [1, ldual) when the dual
