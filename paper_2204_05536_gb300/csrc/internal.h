@@ -82,11 +82,16 @@ struct ProjTask {
 
 // Plan and scratch of the second-generation product (product.cu).
 // Pair-mode work of one level: (level, pair) of every stored pair of rank > 0,
-// and the largest box of the level.
-struct StageLevel {
-  int2* d_work = nullptr;
+// sorted into size classes by max(|X|, |Y|) (bounds kPairClassRows), so that
+// each class runs with a block shape fitted to its boxes.
+constexpr int kPairClasses = 9;
+constexpr int kPairClassRows[kPairClasses] = {48, 64, 128, 256, 384, 1280, 2560, 4608, 1 << 30};
+struct PairLevel {
+  int2* d_work = nullptr;              // all classes, class by class
   int64_t nwork = 0;
-  int max_rows = 0;
+  int max_rows = 0;                    // largest box of the level
+  int64_t off[kPairClasses + 1] = {};  // class c: work [off[c], off[c + 1])
+  int cls_rows[kPairClasses] = {};     // largest box of class c
 };
 
 struct V2Plan {
@@ -105,6 +110,8 @@ struct V2Plan {
   int lpair_small = 1 << 20;           // first pair-mode level with 64-thread blocks
   BoxWork* d_bw = nullptr;     // box-mode work, boxes <= 64 points
   int64_t nbw = 0;
+  int2* d_nearw = nullptr;     // near-field work: (leaf, first target), <= 32 targets
+  int64_t nnearw = 0;
   bool zero_partials = false;
   int64_t pstride = 1;
   int32_t* d_leaf_of = nullptr;
@@ -120,7 +127,7 @@ struct V2Plan {
   void* d_x32 = nullptr;  // binary32 coordinates (F32 / BF16 modes)
   void* d_y32 = nullptr;
   KernelF32 kf32{};
-  StageLevel stg[HODLR2D_MAX_LEVELS];
+  PairLevel plev[HODLR2D_MAX_LEVELS];
   // side streams: near field, and the single-read far-field levels
   cudaStream_t s_near = nullptr, s_far = nullptr;
   cudaEvent_t ev_in = nullptr, ev_near = nullptr, ev_far = nullptr;

@@ -142,25 +142,29 @@ struct NearF32 {  // binary32 points, entries and sums (mixed form)
 template <class NP>
 __global__ void __launch_bounds__(32 * kNearWarps, 10)
     k_near_warp(const typename NP::pt* __restrict__ xf, const typename NP::pt* __restrict__ yf,
-                const int32_t* __restrict__ leaf_off, int kappa,
-                int64_t nleaf, typename NP::K kp, const typename NP::A::val* __restrict__ xt,
+                const int32_t* __restrict__ leaf_off, int kappa, const int2* __restrict__ work,
+                int64_t nwork, typename NP::K kp, const typename NP::A::val* __restrict__ xt,
                 int64_t n, int nrhs, typename NP::A::val* __restrict__ yout) {
   using A = typename NP::A;
   using Val = typename A::val;
   using Pt = typename NP::pt;
   const int lane = threadIdx.x & 31;
-  const int64_t bl = (int64_t)blockIdx.x * kNearWarps + (threadIdx.x >> 5);
-  if (bl >= nleaf) return;
-  const uint32_t b = (uint32_t)bl;
-  const int32_t s0 = leaf_off[b], m = leaf_off[b + 1] - s0;
-  if (m == 0) return;
+  const int64_t wi = (int64_t)blockIdx.x * kNearWarps + (threadIdx.x >> 5);
+  if (wi >= nwork) return;
+  // work item: (leaf, first target); a leaf of more than 32 points is split
+  // into items of 32 targets, each against all of the leaf's sources
+  const int2 wk = work[wi];
+  const uint32_t b = (uint32_t)wk.x;
+  const int32_t s0 = leaf_off[b] + wk.y;
+  const int32_t m = min(leaf_off[b + 1] - s0, 32);
+  if (m <= 0) return;
   int cx, cy;
   morton_decode(b, cx, cy);
   const int side = 1 << kappa;
   int32_t sb[5], se[5];
   int ns = 0;
-  sb[0] = s0;
-  se[0] = s0 + m;
+  sb[0] = leaf_off[b];
+  se[0] = leaf_off[b + 1];
   ns = 1;
   uint32_t nb[4];
   int nn = 0;
@@ -880,7 +884,7 @@ __global__ void k_near_f64(const double* __restrict__ xs, const double* __restri
 // the box kernel.
 static bool box_as_pairs(const hodlr2d* h, int l, int nrhs, int mode) {
   if (nrhs != 1 || mode == HODLR2D_MODE_F64) return false;
-  return mode != HODLR2D_MODE_DF32 || h->v2.stg[l].max_rows > 48;
+  return mode != HODLR2D_MODE_DF32 || h->v2.plev[l].max_rows > 48;
 }
 
 // The dual levels [ldual, lfuse) run as pairs for one right-hand side in the
@@ -1114,7 +1118,7 @@ int plan_v2(hodlr2d* h) {
   // pair work lists, one per single-read or dual level
   for (int l = V.ldual; l <= kappa; ++l) {
     Level& L = h->lev[l];
-    StageLevel& G = V.stg[l];
+    PairLevel& G = V.plev[l];
     const int64_t np = L.npairs;
     const int sh = 2 * (kappa - l);
     std::vector<int32_t> px(np), py(np);
@@ -1125,12 +1129,22 @@ int plan_v2(hodlr2d* h) {
     auto cnt = [&](int32_t b) {
       return h->h_leaf_off[(int64_t)(b + 1) << sh] - h->h_leaf_off[(int64_t)b << sh];
     };
-    std::vector<int2> wl;
+    std::vector<int2> cls_work[kPairClasses];
     for (int64_t p = 0; p < np; ++p) {
       if (L.h_rank[p] <= 0) continue;
-      wl.push_back(make_int2(l, (int)p));
-      G.max_rows = (int)std::max<int64_t>(G.max_rows, std::max(cnt(px[p]), cnt(py[p])));
+      const int rows = (int)std::max(cnt(px[p]), cnt(py[p]));
+      int c = 0;
+      while (rows > kPairClassRows[c]) ++c;
+      cls_work[c].push_back(make_int2(l, (int)p));
+      G.cls_rows[c] = std::max(G.cls_rows[c], rows);
+      G.max_rows = std::max(G.max_rows, rows);
     }
+    std::vector<int2> wl;
+    for (int c = 0; c < kPairClasses; ++c) {
+      G.off[c] = (int64_t)wl.size();
+      wl.insert(wl.end(), cls_work[c].begin(), cls_work[c].end());
+    }
+    G.off[kPairClasses] = (int64_t)wl.size();
     G.nwork = (int64_t)wl.size();
     H2D_CK(cudaMalloc(&G.d_work, sizeof(int2) * std::max<int64_t>(G.nwork, 1)));
     if (G.nwork)
@@ -1144,6 +1158,18 @@ int plan_v2(hodlr2d* h) {
   for (int l = V.ldual; l <= kappa; ++l)
     for (int64_t p = 0; p < h->lev[l].npairs; ++p)
       if (h->lev[l].h_rank[p] == 0) V.zero_partials = true;
+  // near-field work items: (leaf, first target), at most 32 targets each
+  {
+    std::vector<int2> nw;
+    const int64_t nl = (int64_t)1 << (2 * kappa);
+    for (int64_t b = 0; b < nl; ++b)
+      for (int32_t t = 0; t < h->h_leaf_off[b + 1] - h->h_leaf_off[b]; t += 32)
+        nw.push_back(make_int2((int)b, t));
+    V.nnearw = (int64_t)nw.size();
+    H2D_CK(cudaMalloc(&V.d_nearw, sizeof(int2) * std::max<int64_t>(V.nnearw, 1)));
+    if (V.nnearw)
+      H2D_CK(cudaMemcpy(V.d_nearw, nw.data(), sizeof(int2) * V.nnearw, cudaMemcpyHostToDevice));
+  }
   // leaf of every tree position
   const int64_t nleaf = (int64_t)1 << (2 * kappa);
   H2D_CK(cudaMalloc(&V.d_leaf_of, sizeof(int32_t) * h->n));
@@ -1180,63 +1206,68 @@ int scratch_v2(hodlr2d* h, int nrhs) {
   return HODLR2D_OK;
 }
 
-// Launchers of the pair-mode levels: k_pairg (each factor value read once)
-// for one right-hand side, block size by the level's largest box; k_pair for
-// binary64 sums (its shuffle-free second phase suits the slow binary64 pipe)
-// and for several right-hand sides.
 template <class A>
-static int launch_pair_plain(const StageLevel& G, const ArgsV2& P, const typename A::val* xt,
-                             typename A::val* ppart, cudaStream_t st) {
-  if (G.max_rows <= kSmallPair)
-    k_pair<A, 64><<<(unsigned)G.nwork, 64, 0, st>>>(P, G.d_work, xt, ppart);
+static int launch_pair_plain(const int2* work, int64_t nw, int rows, const ArgsV2& P,
+                             const typename A::val* xt, typename A::val* ppart, cudaStream_t st) {
+  if (rows <= kSmallPair)
+    k_pair<A, 64><<<(unsigned)nw, 64, 0, st>>>(P, work, xt, ppart);
   else
-    k_pair<A, 256><<<(unsigned)G.nwork, 256, 0, st>>>(P, G.d_work, xt, ppart);
+    k_pair<A, 256><<<(unsigned)nw, 256, 0, st>>>(P, work, xt, ppart);
   H2D_CK(cudaGetLastError());
   return HODLR2D_OK;
 }
 
 template <class A>
-static int launch_pair_reg(const StageLevel& G, const ArgsV2& P, const typename A::val* xt,
-                           typename A::val* ppart, cudaStream_t st) {
+static int launch_pair_reg(const int2* work, int64_t nw, int rows, const ArgsV2& P,
+                           const typename A::val* xt, typename A::val* ppart, cudaStream_t st) {
   // column group of the small-box forms: 4, or 2 for float-float (registers)
   constexpr bool b32 = sizeof(typename A::acc) == 4;
   constexpr int GS = b32 ? 4 : 2;
-  const int mr = G.max_rows;
-  const unsigned nb = (unsigned)G.nwork;
-  if (mr <= 48)  // 16 pairs per 128-thread block
-    k_pairs<A, 8, 6, GS><<<(unsigned)((G.nwork + 15) / 16), 128, 0, st>>>(P, G.d_work, G.nwork,
-                                                                          xt, ppart);
-  else if (mr <= 64)  // 8 pairs per block
-    k_pairs<A, 16, 4, GS><<<(unsigned)((G.nwork + 7) / 8), 128, 0, st>>>(P, G.d_work, G.nwork,
-                                                                         xt, ppart);
-  else if (mr <= 128)
-    k_pairg<A, 32, 4, GS><<<nb, 32, 0, st>>>(P, G.d_work, xt, ppart);
-  else if (mr <= 256)
-    k_pairg<A, 64, 4, GS><<<nb, 64, 0, st>>>(P, G.d_work, xt, ppart);
-  else if (mr <= 384)
-    k_pairg<A, 128, 3, GS><<<nb, 128, 0, st>>>(P, G.d_work, xt, ppart);
-  else if (mr <= 1280)
-    k_pairg<A, 256, 5, 2><<<nb, 256, 0, st>>>(P, G.d_work, xt, ppart);
-  else if (mr <= 2560)
-    k_pairg<A, 512, 5, 2><<<nb, 512, 0, st>>>(P, G.d_work, xt, ppart);
-  else if (mr <= kDualRows && b32) {
-    if constexpr (b32) k_pairg<A, 512, 9, 2><<<nb, 512, 0, st>>>(P, G.d_work, xt, ppart);
+  const unsigned nb = (unsigned)nw;
+  if (rows <= 48)  // 16 pairs per 128-thread block
+    k_pairs<A, 8, 6, GS><<<(unsigned)((nw + 15) / 16), 128, 0, st>>>(P, work, nw, xt, ppart);
+  else if (rows <= 64)  // 8 pairs per block
+    k_pairs<A, 16, 4, GS><<<(unsigned)((nw + 7) / 8), 128, 0, st>>>(P, work, nw, xt, ppart);
+  else if (rows <= 128)
+    k_pairg<A, 32, 4, GS><<<nb, 32, 0, st>>>(P, work, xt, ppart);
+  else if (rows <= 256)
+    k_pairg<A, 64, 4, GS><<<nb, 64, 0, st>>>(P, work, xt, ppart);
+  else if (rows <= 384)
+    k_pairg<A, 128, 3, GS><<<nb, 128, 0, st>>>(P, work, xt, ppart);
+  else if (rows <= 1280)
+    k_pairg<A, 256, 5, 2><<<nb, 256, 0, st>>>(P, work, xt, ppart);
+  else if (rows <= 2560)
+    k_pairg<A, 512, 5, 2><<<nb, 512, 0, st>>>(P, work, xt, ppart);
+  else if (rows <= kDualRows && b32) {
+    if constexpr (b32) k_pairg<A, 512, 9, 2><<<nb, 512, 0, st>>>(P, work, xt, ppart);
   } else
-    return launch_pair_plain<A>(G, P, xt, ppart, st);
+    return launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st);
   H2D_CK(cudaGetLastError());
   return HODLR2D_OK;
 }
 
+// Runs the pairs of level l, one launch per non-empty size class: k_pairg /
+// k_pairs (each factor value read once) for one right-hand side, block shape
+// by the class's largest box; k_pair for binary64 sums (its shuffle-free
+// second phase suits the slow binary64 pipe) and for several right-hand sides.
 template <class A>
 static int launch_pairs(hodlr2d* h, int l, const ArgsV2& P, const typename A::val* xt,
                         typename A::val* ppart, cudaStream_t st) {
-  const StageLevel& G = h->v2.stg[l];
-  if constexpr (std::is_same<typename A::acc, double>::value)
-    return launch_pair_plain<A>(G, P, xt, ppart, st);
-  else if (P.nrhs == 1)
-    return launch_pair_reg<A>(G, P, xt, ppart, st);
-  else
-    return launch_pair_plain<A>(G, P, xt, ppart, st);
+  const PairLevel& G = h->v2.plev[l];
+  for (int c = 0; c < kPairClasses; ++c) {
+    const int64_t nw = G.off[c + 1] - G.off[c];
+    if (nw == 0) continue;
+    const int2* work = G.d_work + G.off[c];
+    const int rows = G.cls_rows[c];
+    if constexpr (std::is_same<typename A::acc, double>::value) {
+      H2D_TRY(launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st));
+    } else if (P.nrhs == 1) {
+      H2D_TRY(launch_pair_reg<A>(work, nw, rows, P, xt, ppart, st));
+    } else {
+      H2D_TRY(launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st));
+    }
+  }
+  return HODLR2D_OK;
 }
 
 template <class A>
@@ -1274,16 +1305,16 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
                                        reinterpret_cast<const double*>(xt), n, nrhs,
                                        reinterpret_cast<double*>(yl));
     else if (mode == HODLR2D_MODE_DF32)
-      k_near_warp<NearDF32><<<(unsigned)((nleaf + kNearWarps - 1) / kNearWarps), 32 * kNearWarps,
-                              0, sn>>>(
+      k_near_warp<NearDF32><<<(unsigned)((V.nnearw + kNearWarps - 1) / kNearWarps),
+                              32 * kNearWarps, 0, sn>>>(
           reinterpret_cast<const float2*>(V.d_xf), reinterpret_cast<const float2*>(V.d_yf),
-          h->d_leaf_off, h->kappa, (int64_t)nleaf, V.kff,
+          h->d_leaf_off, h->kappa, V.d_nearw, V.nnearw, V.kff,
           reinterpret_cast<const float2*>(xt), n, nrhs, reinterpret_cast<float2*>(yl));
     else
-      k_near_warp<NearF32><<<(unsigned)((nleaf + kNearWarps - 1) / kNearWarps), 32 * kNearWarps,
-                             0, sn>>>(
+      k_near_warp<NearF32><<<(unsigned)((V.nnearw + kNearWarps - 1) / kNearWarps),
+                             32 * kNearWarps, 0, sn>>>(
           reinterpret_cast<const float*>(V.d_x32), reinterpret_cast<const float*>(V.d_y32),
-          h->d_leaf_off, h->kappa, (int64_t)nleaf, V.kf32,
+          h->d_leaf_off, h->kappa, V.d_nearw, V.nnearw, V.kf32,
           reinterpret_cast<const float*>(xt), n, nrhs, reinterpret_cast<float*>(yl));
   }
   // two-pass levels: all of [1, lfuse), or only [1, ldual) when the dual
@@ -1318,9 +1349,11 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   H2D_CK(cudaEventRecord(V.ev_near, sn));
   if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, sf));
   for (int l = V.ldual; l <= h->kappa; ++l) {
-    if (P.lmode[l] != LMODE_PAIR || V.stg[l].nwork == 0) continue;
+    if (P.lmode[l] != LMODE_PAIR || V.plev[l].nwork == 0) continue;
     const int phase = V.lmode[l] == LMODE_BOX ? 7 : l < V.lpair_small ? 6 : 8;
-    PhaseScope ps(h, phase, 1, fs * h->lev[l].nstored, sf);
+    int nlaunch = 0;  // one launch per non-empty size class
+    for (int c = 0; c < kPairClasses; ++c) nlaunch += V.plev[l].off[c + 1] > V.plev[l].off[c];
+    PhaseScope ps(h, phase, nlaunch, fs * h->lev[l].nstored, sf);
     H2D_TRY(launch_pairs<A>(h, l, P, xt, ppart, sf));
   }
   int64_t box_vals = 0;  // levels left to the box kernel in this product
@@ -1442,6 +1475,7 @@ void free_v2(hodlr2d* h) {
   cudaFree(V.d_wtask);
   cudaFree(V.d_sideq);
   cudaFree(V.d_bw);
+  cudaFree(V.d_nearw);
   cudaFree(V.d_leaf_of);
   cudaFree(V.d_xt);
   cudaFree(V.d_yl);
@@ -1452,7 +1486,7 @@ void free_v2(hodlr2d* h) {
   cudaFree(V.d_yf);
   cudaFree(V.d_x32);
   cudaFree(V.d_y32);
-  for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) cudaFree(V.stg[l].d_work);
+  for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) cudaFree(V.plev[l].d_work);
   if (V.s_near) cudaStreamDestroy(V.s_near);
   if (V.s_far) cudaStreamDestroy(V.s_far);
   if (V.ev_in) cudaEventDestroy(V.ev_in);

@@ -309,6 +309,24 @@ def test_register_pair_kernel_block_sizes(h2d, oracle, n):
         assert torch.equal(y1, g.matvec(xd, mode=mode))  # deterministic
 
 
+def test_large_leaves_near_field(h2d, oracle):
+    """Leaves of several hundred points (depth forced to 2): the float-float
+    and binary32 near fields split each leaf into 32-target work items."""
+    n = 5000
+    pts = inputs.chebyshev_grid(71)[:n]
+    kind, a, leaf, eps = "mq", 0.01, 64, 1e-10
+    o = oracle.Oracle(pts, oracle.kernel(kind, a), leaf, eps, levels=2)
+    g = h2d.HODLR2D(pts, h2d.kernel(kind, a), leaf, eps, levels=2, compress=False)
+    g.import_factors(*o.export_factors())
+    assert g.stats()["kappa"] == 2
+    x = inputs.rhs(n, seed=6)
+    y_o = o.matvec(x)
+    xd = torch.from_numpy(x).cuda()
+    for mode, bound in (("df32", 1e-12), ("f32", 5e-6)):
+        g.prepare(mode)
+        assert rel(g.matvec(xd, mode=mode).cpu().numpy(), y_o) <= bound, mode
+
+
 def test_df32_full_size_sampled_rows(h2d, oracle):
     n, eps = 1 << 20, 1e-8
     pts = inputs.uniform(n, seed=0)
