@@ -98,8 +98,10 @@ struct V2Plan {
   bool ready = false;
   int lfuse = 1;   // first single-read level
   int ldual = 1;   // first two-pass level that also has a pair plan (<= lfuse)
-  // two-pass task counts of the levels below ldual (prefixes of the lists)
-  int64_t nproj_pre = 0, nexp_pre = 0, proj_partials_pre = 0, ntsum_pre = 0;
+  int l2max = 1;   // two-pass plans exist for levels [1, l2max) (>= lfuse)
+  // two-pass task counts of the levels below l (level-ordered list prefixes)
+  int64_t pre_proj[HODLR2D_MAX_LEVELS + 1] = {}, pre_exp[HODLR2D_MAX_LEVELS + 1] = {};
+  int64_t pre_part[HODLR2D_MAX_LEVELS + 1] = {}, pre_tsum[HODLR2D_MAX_LEVELS + 1] = {};
   ProjTask* d_proj = nullptr;
   ExpTask* d_exp = nullptr;
   int64_t* d_red = nullptr;

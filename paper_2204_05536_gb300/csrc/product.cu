@@ -36,12 +36,16 @@ namespace h2d {
 constexpr int kFuseRows = H2D_FUSE_ROWS;  // largest box handled by the single-read kernels
 constexpr int kSmallPair = 256;   // boxes up to this size: 64-thread pair blocks
 constexpr int kChunk2 = 256;      // rows of one expansion task of the two-pass levels
+constexpr int kExpMaxEnt = 64;    // largest list of a box (15 pairs, two sides, margin)
 constexpr int kChunkP = 512;      // rows of one projection task (16 per lane)
 // Two-pass levels whose boxes hold at most kDualRows points also get a pair
 // plan; binary32 / bfloat16 products with one right-hand side run them as
 // pairs (each factor value read once) instead of in two passes.
 constexpr int kDualRows = 512 * 9;
-constexpr int kNearRhs = 4;       // right-hand sides per near-field pass
+// With several right-hand sides, boxes of more than kMultiRows points run in
+// two passes (each factor value read twice for all of them); smaller ones run
+// with the multi-RHS register pair kernel.
+constexpr int kMultiRows = 256;
 
 struct LevelV2 {
   const int32_t* px;
@@ -137,9 +141,10 @@ struct NearF32 {  // binary32 points, entries and sums (mixed form)
   }
 };
 
-// at least 10 blocks (40 warps) per SM: the float-float entry chains need
-// the occupancy more than registers (measured 0.85 -> 0.68 ms at N = 2^20)
-template <class NP>
+// NRH right-hand sides per pass (each entry evaluated once per pass).  At
+// least 10 blocks (40 warps) per SM: the float-float entry chains need the
+// occupancy more than registers (measured 0.85 -> 0.68 ms at N = 2^20).
+template <class NP, int NRH>
 __global__ void __launch_bounds__(32 * kNearWarps, 10)
     k_near_warp(const typename NP::pt* __restrict__ xf, const typename NP::pt* __restrict__ yf,
                 const int32_t* __restrict__ leaf_off, int kappa, const int2* __restrict__ work,
@@ -193,11 +198,11 @@ __global__ void __launch_bounds__(32 * kNearWarps, 10)
     const bool act = t < m;
     const int64_t it = s0 + (act ? t : 0);
     const Pt xi = xf[it], yi = yf[it];
-    for (int c0 = 0; c0 < nrhs; c0 += kNearRhs) {
-      const int nc = min(kNearRhs, nrhs - c0);
-      typename A::acc acc[kNearRhs];
+    for (int c0 = 0; c0 < nrhs; c0 += NRH) {
+      const int nc = min(NRH, nrhs - c0);
+      typename A::acc acc[NRH];
 #pragma unroll
-      for (int r = 0; r < kNearRhs; ++r) acc[r] = A::zero();
+      for (int r = 0; r < NRH; ++r) acc[r] = A::zero();
       int sidx = 0;  // running index over the concatenated sources
       for (int q = 0; q < ns; ++q) {
         const int32_t len = se[q] - sb[q];
@@ -210,14 +215,14 @@ __global__ void __launch_bounds__(32 * kNearWarps, 10)
           const int64_t js = sb[q] + j;
           const Val kij = NP::entry(kp, xi, yi, it, xf[js], yf[js], js);
 #pragma unroll
-          for (int r = 0; r < kNearRhs; ++r)
+          for (int r = 0; r < NRH; ++r)
             if (r < nc) A::fma(acc[r], kij, xt[(int64_t)(c0 + r) * n + js]);
         }
         sidx += len;
       }
-      Val res[kNearRhs];
+      Val res[NRH];
 #pragma unroll
-      for (int r = 0; r < kNearRhs; ++r) {
+      for (int r = 0; r < NRH; ++r) {
         Val v = A::fin(acc[r]);
         for (int o = tpr; o < 32; o <<= 1) v = A::add(v, shfl_val(v, o));
         res[r] = v;
@@ -456,6 +461,113 @@ __global__ void __launch_bounds__(T)
     const int i = tid + a * T;
     if (i < m) outx[i] = A::fin(yX[a]);
     if (i < n) outy[i] = A::fin(yY[a]);
+  }
+}
+
+// Several right-hand sides: k_pairg with one column per step and NR
+// right-hand sides per pass.  Thread t keeps x and y of its rows (at most RM
+// of X and of Y) for the pass's NR right-hand sides in registers; each column
+// of U and V is loaded once per pass and used for all of them.  The 2 NR
+// sums of a column reduce like k_pairg's.
+template <class A, int T, int RM, int NR>
+__global__ void __launch_bounds__(T)
+    k_pairm(ArgsV2 P, const int2* __restrict__ work, const typename A::val* __restrict__ xt,
+            typename A::val* __restrict__ ppart) {
+  using V = typename A::val;
+  using F = typename A::fac;
+  using Acc = typename A::acc;
+  constexpr int NW = T / 32;
+  constexpr int NV = 2 * NR;
+  constexpr int SH = 5 - ilog2c(NV);
+  __shared__ V red[2][NW > 1 ? NW : 1][NV];
+  __shared__ V tot[2][NV];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int2 wk = work[blockIdx.x];
+  const LevelV2& L = P.lev[wk.x];
+  const PairMeta PM = L.meta[wk.y];
+  const int m = PM.m, n = PM.n, k = PM.k;
+  const int64_t lm = ldpad(m), ln = ldpad(n);
+  const F* Ug = reinterpret_cast<const F*>(L.fac) + PM.foff;
+  const F* Vg = Ug + lm * k;
+  const int mn = max(m, n);
+  int par = 0;
+  for (int c0 = 0; c0 < P.nrhs; c0 += NR) {
+    V xX[RM][NR], xY[RM][NR];
+    Acc yX[RM][NR], yY[RM][NR];
+#pragma unroll
+    for (int a = 0; a < RM; ++a) {
+      const int i = tid + a * T;
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        const bool ok = c0 + c < P.nrhs;
+        const V* xc = xt + (int64_t)(c0 + c) * P.n;
+        xX[a][c] = (ok && i < m) ? xc[PM.xs + i] : A::vzero();
+        xY[a][c] = (ok && i < n) ? xc[PM.ys + i] : A::vzero();
+        yX[a][c] = A::zero();
+        yY[a][c] = A::zero();
+      }
+    }
+    for (int q = 0; q < k; ++q) {
+      F u[RM], v[RM];
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        const int i = tid + a * T;
+        u[a] = i < m ? Ug[(int64_t)q * lm + i] : fac_zero<F>();
+        v[a] = i < n ? Vg[(int64_t)q * ln + i] : fac_zero<F>();
+      }
+      V s[NV];  // s[c] = partial t1 of RHS c (V), s[NR + c] = partial t2 (U)
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        Acc a1 = A::zero(), a2 = A::zero();
+#pragma unroll
+        for (int a = 0; a < RM; ++a)
+          if (a * T < mn) {
+            A::fma(a1, A::ld(v[a]), xY[a][c]);
+            A::fma(a2, A::ld(u[a]), xX[a][c]);
+          }
+        s[c] = A::fin(a1);
+        s[NR + c] = A::fin(a2);
+      }
+      const V mine = warp_reduce_scatter<A, NV>(s, lane);
+      V t[NV];
+      if (NW == 1) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) t[c] = shfl_idx(mine, c << SH);
+      } else {
+        if ((lane & ((1 << SH) - 1)) == 0) red[par][warp][lane >> SH] = mine;
+        __syncthreads();
+        if (tid < NV) {
+          V acc = red[par][0][tid];
+#pragma unroll
+          for (int w = 1; w < NW; ++w) acc = A::add(acc, red[par][w][tid]);
+          tot[par][tid] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < NV; ++c) t[c] = tot[par][c];
+        par ^= 1;
+      }
+#pragma unroll
+      for (int c = 0; c < NR; ++c)
+#pragma unroll
+        for (int a = 0; a < RM; ++a)
+          if (a * T < mn) {
+            A::fma(yX[a][c], A::ld(u[a]), t[c]);       // U with t1
+            A::fma(yY[a][c], A::ld(v[a]), t[NR + c]);  // V with t2
+          }
+    }
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      if (c0 + c >= P.nrhs) break;
+      V* outx = ppart + (int64_t)(c0 + c) * P.pstride + PM.ppx;
+      V* outy = ppart + (int64_t)(c0 + c) * P.pstride + PM.ppy;
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        const int i = tid + a * T;
+        if (i < m) outx[i] = A::fin(yX[a][c]);
+        if (i < n) outy[i] = A::fin(yY[a][c]);
+      }
+    }
   }
 }
 
@@ -735,6 +847,78 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Several right-hand sides (two-pass levels): one block of 256 threads per
+// projection task computes its k x R partial sums (R <= 32 right-hand sides
+// per pass, 64 columns per pass) from shared-memory tiles of 64 rows (32 for
+// 8-byte values): the
+// task's rows of the matrix (transposed, row r of the tile = the task's row)
+// and of x.  Thread (qg, cg) owns columns 4 qg .. 4 qg + 3 and right-hand
+// sides 2 cg, 2 cg + 1, summed over the rows in row order.
+constexpr int kPmRows = 64;  // rows per tile
+constexpr int kPmCols = 64;  // columns per pass
+constexpr int kPmRhs = 32;   // right-hand sides per pass
+
+template <class A>
+__global__ void __launch_bounds__(256)
+    k_projm(ArgsV2 P, const ProjTask* __restrict__ tasks, const typename A::val* __restrict__ xt,
+            typename A::val* __restrict__ part) {
+  using V = typename A::val;
+  using F = typename A::fac;
+  using Acc = typename A::acc;
+  constexpr int RT = sizeof(V) == 4 ? kPmRows : kPmRows / 2;  // tile rows (48 KB static limit)
+  static_assert(sizeof(V) == 4 || RT == kPmRows / 2, "tile fits static shared memory");
+  __shared__ V Ms[RT][kPmCols + 1];
+  __shared__ V Xs[RT][kPmRhs + 1];
+  const int tid = threadIdx.x;
+  const int qg = tid & 15, cg = tid >> 4;
+  const ProjTask T = tasks[blockIdx.x];
+  const LevelV2& L = P.lev[T.level];
+  const F* M = reinterpret_cast<const F*>(L.fac) + T.mat;
+  const int k = T.k;
+  for (int q0 = 0; q0 < k; q0 += kPmCols) {
+    const int kc = min(kPmCols, k - q0);
+    for (int c0 = 0; c0 < P.nrhs; c0 += kPmRhs) {
+      const int rc = min(kPmRhs, P.nrhs - c0);
+      Acc acc[4][2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = A::zero();
+      for (int r0 = 0; r0 < T.nr; r0 += RT) {
+        const int rows = min(RT, T.nr - r0);
+        __syncthreads();  // the previous tile is consumed
+        for (int e = tid; e < RT * kPmCols; e += 256) {
+          const int rr = e & (RT - 1), q = e / RT;
+          Ms[rr][q] = (rr < rows && q < kc) ? A::ld(M[(int64_t)(q0 + q) * T.ld + T.r0 + r0 + rr])
+                                            : A::vzero();
+        }
+        for (int e = tid; e < RT * kPmRhs; e += 256) {
+          const int rr = e & (RT - 1), c = e / RT;
+          Xs[rr][c] = (rr < rows && c < rc)
+                          ? xt[(int64_t)(c0 + c) * P.n + T.base + T.r0 + r0 + rr]
+                          : A::vzero();
+        }
+        __syncthreads();
+        for (int rr = 0; rr < rows; ++rr) {
+          const V x0 = Xs[rr][2 * cg], x1 = Xs[rr][2 * cg + 1];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const V mv = Ms[rr][4 * qg + i];
+            A::fma(acc[i][0], mv, x0);
+            A::fma(acc[i][1], mv, x1);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int q = 4 * qg + i, c = 2 * cg + j;
+          if (q < kc && c < rc)
+            part[T.out * P.nrhs + (int64_t)(c0 + c) * k + q0 + q] = A::fin(acc[i][j]);
+        }
+    }
+  }
+}
+
 // t[pair, side, q] = sum of the chunk partials in chunk order: one warp per
 // (pair, side, column); lane j sums chunks j, j + 32, ..., then a fixed
 // shuffle tree adds the 32 lane sums.  red[2 s] = {first task, count}.
@@ -768,7 +952,6 @@ __global__ void __launch_bounds__(256)
 // (matrix offset, rank, t offset per entry) is staged in shared memory once,
 // then one thread per row sums U t1 / V t2 over the list in ascending partner
 // order, eight independent loads at a time.
-constexpr int kExpMaxEnt = 64;
 
 template <class A>
 __global__ void __launch_bounds__(256)
@@ -802,6 +985,30 @@ __global__ void __launch_bounds__(256)
   const int32_t base = bstart(P.leaf_off, P.kappa, l, X);
   const int64_t ld = ldpad(bsize(P.leaf_off, P.kappa, l, X));
   const F* fac = reinterpret_cast<const F*>(L.fac);
+  if (P.nrhs > 1) {  // EC right-hand sides per pass: each factor value loaded once per pass
+    constexpr int EC = sizeof(typename A::acc) == 4 ? 8 : 4;
+    for (int c0 = 0; c0 < P.nrhs; c0 += EC) {
+      Acc a[EC];
+#pragma unroll
+      for (int c = 0; c < EC; ++c) a[c] = A::zero();
+      for (int e = 0; e < ne; ++e) {
+        const int k = s_k[e];
+        const F* M = fac + s_off[e] + r;
+        const V* tv = t + s_toff[e];
+#pragma unroll 4
+        for (int q = 0; q < k; ++q) {
+          const V mv = A::ld(M[q * ld]);
+#pragma unroll
+          for (int c = 0; c < EC; ++c)
+            if (c0 + c < P.nrhs) A::fma(a[c], mv, tv[(int64_t)(c0 + c) * k + q]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < EC; ++c)
+        if (c0 + c < P.nrhs) yl[((int64_t)l * P.nrhs + c0 + c) * P.n + base + r] = A::fin(a[c]);
+    }
+    return;
+  }
   for (int c = 0; c < P.nrhs; ++c) {
     Acc a = A::zero();
     for (int e = 0; e < ne; ++e) {
@@ -878,20 +1085,27 @@ __global__ void k_near_f64(const double* __restrict__ xs, const double* __restri
                            int kappa, KernelParams kp, const double* __restrict__ xt, int64_t n,
                            int nrhs, double* __restrict__ yout);
 
-// A box level runs as pairs (sub-warp register kernel) for one right-hand
-// side in the binary32 and bfloat16 modes, and in float-float when its boxes
-// exceed 48 points (below that the box kernel is faster there); else with
-// the box kernel.
+// A box level runs as pairs outside binary64: with several right-hand sides
+// (multi-RHS register kernel), and for one in the binary32 and bfloat16
+// modes and in float-float when its boxes exceed 48 points (sub-warp register
+// kernel; below that the box kernel is faster in float-float).
 static bool box_as_pairs(const hodlr2d* h, int l, int nrhs, int mode) {
-  if (nrhs != 1 || mode == HODLR2D_MODE_F64) return false;
+  if (mode == HODLR2D_MODE_F64) return false;
+  if (nrhs > 1) return true;  // the multi-RHS register kernel
   return mode != HODLR2D_MODE_DF32 || h->v2.plev[l].max_rows > 48;
 }
 
-// The dual levels [ldual, lfuse) run as pairs for one right-hand side in the
-// binary32 and bfloat16 modes (the 512 x 9 register form holds their boxes),
-// else in two passes.
-static bool dual_as_pairs(int nrhs, int mode) {
-  return nrhs == 1 && (mode == HODLR2D_MODE_F32 || mode == HODLR2D_MODE_BF16);
+// First level that is not run in two passes by a product:
+//   binary64                    lfuse (pairs from there on)
+//   several right-hand sides    l2max (boxes of <= kMultiRows points as pairs)
+//   one, binary32 / bfloat16    ldual (the 512 x 9 register form holds the
+//                               boxes of [ldual, lfuse))
+//   one, float-float            lfuse
+static int two_pass_end(const hodlr2d* h, int nrhs, int mode) {
+  const V2Plan& V = h->v2;
+  if (mode == HODLR2D_MODE_F64) return V.lfuse;
+  if (nrhs > 1) return V.l2max;
+  return (mode == HODLR2D_MODE_F32 || mode == HODLR2D_MODE_BF16) ? V.ldual : V.lfuse;
 }
 
 static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
@@ -902,10 +1116,15 @@ static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
     P.lev[l] = LevelV2{L.d_px, L.d_py, L.d_rank, L.d_foff, L.d_prow, L.d_ppoff,
                        L.d_toff, L.d_ent_off, L.d_ent, fac, L.d_meta};
   }
+  const int l2end = two_pass_end(h, nrhs, mode);
   for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) {
-    P.lmode[l] = h->v2.lmode[l];
-    if (P.lmode[l] == LMODE_BOX && box_as_pairs(h, l, nrhs, mode)) P.lmode[l] = LMODE_PAIR;
-    if (l >= h->v2.ldual && l < h->v2.lfuse && dual_as_pairs(nrhs, mode)) P.lmode[l] = LMODE_PAIR;
+    const int base = h->v2.lmode[l];
+    if (l < l2end)
+      P.lmode[l] = LMODE_TWO;
+    else if (base == LMODE_BOX)
+      P.lmode[l] = box_as_pairs(h, l, nrhs, mode) ? LMODE_PAIR : LMODE_BOX;
+    else
+      P.lmode[l] = LMODE_PAIR;  // pair levels, and two-pass levels with a pair plan
   }
   P.leaf_off = h->d_leaf_off;
   P.kappa = h->kappa;
@@ -937,18 +1156,22 @@ int plan_v2(hodlr2d* h) {
   while (V.ldual > 1 && maxcount(V.ldual - 1) <= kDualRows &&
          h->lev[V.ldual - 1].max_rank <= kPairKmax)
     --V.ldual;
+  // pair levels with boxes of more than kMultiRows points also get a two-pass
+  // plan, which several right-hand sides use: [lfuse, l2max)
+  V.l2max = V.lfuse;
+  while (V.l2max <= kappa && maxcount(V.l2max) > kMultiRows) ++V.l2max;
   // two-pass task lists for levels < lfuse
   std::vector<ProjTask> proj;
   std::vector<ExpTask> exps;
   std::vector<int64_t> red;
-  int64_t out = 0, sides_pre = 0;
-  for (int l = 1; l < V.lfuse; ++l) {
-    if (l == V.ldual) {  // the task lists are level-ordered: record the prefix below ldual
-      V.nproj_pre = (int64_t)proj.size();
-      V.nexp_pre = (int64_t)exps.size();
-      V.proj_partials_pre = out;
-      sides_pre = (int64_t)red.size() / 2;
-    }
+  int64_t out = 0;
+  int64_t pre_sides[HODLR2D_MAX_LEVELS + 1] = {};
+  for (int l = 1; l < V.l2max; ++l) {
+    // the task lists are level-ordered: record the counts below level l
+    V.pre_proj[l] = (int64_t)proj.size();
+    V.pre_exp[l] = (int64_t)exps.size();
+    V.pre_part[l] = out;
+    pre_sides[l] = (int64_t)red.size() / 2;
     Level& L = h->lev[l];
     const int64_t np = L.npairs;
     const int sh = 2 * (kappa - l);
@@ -994,11 +1217,11 @@ int plan_v2(hodlr2d* h) {
   }
   V.nproj = (int64_t)proj.size();
   V.nexp = (int64_t)exps.size();
-  if (V.ldual == V.lfuse) {
-    V.nproj_pre = V.nproj;
-    V.nexp_pre = V.nexp;
-    V.proj_partials_pre = out;
-    sides_pre = (int64_t)red.size() / 2;
+  for (int l = V.l2max; l <= HODLR2D_MAX_LEVELS; ++l) {
+    V.pre_proj[l] = V.nproj;
+    V.pre_exp[l] = V.nexp;
+    V.pre_part[l] = out;
+    pre_sides[l] = (int64_t)red.size() / 2;
   }
   {
     std::vector<int32_t> wt(std::max<int64_t>(out, 1));
@@ -1007,9 +1230,9 @@ int plan_v2(hodlr2d* h) {
       for (int q = 0; q < k; ++q) wt[proj[t].out + q] = (int32_t)t;
     }
     std::vector<int64_t> sq;
-    V.ntsum_pre = -1;
+    std::vector<int64_t> sq_at_side((int64_t)red.size() / 2 + 1, 0);  // sq entries before side sd
     for (int64_t sd = 0; sd < (int64_t)red.size() / 2; ++sd) {
-      if (sd == sides_pre) V.ntsum_pre = (int64_t)sq.size() / 2;
+      sq_at_side[sd] = (int64_t)sq.size() / 2;
       if (red[2 * sd + 1] == 0) continue;
       const ProjTask& T0 = proj[red[2 * sd]];
       const int k = h->lev[T0.level].h_rank[T0.pair];
@@ -1019,7 +1242,8 @@ int plan_v2(hodlr2d* h) {
       }
     }
     V.ntsum = (int64_t)sq.size() / 2;
-    if (V.ntsum_pre < 0) V.ntsum_pre = V.ntsum;
+    sq_at_side[(int64_t)red.size() / 2] = V.ntsum;
+    for (int l = 1; l <= HODLR2D_MAX_LEVELS; ++l) V.pre_tsum[l] = sq_at_side[pre_sides[l]];
     H2D_CK(cudaMalloc(&V.d_wtask, sizeof(int32_t) * wt.size()));
     H2D_CK(cudaMemcpy(V.d_wtask, wt.data(), sizeof(int32_t) * wt.size(), cudaMemcpyHostToDevice));
     H2D_CK(cudaMalloc(&V.d_sideq, sizeof(int64_t) * std::max<size_t>(sq.size(), 2)));
@@ -1246,10 +1470,28 @@ static int launch_pair_reg(const int2* work, int64_t nw, int rows, const ArgsV2&
   return HODLR2D_OK;
 }
 
+template <class A>
+static int launch_pair_multi(const int2* work, int64_t nw, int rows, const ArgsV2& P,
+                             const typename A::val* xt, typename A::val* ppart,
+                             cudaStream_t st) {
+  constexpr int NR = sizeof(typename A::acc) == 4 ? 8 : 4;  // right-hand sides per pass
+  const unsigned nb = (unsigned)nw;
+  if (rows <= 64)
+    k_pairm<A, 32, 2, NR><<<nb, 32, 0, st>>>(P, work, xt, ppart);
+  else if (rows <= 128)
+    k_pairm<A, 64, 2, NR><<<nb, 64, 0, st>>>(P, work, xt, ppart);
+  else if (rows <= kMultiRows)
+    k_pairm<A, 128, 2, NR><<<nb, 128, 0, st>>>(P, work, xt, ppart);
+  else
+    return launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st);
+  H2D_CK(cudaGetLastError());
+  return HODLR2D_OK;
+}
+
 // Runs the pairs of level l, one launch per non-empty size class: k_pairg /
 // k_pairs (each factor value read once) for one right-hand side, block shape
-// by the class's largest box; k_pair for binary64 sums (its shuffle-free
-// second phase suits the slow binary64 pipe) and for several right-hand sides.
+// by the class's largest box; k_pairm for several right-hand sides; k_pair for
+// binary64 sums (its shuffle-free second phase suits the slow binary64 pipe).
 template <class A>
 static int launch_pairs(hodlr2d* h, int l, const ArgsV2& P, const typename A::val* xt,
                         typename A::val* ppart, cudaStream_t st) {
@@ -1264,10 +1506,26 @@ static int launch_pairs(hodlr2d* h, int l, const ArgsV2& P, const typename A::va
     } else if (P.nrhs == 1) {
       H2D_TRY(launch_pair_reg<A>(work, nw, rows, P, xt, ppart, st));
     } else {
-      H2D_TRY(launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st));
+      H2D_TRY(launch_pair_multi<A>(work, nw, rows, P, xt, ppart, st));
     }
   }
   return HODLR2D_OK;
+}
+
+// The near field with one right-hand side per pass, or NM per pass for
+// several.
+template <class NP, int NM>
+static void launch_near(const V2Plan& V, const hodlr2d* h, cudaStream_t sn,
+                        const typename NP::pt* xf, const typename NP::pt* yf,
+                        const typename NP::K& kp, const typename NP::A::val* xt, int nrhs,
+                        typename NP::A::val* yl) {
+  const unsigned g = (unsigned)((V.nnearw + kNearWarps - 1) / kNearWarps);
+  if (nrhs == 1)
+    k_near_warp<NP, 1><<<g, 32 * kNearWarps, 0, sn>>>(xf, yf, h->d_leaf_off, h->kappa,
+                                                      V.d_nearw, V.nnearw, kp, xt, h->n, nrhs, yl);
+  else
+    k_near_warp<NP, NM><<<g, 32 * kNearWarps, 0, sn>>>(xf, yf, h->d_leaf_off, h->kappa,
+                                                       V.d_nearw, V.nnearw, kp, xt, h->n, nrhs, yl);
 }
 
 template <class A>
@@ -1305,34 +1563,34 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
                                        reinterpret_cast<const double*>(xt), n, nrhs,
                                        reinterpret_cast<double*>(yl));
     else if (mode == HODLR2D_MODE_DF32)
-      k_near_warp<NearDF32><<<(unsigned)((V.nnearw + kNearWarps - 1) / kNearWarps),
-                              32 * kNearWarps, 0, sn>>>(
-          reinterpret_cast<const float2*>(V.d_xf), reinterpret_cast<const float2*>(V.d_yf),
-          h->d_leaf_off, h->kappa, V.d_nearw, V.nnearw, V.kff,
-          reinterpret_cast<const float2*>(xt), n, nrhs, reinterpret_cast<float2*>(yl));
+      launch_near<NearDF32, 4>(V, h, sn, reinterpret_cast<const float2*>(V.d_xf),
+                               reinterpret_cast<const float2*>(V.d_yf), V.kff,
+                               reinterpret_cast<const float2*>(xt), nrhs,
+                               reinterpret_cast<float2*>(yl));
     else
-      k_near_warp<NearF32><<<(unsigned)((V.nnearw + kNearWarps - 1) / kNearWarps),
-                             32 * kNearWarps, 0, sn>>>(
-          reinterpret_cast<const float*>(V.d_x32), reinterpret_cast<const float*>(V.d_y32),
-          h->d_leaf_off, h->kappa, V.d_nearw, V.nnearw, V.kf32,
-          reinterpret_cast<const float*>(xt), n, nrhs, reinterpret_cast<float*>(yl));
+      launch_near<NearF32, 4>(V, h, sn, reinterpret_cast<const float*>(V.d_x32),
+                              reinterpret_cast<const float*>(V.d_y32), V.kf32,
+                              reinterpret_cast<const float*>(xt), nrhs,
+                              reinterpret_cast<float*>(yl));
   }
-  // two-pass levels: all of [1, lfuse), or only [1, ldual) when the dual
-  // levels run as pairs (the task lists are level-ordered prefixes)
-  const bool dual = dual_as_pairs(nrhs, mode);
-  const int l2end = dual ? V.ldual : V.lfuse;
-  const int64_t nproj = dual ? V.nproj_pre : V.nproj;
-  const int64_t npart = dual ? V.proj_partials_pre : V.proj_partials;
-  const int64_t ntsum = dual ? V.ntsum_pre : V.ntsum;
-  const int64_t nexp = dual ? V.nexp_pre : V.nexp;
+  // two-pass levels [1, l2end): level-ordered prefixes of the task lists
+  const int l2end = two_pass_end(h, nrhs, mode);
+  const int64_t nproj = V.pre_proj[l2end];
+  const int64_t npart = V.pre_part[l2end];
+  const int64_t ntsum = V.pre_tsum[l2end];
+  const int64_t nexp = V.pre_exp[l2end];
   int64_t two_pass_vals = 0;
   for (int l = 1; l < l2end; ++l) two_pass_vals += h->lev[l].nstored;
   if (nproj) {
     {
       PhaseScope ps(h, 2, 1, fs * two_pass_vals + vs * npart * nrhs);
       const int64_t thr = npart * 32;  // one warp per (task, column)
-      k_proj2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
-          P, V.d_proj, V.d_wtask, npart, xt, reinterpret_cast<Val*>(V.d_part));
+      if (nrhs >= 24 && sizeof(Val) == 4)  // binary32 sums: tiled over many right-hand sides
+        k_projm<A><<<(unsigned)nproj, 256, 0, s>>>(P, V.d_proj, xt,
+                                                   reinterpret_cast<Val*>(V.d_part));
+      else
+        k_proj2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
+            P, V.d_proj, V.d_wtask, npart, xt, reinterpret_cast<Val*>(V.d_part));
     }
     {
       PhaseScope ps(h, 3, 1, vs * (npart + h->t_total) * nrhs);
@@ -1348,7 +1606,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   }
   H2D_CK(cudaEventRecord(V.ev_near, sn));
   if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, sf));
-  for (int l = V.ldual; l <= h->kappa; ++l) {
+  for (int l = l2end; l <= h->kappa; ++l) {
     if (P.lmode[l] != LMODE_PAIR || V.plev[l].nwork == 0) continue;
     const int phase = V.lmode[l] == LMODE_BOX ? 7 : l < V.lpair_small ? 6 : 8;
     int nlaunch = 0;  // one launch per non-empty size class

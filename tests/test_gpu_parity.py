@@ -299,7 +299,9 @@ def test_register_pair_kernel_block_sizes(h2d, oracle, n):
     y_o = o.matvec(x)
     xd = torch.from_numpy(x).cuda()
     x2 = torch.stack([xd, xd], dim=1)
-    for mode, bound, bound2 in (("df32", 1e-12, 1e-13), ("f32", 5e-6, 1e-6), ("bf16", 2e-2, 1e-6)):
+    # bound2: the two forms sum in different orders; float-float rounds each
+    # operation to about 2^-44, binary32 to 2^-24
+    for mode, bound, bound2 in (("df32", 1e-12, 1e-12), ("f32", 5e-6, 1e-6), ("bf16", 2e-2, 1e-6)):
         g.prepare(mode)
         y1 = g.matvec(xd, mode=mode)
         y2 = g.matvec(x2, mode=mode)
@@ -307,6 +309,24 @@ def test_register_pair_kernel_block_sizes(h2d, oracle, n):
         assert torch.equal(y2[:, 0], y2[:, 1])
         assert rel(y1.cpu().numpy(), y2[:, 0].cpu().numpy()) <= bound2, mode
         assert torch.equal(y1, g.matvec(xd, mode=mode))  # deterministic
+
+
+def test_many_rhs_equal_columnwise(h2d):
+    """11 right-hand sides (not a multiple of the kernels' 8 or 4 per pass):
+    coarse boxes in two passes, boxes of <= 256 points with the multi-RHS
+    register kernel; each column agrees with the one-RHS product."""
+    n = 30000
+    pts = inputs.uniform(n, seed=8)
+    g = h2d.HODLR2D(pts, h2d.kernel("imq", 1.0 / np.sqrt(n)), 64, 1e-10)
+    X = torch.from_numpy(inputs.rhs(n, 11, seed=9)).cuda()
+    for mode, bound in (("f64", 1e-15), ("df32", 1e-12), ("f32", 1e-6), ("bf16", 1e-6)):
+        if mode != "f64":
+            g.prepare(mode)
+        Y = g.matvec(X, mode=mode)
+        assert torch.equal(Y, g.matvec(X, mode=mode))
+        for c in (0, 7, 8, 10):
+            y1 = g.matvec(X[:, c].contiguous(), mode=mode)
+            assert rel(Y[:, c].cpu().numpy(), y1.cpu().numpy()) <= bound, (mode, c)
 
 
 def test_large_leaves_near_field(h2d, oracle):
