@@ -423,6 +423,46 @@ def direct_rows_gpu(pts, kind, a, diag, x, rows, chunk=1024):
     return out.cpu().numpy()
 
 
+def extra_panel_system(pkg, inputs, stream):
+    """log r on the 512 x 512 jittered grid (N = 2^18, spacing h = 2/512),
+    leaf 64, eps 1e-10, GMRES(50) to 1e-8 with b ~ N(0,1): the literal
+    panel diagonal (h^2/2pi)(log h - 1.5), a first-kind system on which
+    GMRES stalls (capped at 300 products), and the second-kind variant (the
+    matrix scaled by 2pi/h^2: diagonal 2pi/h^2 + log h - 1.5)."""
+    import torch
+    pts, h = inputs.jittered_grid(512, seed=0)
+    n = len(pts)
+    b = torch.from_numpy(inputs.rhs(n, seed=1)).cuda()
+    out = {}
+    for name, diag, maxit in (
+            ("literal", (h * h / (2 * np.pi)) * (np.log(h) - 1.5), 300),
+            ("second_kind", 2 * np.pi / (h * h) + np.log(h) - 1.5, 2000)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = pkg.HODLR2D(pts, pkg.kernel("log", 0.0, diag), 64, 1e-10, root=ROOT_BOX)
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - t0
+        g.set_stream(stream)
+        g.prepare("df32")
+        g.prepare("f32")
+        st = g.stats()
+        res = {"kappa": st["kappa"], "r_m": st["max_rank"], "build_s": round(t_b, 3)}
+        y = torch.empty_like(b)
+        for mode in ("f64", "df32", "f32"):
+            res["matvec_ms_" + mode] = round(timed(g, b, y, mode, 5, 2, stream), 3)
+        g.gmres(b, tol=1e-2, restart=50, maxit=50)  # Krylov workspace (untimed)
+        for mode in ("f64", "df32", "f32"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xs, it, rr, code = g.gmres(b, tol=1e-8, restart=50, maxit=maxit, inner_mode=mode)
+            torch.cuda.synchronize()
+            res["gmres_" + mode] = {"ms": round((time.perf_counter() - t0) * 1e3, 1),
+                                    "products": it, "relres": rr, "converged": code == 0}
+        out[name] = res
+        g.close()
+    return out
+
+
 def extra_paper_replay(pkg, inputs, stream):
     """The paper's own workloads on the GPU, next to its printed tables
     (context): Sec. 5.1 (1/r, Chebyshev grid, N_max 500, eps 1e-12; r_m,
@@ -498,6 +538,7 @@ def extras(pkg, inputs, n, n_learned):
     out = {}
     for name, fn in (("rbf_system", lambda: extra_gmres_nrhs(pkg, inputs, n, stream)),
                      ("paper_replay", lambda: extra_paper_replay(pkg, inputs, stream)),
+                     ("panel_system_log", lambda: extra_panel_system(pkg, inputs, stream)),
                      ("batch_point_sets", lambda: extra_batch(pkg, inputs, stream)),
                      ("learned_rank_log", lambda: extra_learned(pkg, inputs, stream, n_learned))):
         t0 = time.perf_counter()

@@ -169,12 +169,64 @@ __device__ __forceinline__ bool ffv_ge(float2 a, float2 b) {
   return a.x > b.x || (a.x == b.x && a.y >= b.y);
 }
 
-// Kernel parameters in float-float, plus the binary64 set for the kernels
-// whose logarithm is evaluated in binary64 (log r, phi_1).
+// float-float pair of a binary64 constant, at compile time
+struct FFConst {
+  float hi, lo;
+  __host__ __device__ constexpr FFConst(double d)
+      : hi((float)d), lo((float)(d - (double)(float)d)) {}
+};
+
+// Natural logarithm of a float-float x > 0 (a normal binary32 high part), to
+// about 2^-46 relative.  Argument reduction x = 2^e m with m in [sqrt(1/2),
+// sqrt(2)), then log m = 2 atanh(s) = 2 s (1 + z/3 + z^2/5 + ...), s =
+// (m - 1) / (m + 1), z = s^2 <= 0.0295: the series to z^8 (its remainder is
+// below 2^-48) by Horner's rule, the four leading steps in float-float and
+// the tail in binary32.  log x = e log 2 + log m.
+__device__ __forceinline__ float2 ffv_log(float2 x) {
+  constexpr FFConst LN2(0.69314718055994530942);
+  constexpr FFConst C3(1.0 / 3.0), C5(1.0 / 5.0), C7(1.0 / 7.0);
+  const int bits = __float_as_int(x.x);
+  int e = ((bits >> 23) & 0xff) - 127;
+  float mh = __int_as_float((bits & 0x007fffff) | 0x3f800000);  // [1, 2)
+  if (mh > 1.41421356f) {
+    mh *= 0.5f;
+    e += 1;
+  }
+  const float ml = ldexpf(x.y, -e);  // exact: a power-of-two scaling
+  // s = (m - 1) / (m + 1); m - 1 is exact in its high part (Sterbenz)
+  float nh, nl, dh, dl;
+  two_sum(mh - 1.0f, ml, nh, nl);
+  two_sum(mh, 1.0f, dh, dl);
+  dl = __fadd_rn(dl, ml);
+  fast_two_sum(dh, dl, dh, dl);
+  const float2 sv = ffv_mul(make_float2(nh, nl), ffv_rcp(make_float2(dh, dl)));
+  const float2 z = ffv_mul(sv, sv);
+  const float zf = z.x;
+  float r = __fmaf_rn(zf, 1.0f / 17.0f, 1.0f / 15.0f);
+  r = __fmaf_rn(zf, r, 1.0f / 13.0f);
+  r = __fmaf_rn(zf, r, 1.0f / 11.0f);
+  r = __fmaf_rn(zf, r, 1.0f / 9.0f);
+  float2 c = DF32A::add(make_float2(C7.hi, C7.lo), ffv_mul(z, make_float2(r, 0.f)));
+  c = DF32A::add(make_float2(C5.hi, C5.lo), ffv_mul(z, c));
+  c = DF32A::add(make_float2(C3.hi, C3.lo), ffv_mul(z, c));
+  c = DF32A::add(make_float2(1.f, 0.f), ffv_mul(z, c));
+  float2 lm = ffv_mul(sv, c);
+  lm.x *= 2.f;
+  lm.y *= 2.f;
+  const float ef = (float)e;
+  float ph, pe;
+  two_prod(ef, LN2.hi, ph, pe);
+  pe = __fmaf_rn(ef, LN2.lo, pe);
+  float eh, el;
+  fast_two_sum(ph, pe, eh, el);
+  return DF32A::add(make_float2(eh, el), lm);
+}
+
+// Kernel parameters in float-float.
 struct KernelFF {
   int kind;
   float2 a, a2, inv_a, diag;
-  KernelParams p64;
+  float2 inv_log_a, inv_phi1_den;  // 1 / log a and 1 / (a log a - 1) for phi_1
 };
 
 // Entry phi(|x_i - x_j|) of the kernel; gi and gj identify the two points
@@ -193,9 +245,16 @@ __device__ __forceinline__ float2 entry_ff(const KernelFF& k, float2 xi, float2 
       if (ffv_ge(r, k.a)) return ffv_mul(k.a, ffv_rcp(r));
       return ffv_mul(r, k.inv_a);
     }
-    default: {  // log r and phi_1: binary64 logarithm of the float-float r^2
-      const double v = phi_r2(k.p64, (double)r2.x + (double)r2.y);
-      return DF32A::from_double(v);
+    case HODLR2D_LOG: {  // log r = log(r^2) / 2
+      const float2 l = ffv_log(r2);
+      return make_float2(0.5f * l.x, 0.5f * l.y);
+    }
+    default: {  // phi_1
+      const float2 r = ffv_sqrt(r2);
+      const float2 l2 = ffv_log(r2);
+      const float2 lr = make_float2(0.5f * l2.x, 0.5f * l2.y);
+      if (ffv_ge(r, k.a)) return ffv_mul(lr, k.inv_log_a);
+      return ffv_mul(DF32A::add(ffv_mul(r, lr), make_float2(-1.f, 0.f)), k.inv_phi1_den);
     }
   }
 }

@@ -1674,7 +1674,8 @@ int prepare_df32(hodlr2d* h) {
   V.kff.a2 = split(h->kp.a2);
   V.kff.inv_a = split(h->kp.inv_a);
   V.kff.diag = split(h->kp.diag);
-  V.kff.p64 = h->kp;
+  V.kff.inv_log_a = split(h->kp.log_a != 0.0 ? 1.0 / h->kp.log_a : 0.0);
+  V.kff.inv_phi1_den = split(h->kp.phi1_den != 0.0 ? 1.0 / h->kp.phi1_den : 0.0);
   return HODLR2D_OK;
 }
 

@@ -329,12 +329,15 @@ def test_many_rhs_equal_columnwise(h2d):
             assert rel(Y[:, c].cpu().numpy(), y1.cpu().numpy()) <= bound, (mode, c)
 
 
-def test_large_leaves_near_field(h2d, oracle):
-    """Leaves of several hundred points (depth forced to 2): the float-float
-    and binary32 near fields split each leaf into 32-target work items."""
+@pytest.mark.parametrize("kind,a", [("mq", 0.01), ("log", 0.0), ("phi1", 0.001)])
+def test_large_leaves_near_field(h2d, oracle, kind, a):
+    """Leaves of several hundred points (depth forced to 2), so the near field
+    carries most of the product: the float-float and binary32 near fields
+    (32-target work items; float-float logarithm for log r and phi_1)
+    against the oracle on the same factors."""
     n = 5000
     pts = inputs.chebyshev_grid(71)[:n]
-    kind, a, leaf, eps = "mq", 0.01, 64, 1e-10
+    leaf, eps = 64, 1e-10
     o = oracle.Oracle(pts, oracle.kernel(kind, a), leaf, eps, levels=2)
     g = h2d.HODLR2D(pts, h2d.kernel(kind, a), leaf, eps, levels=2, compress=False)
     g.import_factors(*o.export_factors())
