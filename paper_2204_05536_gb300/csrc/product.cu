@@ -919,9 +919,194 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------------------
+// bfloat16 factors, several right-hand sides, two-pass levels: the products
+// on the tensor cores (mma.sync m16n8k16, bfloat16 operands, binary32
+// accumulation).  x and t are split into two bfloat16 terms (hi + lo, about
+// 2^-17 relative), each multiplied in, so the result keeps the bfloat16
+// mode's accuracy (set by the factors).
+//
+// Fragment layout of m16n8k16 (g = lane / 4, t = lane % 4): A (16 x 16, row
+// major) a0 = (g, 2t..2t+1), a1 = (g+8, 2t..), a2 = (g, 2t+8..), a3 = (g+8,
+// 2t+8..); B (16 x 8) b0 = (2t..2t+1, g), b1 = (2t+8.., g); C c0 = (g, 2t),
+// c1 = (g, 2t+1), c2 = (g+8, 2t), c3 = (g+8, 2t+1).  Two bfloat16 per 32-bit
+// register, the lower index in the low half.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bf2_pack(__nv_bfloat16 lo_idx, __nv_bfloat16 hi_idx) {
+  return (uint32_t)__bfloat16_as_ushort(lo_idx) | ((uint32_t)__bfloat16_as_ushort(hi_idx) << 16);
+}
+__device__ __forceinline__ void bf_split(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  l = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Projection: one block of 128 threads per projection task; warp w owns the
+// 16-column tiles w, w + 4, ... of the task's k columns and all right-hand
+// sides of the pass (4 tiles of 8, R <= 32); rows in steps of 16.
+__global__ void __launch_bounds__(128)
+    k_proj_tc(ArgsV2 P, const ProjTask* __restrict__ tasks, const float* __restrict__ xt,
+              float* __restrict__ part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  const ProjTask T = tasks[blockIdx.x];
+  const LevelV2& L = P.lev[T.level];
+  const __nv_bfloat16* M = reinterpret_cast<const __nv_bfloat16*>(L.fac) + T.mat + T.r0;
+  const int k = T.k, nr = T.nr;
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  // (r, r + 1) of column q as one bfloat16 pair; rows past the chunk are 0
+  auto colpair = [&](int q, int r) -> uint32_t {
+    if (q >= k || r >= nr) return 0u;
+    const __nv_bfloat16* c = M + (int64_t)q * T.ld + r;
+    return bf2_pack(c[0], r + 1 < nr ? c[1] : z);
+  };
+  for (int c0 = 0; c0 < P.nrhs; c0 += 32) {
+    for (int q0 = 16 * warp; q0 < k; q0 += 64) {
+      float acc[4][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+      for (int kk = 0; kk < nr; kk += 16) {
+        uint32_t a[4];
+        a[0] = colpair(q0 + g, kk + 2 * t4);
+        a[1] = colpair(q0 + g + 8, kk + 2 * t4);
+        a[2] = colpair(q0 + g, kk + 2 * t4 + 8);
+        a[3] = colpair(q0 + g + 8, kk + 2 * t4 + 8);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + 8 * j + g;
+          __nv_bfloat16 h[4], l[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int r = kk + 2 * t4 + (e & 1) + 8 * (e >> 1);
+            const float xv = (c < P.nrhs && r < nr)
+                                 ? xt[(int64_t)c * P.n + T.base + T.r0 + r] : 0.f;
+            bf_split(xv, h[e], l[e]);
+          }
+          mma_bf16(acc[j], a, bf2_pack(h[0], h[1]), bf2_pack(h[2], h[3]));
+          mma_bf16(acc[j], a, bf2_pack(l[0], l[1]), bf2_pack(l[2], l[3]));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = q0 + g + 8 * (e >> 1), c = c0 + 8 * j + 2 * t4 + (e & 1);
+          if (q < k && c < P.nrhs) part[T.out * P.nrhs + (int64_t)c * k + q] = acc[j][e];
+        }
+    }
+  }
+}
+
+// Expansion: one block of 256 threads per expansion task (<= 256 rows of one
+// box); warp w owns rows 32 w .. 32 w + 31 (two 16-row tiles) and all
+// right-hand sides of the pass; the box's list entries in partner order,
+// each entry's k columns in steps of 16.
+__global__ void __launch_bounds__(256)
+    k_exp_tc(ArgsV2 P, const ExpTask* __restrict__ tasks, const float* __restrict__ t,
+             float* __restrict__ yl) {
+  __shared__ int64_t s_off[kExpMaxEnt];
+  __shared__ int64_t s_toff[kExpMaxEnt];
+  __shared__ int s_k[kExpMaxEnt];
+  const ExpTask T = tasks[blockIdx.x];
+  const int l = T.level;
+  const LevelV2& L = P.lev[l];
+  const uint32_t X = (uint32_t)T.box;
+  const int32_t e0 = L.ent_off[X], ne = L.ent_off[X + 1] - e0;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const int32_t code = L.ent[e0 + e];
+    const int64_t p = code >> 1;
+    const int side = code & 1;
+    const int k = L.rank[p];
+    int64_t off = L.foff[p];
+    if (side == 1) off += ldpad(bsize(P.leaf_off, P.kappa, l, (uint32_t)L.px[p])) * k;
+    s_off[e] = off;
+    s_k[e] = k;
+    s_toff[e] = L.toff[p] * P.nrhs + (int64_t)side * k * P.nrhs;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  const int32_t base = bstart(P.leaf_off, P.kappa, l, X);
+  const int64_t ld = ldpad(bsize(P.leaf_off, P.kappa, l, X));
+  const __nv_bfloat16* fac = reinterpret_cast<const __nv_bfloat16*>(L.fac);
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  const int rw = 32 * warp;  // this warp's first row in the task
+  if (rw >= T.nr) return;
+  for (int c0 = 0; c0 < P.nrhs; c0 += 32) {
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+    for (int e = 0; e < ne; ++e) {
+      const int k = s_k[e];
+      const __nv_bfloat16* U = fac + s_off[e] + T.r0;
+      const float* tv = t + s_toff[e];
+      for (int kk = 0; kk < k; kk += 16) {
+        // B: t (q x c), split into two bfloat16 terms
+        uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + 8 * j + g;
+          __nv_bfloat16 h[4], lo[4];
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            const int q = kk + 2 * t4 + (e2 & 1) + 8 * (e2 >> 1);
+            const float tvv = (c < P.nrhs && q < k) ? tv[(int64_t)c * k + q] : 0.f;
+            bf_split(tvv, h[e2], lo[e2]);
+          }
+          bh[j][0] = bf2_pack(h[0], h[1]);
+          bh[j][1] = bf2_pack(h[2], h[3]);
+          bl[j][0] = bf2_pack(lo[0], lo[1]);
+          bl[j][1] = bf2_pack(lo[2], lo[3]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          // A: rows of U (r x q); the two values of a register are columns
+          // q, q + 1 of one row, ld apart
+          auto at = [&](int r, int q) -> __nv_bfloat16 {
+            return (r < T.nr && q < k) ? U[(int64_t)q * ld + r] : z;
+          };
+          const int r0 = rw + 16 * i + g;
+          const int qa = kk + 2 * t4;
+          uint32_t a[4];
+          a[0] = bf2_pack(at(r0, qa), at(r0, qa + 1));
+          a[1] = bf2_pack(at(r0 + 8, qa), at(r0 + 8, qa + 1));
+          a[2] = bf2_pack(at(r0, qa + 8), at(r0, qa + 9));
+          a[3] = bf2_pack(at(r0 + 8, qa + 8), at(r0 + 8, qa + 9));
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            mma_bf16(acc[i][j], a, bh[j][0], bh[j][1]);
+            mma_bf16(acc[i][j], a, bl[j][0], bl[j][1]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int e2 = 0; e2 < 4; ++e2) {
+          const int r = rw + 16 * i + g + 8 * (e2 >> 1);
+          const int c = c0 + 8 * j + 2 * t4 + (e2 & 1);
+          if (r < T.nr && c < P.nrhs)
+            yl[((int64_t)l * P.nrhs + c) * P.n + base + T.r0 + r] = acc[i][j][e2];
+        }
+  }
+}
+
 // t[pair, side, q] = sum of the chunk partials in chunk order: one warp per
 // (pair, side, column); lane j sums chunks j, j + 32, ..., then a fixed
-// shuffle tree adds the 32 lane sums.  red[2 s] = {first task, count}.
+// shuffle tree adds the 32 lane sums (one right-hand side), or lane c sums
+// all chunks of right-hand side c (several).  red[2 s] = {first task, count}.
 template <class A>
 __global__ void __launch_bounds__(256)
     k_tsum2(ArgsV2 P, const ProjTask* __restrict__ tasks, const int64_t* __restrict__ red,
@@ -938,6 +1123,15 @@ __global__ void __launch_bounds__(256)
   const LevelV2& L = P.lev[T0.level];
   const int k = L.rank[T0.pair];
   V* out = t + L.toff[T0.pair] * P.nrhs + (int64_t)T0.side * k * P.nrhs;
+  if (P.nrhs > 1) {  // lane per right-hand side, chunks in order
+    for (int c = lane; c < P.nrhs; c += 32) {
+      V acc = A::vzero();
+      for (int64_t j = 0; j < count; ++j)
+        acc = A::add(acc, part[tasks[first + j].out * P.nrhs + c * k + q]);
+      out[c * k + q] = acc;
+    }
+    return;
+  }
   for (int c = 0; c < P.nrhs; ++c) {
     V acc = A::vzero();
     for (int64_t j = lane; j < count; j += 32)
@@ -1585,7 +1779,11 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
     {
       PhaseScope ps(h, 2, 1, fs * two_pass_vals + vs * npart * nrhs);
       const int64_t thr = npart * 32;  // one warp per (task, column)
-      if (nrhs >= 24 && sizeof(Val) == 4)  // binary32 sums: tiled over many right-hand sides
+      if (std::is_same<A, BF16A>::value && nrhs > 1)  // tensor cores
+        k_proj_tc<<<(unsigned)nproj, 128, 0, s>>>(P, V.d_proj,
+                                                  reinterpret_cast<const float*>(xt),
+                                                  reinterpret_cast<float*>(V.d_part));
+      else if (nrhs >= 24 && sizeof(Val) == 4)  // binary32 sums: tiled over many right-hand sides
         k_projm<A><<<(unsigned)nproj, 256, 0, s>>>(P, V.d_proj, xt,
                                                    reinterpret_cast<Val*>(V.d_part));
       else
@@ -1602,7 +1800,12 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   }
   if (nexp) {
     PhaseScope ps(h, 4, 1, fs * two_pass_vals + vb * (l2end - 1));
-    k_exp2<A><<<(unsigned)nexp, 256, 0, s>>>(P, V.d_exp, reinterpret_cast<const Val*>(V.d_t), yl);
+    if (std::is_same<A, BF16A>::value && nrhs > 1)  // tensor cores
+      k_exp_tc<<<(unsigned)nexp, 256, 0, s>>>(P, V.d_exp, reinterpret_cast<const float*>(V.d_t),
+                                              reinterpret_cast<float*>(yl));
+    else
+      k_exp2<A><<<(unsigned)nexp, 256, 0, s>>>(P, V.d_exp, reinterpret_cast<const Val*>(V.d_t),
+                                               yl);
   }
   H2D_CK(cudaEventRecord(V.ev_near, sn));
   if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, sf));
