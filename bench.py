@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--modes", default="df32,f64,f32,bf16",
                    help="product modes to time; the first is the headline")
     p.add_argument("--n", type=int, default=N_FULL, help="points (smaller for quick checks)")
+    p.add_argument("--nrhs", type=int, default=1, help="right-hand sides per product")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     p.add_argument("--n-learned", type=int, default=1 << 22,
@@ -189,11 +190,14 @@ def cpu_baseline_leg(rows, x, pts, n):
             "kappa_sample": o.kappa, "t_rows_s": t_rows, "y_direct_rows": yd}
 
 
-def workload_config(n, kappa, mode):
+def workload_config(n, kappa, mode, nrhs=1):
     """The bench line's config (the same for both arms)."""
     fb = {"f64": 8, "df32": 8, "f32": 4, "bf16": 2}[mode]
-    return {"workload": WORKLOAD if n == N_FULL else WORKLOAD.replace("2^20", str(n)),
-            "n": n, "leaf": LEAF, "eps": EPS, "kernel": "mq", "a": 1.0 / np.sqrt(n), "nrhs": 1,
+    w = WORKLOAD if n == N_FULL else WORKLOAD.replace("2^20", str(n))
+    if nrhs > 1:
+        w = w.replace("1 RHS", "%d RHS" % nrhs)
+    return {"workload": w,
+            "n": n, "leaf": LEAF, "eps": EPS, "kernel": "mq", "a": 1.0 / np.sqrt(n), "nrhs": nrhs,
             "mode": mode, "kappa": kappa, "parallelism": "replicas",
             "l2": "no flush: factors (%d bytes per value) exceed the 129 MB L2" % fb}
 
@@ -556,7 +560,8 @@ def run_ours(args, ws, rank, local):
     n = args.n
     pts = inputs.uniform(n, seed=0)
     a = 1.0 / np.sqrt(n)
-    x_h = inputs.rhs(n, seed=1)
+    R = args.nrhs
+    x_h = inputs.rhs(n, R, seed=1)  # (n,) or (n, R)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g = pkg.HODLR2D(pts, pkg.kernel("mq", a), LEAF, EPS, root=ROOT_BOX)
@@ -566,8 +571,10 @@ def run_ours(args, ws, rank, local):
     modes = args.modes.split(",")
     stream = torch.cuda.current_stream()
     g.set_stream(stream)
-    x = torch.from_numpy(x_h).cuda()
-    y = torch.empty_like(x)
+    # device buffers: R x n (column-major n x R); the products take x.t()
+    xc = torch.from_numpy(np.ascontiguousarray(x_h.T if R > 1 else x_h)).cuda()
+    y = torch.empty_like(xc)
+    x = xc.t() if R > 1 else xc
     per_mode = {}
     for mode in modes:
         if mode != "f64":
@@ -593,9 +600,9 @@ def run_ours(args, ws, rank, local):
     clk = per_mode[mode]["clocks"]
 
     # end to end through the public API with pinned host buffers
-    xp = torch.from_numpy(x_h).pin_memory()
+    xp = torch.from_numpy(np.ascontiguousarray(x_h.T if R > 1 else x_h)).pin_memory()
     yp = torch.empty_like(xp).pin_memory()
-    xnp, ynp = xp.numpy(), yp.numpy()
+    xnp, ynp = (xp.numpy().T if R > 1 else xp.numpy()), yp.numpy()
     g.set_stream(None)
     for _ in range(2):
         g.matvec(xnp, mode=mode, out=ynp)
@@ -618,7 +625,8 @@ def run_ours(args, ws, rank, local):
     bytes_step = d["bytes"] // args.steps
     achieved = bytes_step / (per_launch_ms * 1e-3) / 1e9
     launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
-    alg_bytes = st["bytes_per_matvec"][mode]
+    # factors, points (16 N) and the x / y vectors (16 N per right-hand side)
+    alg_bytes = st["bytes_per_matvec"][mode] + 16 * n * (R - 1)
     hbm_frac_product = alg_bytes / (ms_step * 1e-3) / 1e9 / peak
 
     out = {
@@ -634,7 +642,7 @@ def run_ours(args, ws, rank, local):
         "vs_baseline": None,
         "dtype": mode,
         "data": "synthetic",
-        "config": workload_config(n, st["kappa"], mode),
+        "config": workload_config(n, st["kappa"], mode, R),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "peak_source": peak_src, "bytes_per_launch": bytes_step,
@@ -643,7 +651,7 @@ def run_ours(args, ws, rank, local):
                      "traffic": NCU_TRAFFIC.get((dom, mode, n))},
         "hbm_frac_product": round(hbm_frac_product, 4),
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms",
-                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+                "h2d_bytes_per_step": 8 * n * R, "d2h_bytes_per_step": 8 * n * R},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
         "t_build_ms": round(t_build, 1),
@@ -657,8 +665,8 @@ def run_ours(args, ws, rank, local):
         "phases_ms_serialized": {k: round(v["ms"] / args.steps, 4) for k, v in prof.items()
                                  if v["launches"]},
         "modes": {m: {"ms": round(v["ms"], 4),
-                      "hbm_frac_product": round(st["bytes_per_matvec"][m] / (v["ms"] * 1e-3)
-                                                / 1e9 / peak, 4),
+                      "hbm_frac_product": round((st["bytes_per_matvec"][m] + 16 * n * (R - 1))
+                                                / (v["ms"] * 1e-3) / 1e9 / peak, 4),
                       "clocks_sm_mhz": v["clocks"].get("sm_mhz"),
                       "phases_ms_serialized": {k: round(p["ms"] / args.steps, 4)
                                                for k, p in v["prof"].items() if p["launches"]}}
@@ -666,7 +674,7 @@ def run_ours(args, ws, rank, local):
     }
     if rank == 0 and not args.no_cpu:
         rows = np.random.default_rng(7).choice(n, 256, replace=False)
-        cb = cpu_baseline_leg(rows, x_h, pts, n)
+        cb = cpu_baseline_leg(rows, x_h if R == 1 else np.ascontiguousarray(x_h[:, 0]), pts, n)
         # the paper's cost model O(p N kappa) (Sec. 4.1) scales the sample
         scale = (n * st["kappa"]) / (CPU_SAMPLE_N * cb["kappa_sample"])
         full_est_s = cb["t_matvec_s"] * scale
@@ -678,7 +686,7 @@ def run_ours(args, ws, rank, local):
         yd = cb["y_direct_rows"]
         errs = {}
         for m, v in per_mode.items():
-            yr = v["y"].cpu().numpy()[rows]
+            yr = (v["y"][0] if R > 1 else v["y"]).cpu().numpy()[rows]  # first RHS
             errs[m] = {"rel2_256_rows": float(np.linalg.norm(yr - yd) / np.linalg.norm(yd)),
                        "max_rel_256_rows": float(np.max(np.abs(yr - yd) / np.abs(yd)))}
         y64 = per_mode["f64"]["y"] if "f64" in per_mode else None

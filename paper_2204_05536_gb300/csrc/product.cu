@@ -950,11 +950,18 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 
 // Projection: one block of 128 threads per projection task; warp w owns the
 // 16-column tiles w, w + 4, ... of the task's k columns and all right-hand
-// sides of the pass (4 tiles of 8, R <= 32); rows in steps of 16.
+// sides of the pass (4 tiles of 8, R <= 32).  x is staged per 128 rows in
+// shared memory as bfloat16 hi / lo terms, right-hand side by right-hand
+// side, so that a B register (rows r, r + 1 of one column) is one 32-bit
+// load; the factor pairs are 32-bit loads from global memory (even offsets).
+constexpr int kTcRows = 128;  // rows of x staged at a time
+
 __global__ void __launch_bounds__(128)
     k_proj_tc(ArgsV2 P, const ProjTask* __restrict__ tasks, const float* __restrict__ xt,
               float* __restrict__ part) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ uint32_t xh[32][kTcRows / 2 + 4];  // (r, r + 1) pairs of x, hi terms
+  __shared__ uint32_t xl[32][kTcRows / 2 + 4];  // lo terms
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t4 = lane & 3;
   const ProjTask T = tasks[blockIdx.x];
   const LevelV2& L = P.lev[T.level];
@@ -965,32 +972,50 @@ __global__ void __launch_bounds__(128)
   auto colpair = [&](int q, int r) -> uint32_t {
     if (q >= k || r >= nr) return 0u;
     const __nv_bfloat16* c = M + (int64_t)q * T.ld + r;
-    return bf2_pack(c[0], r + 1 < nr ? c[1] : z);
+    if (r + 1 < nr) return *reinterpret_cast<const uint32_t*>(c);  // even offset
+    return bf2_pack(c[0], z);
   };
   for (int c0 = 0; c0 < P.nrhs; c0 += 32) {
-    for (int q0 = 16 * warp; q0 < k; q0 += 64) {
+    const int npass = (k + 63) / 64;  // 64 columns per pass, 16 per warp
+    for (int pass = 0; pass < npass; ++pass) {
+      // every warp runs every pass (the staging below needs all of them);
+      // a warp whose tile starts past k stages x and skips the products
+      const int q0 = 64 * pass + 16 * warp;
       float acc[4][4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-      for (int kk = 0; kk < nr; kk += 16) {
-        uint32_t a[4];
-        a[0] = colpair(q0 + g, kk + 2 * t4);
-        a[1] = colpair(q0 + g + 8, kk + 2 * t4);
-        a[2] = colpair(q0 + g, kk + 2 * t4 + 8);
-        a[3] = colpair(q0 + g + 8, kk + 2 * t4 + 8);
+      for (int rb = 0; rb < nr; rb += kTcRows) {
+        __syncthreads();  // the previous x tile is consumed
+        for (int e = tid; e < 32 * (kTcRows / 2); e += 128) {
+          const int c = e / (kTcRows / 2), rp = e % (kTcRows / 2);
+          const int r = rb + 2 * rp;
+          const float* xc = xt + (int64_t)(c0 + c) * P.n + T.base + T.r0;
+          const bool okc = c0 + c < P.nrhs;
+          const float v0 = (okc && r < nr) ? xc[r] : 0.f;
+          const float v1 = (okc && r + 1 < nr) ? xc[r + 1] : 0.f;
+          __nv_bfloat16 h0, l0, h1, l1;
+          bf_split(v0, h0, l0);
+          bf_split(v1, h1, l1);
+          xh[c][rp] = bf2_pack(h0, h1);
+          xl[c][rp] = bf2_pack(l0, l1);
+        }
+        __syncthreads();
+        if (q0 >= k) continue;  // no columns of this warp in this pass
+        const int rend = min(kTcRows, nr - rb);
+        for (int kk = 0; kk < rend; kk += 16) {
+          const int r = rb + kk + 2 * t4;
+          uint32_t a[4];
+          a[0] = colpair(q0 + g, r);
+          a[1] = colpair(q0 + g + 8, r);
+          a[2] = colpair(q0 + g, r + 8);
+          a[3] = colpair(q0 + g + 8, r + 8);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = c0 + 8 * j + g;
-          __nv_bfloat16 h[4], l[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int r = kk + 2 * t4 + (e & 1) + 8 * (e >> 1);
-            const float xv = (c < P.nrhs && r < nr)
-                                 ? xt[(int64_t)c * P.n + T.base + T.r0 + r] : 0.f;
-            bf_split(xv, h[e], l[e]);
+          for (int j = 0; j < 4; ++j) {
+            const int c = 8 * j + g;
+            const int rp = (kk >> 1) + t4;
+            mma_bf16(acc[j], a, xh[c][rp], xh[c][rp + 4]);
+            mma_bf16(acc[j], a, xl[c][rp], xl[c][rp + 4]);
           }
-          mma_bf16(acc[j], a, bf2_pack(h[0], h[1]), bf2_pack(h[2], h[3]));
-          mma_bf16(acc[j], a, bf2_pack(l[0], l[1]), bf2_pack(l[2], l[3]));
         }
       }
 #pragma unroll
