@@ -294,7 +294,18 @@ int aca_build(hodlr2d* h) {
   cudaStream_t s = h->stream;
   const int capmax = h->opts.max_rank;
   const size_t smem = sizeof(double) * (4 * (size_t)capmax + 2);
-  const int64_t ws_budget = (int64_t)1 << 28;  // workspace values per batch (2 GiB)
+  // workspace values per batch: an eighth of the free device memory, between
+  // 2 and 16 GiB, so that the few huge coarse pairs share batches
+  int64_t ws_budget = (int64_t)1 << 28;
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+      ws_budget = std::min<int64_t>(std::max<int64_t>((int64_t)(free_b / 8 / sizeof(double)),
+                                                      (int64_t)1 << 28),
+                                    (int64_t)1 << 31);
+    else
+      (void)cudaGetLastError();
+  }
   hodlr2d_rank_model* model = reinterpret_cast<hodlr2d_rank_model*>(h->opts.rank_model);
   int64_t unconverged = 0, fallbacks = 0, ws_peak = 0;
   for (int l = h->kappa; l >= 1; --l) {  // Alg. 1: levels kappa down to 1
