@@ -108,8 +108,8 @@ struct V2Plan {
   int64_t nproj = 0, nexp = 0, proj_partials = 0, nsides = 0, ntsum = 0;
   int32_t* d_wtask = nullptr;  // task of each projection warp
   int64_t* d_sideq = nullptr;  // (pair side, column) of each chunk-sum warp
-  int lmode[HODLR2D_MAX_LEVELS] = {};  // per level: two-pass, pair or box mode
-  int lpair_small = 1 << 20;           // first pair-mode level with 64-thread blocks
+  int lmode[HODLR2D_MAX_LEVELS] = {};  // per level: base mode (two-pass, pair or box)
+  int lpair_small = 1 << 20;           // first pair level of boxes <= 256 points (profiling)
   BoxWork* d_bw = nullptr;     // box-mode work, boxes <= 64 points
   int64_t nbw = 0;
   int2* d_nearw = nullptr;     // near-field work: (leaf, first target), <= 32 targets

@@ -2,22 +2,28 @@
 // policies: binary64 (F64A), float-float (DF32A), binary32 (F32A) and
 // binary32 sums over bfloat16 factors (BF16A).
 //
-// Far field, by level (the level mode is fixed by the plan):
-//   two-pass (boxes > kFuseRows points): a projection pass t = V^T x over row
-//     chunks, a fixed-order sum of the chunk partials, and an expansion pass
-//     y_X += U t per row box into the level's slab;
-//   pair (boxes of kBoxRows..kFuseRows points): one block per stored pair
-//     (X,Y) computes t1 = V^T x_Y, t2 = U^T x_X and writes the partial
-//     results U t1 (rows of X) and V t2 (rows of Y); one right-hand side uses
-//     k_pairg (each factor value read once, kept in registers between the two
-//     uses), binary64 or several right-hand sides use k_pair;
+// Far field.  The plan gives every level up to three forms; each product
+// picks one per level from the mode and the number of right-hand sides
+// (two_pass_end, box_as_pairs):
+//   two-pass: a projection pass t = V^T x over row chunks (k_proj2; k_projm
+//     or, for bfloat16, the tensor-core k_proj_tc with several right-hand
+//     sides), a fixed-order sum of the chunk partials (k_tsum2), and an
+//     expansion pass y_X += U t per row box into the level's slab (k_exp2;
+//     k_exp_tc for bfloat16 with several right-hand sides);
+//   pairs: one block, warp or sub-warp per stored pair (X,Y) computes
+//     t1 = V^T x_Y, t2 = U^T x_X and writes the partial results U t1 (rows
+//     of X) and V t2 (rows of Y).  The pairs of a level are split into size
+//     classes, one launch each: k_pairs / k_pairg (one right-hand side) and
+//     k_pairm (several) keep each thread's rows of U and V in registers
+//     between the two uses, so each factor value is read once; k_pair
+//     (binary64) reads a pair twice;
 //   box (boxes of <= kBoxRows points): one warp per row box, the box's pairs
 //     staged in shared memory; own sums to the slab, partials for the column
 //     side.
-// Near field: every leaf against itself and its edge sharers, entries
-// evaluated from the points.  The combine pass adds the near field, the
-// slabs and the partials of each point in a fixed order.
-// No atomics anywhere: a product is bitwise reproducible.
+// Near field: every leaf against itself and its edge sharers in work items of
+// at most 32 targets, entries evaluated from the points.  The combine pass
+// adds the near field, the slabs and the partials of each point in a fixed
+// order.  No atomics anywhere: a product is bitwise reproducible.
 #include <algorithm>
 #include <type_traits>
 #include <vector>
