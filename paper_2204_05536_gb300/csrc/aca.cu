@@ -258,6 +258,384 @@ __global__ void k_pack_pairs(const double* const* __restrict__ src,
   for (int64_t t = threadIdx.x; t < cnt[p]; t += blockDim.x) d[t] = s[t];
 }
 
+// ---------------------------------------------------------------------------
+// Wide ACA: the same steps for pairs too large for one thread block (boxes of
+// hundreds of thousands of points at the coarse levels), each step spread
+// over many blocks and driven from the host one term at a time:
+//   k_wrow   residual row i over column chunks; argmax partial per chunk
+//   k_wpiv   pivot (chunk partials in chunk order), row i marked used; a zero
+//            pivot moves to the unused row of smallest original index
+//   k_wcol   v scaled by the pivot, residual column u over row chunks; chunk
+//            partials of V_q . v, U_q . u (q <= k) and argmax |u| (unused)
+//   k_wfin   |S_k|_F^2 update (partials in chunk order), stopping test, next
+//            row
+// The residual entries are the k_aca ones (same expressions, same order over
+// q); the dot products sum in a different order, so the stopping test can in
+// principle decide differently on an exact tie.
+// ---------------------------------------------------------------------------
+constexpr int kWideChunk = 4096;  // elements per block
+constexpr int64_t kWideRows = 24576;  // |X| + |Y| from which a pair runs wide
+constexpr int kWideT = 256;
+
+struct WideState {
+  int64_t p;             // pair of the level
+  int64_t wsoff, fgoff;  // workspace (U then V) and row-flag offsets
+  int32_t xs, m, ys, n, cap, kfull;
+  int32_t k, i, jp, nused;
+  int32_t active, conv, skip;  // skip: this term's column step is not run
+  int32_t ncm, ncn;            // row / column chunks
+  int64_t cm0, cn0;            // first chunk of this pair in the row / column chunk lists
+  double S2, piv;
+};
+
+struct WideArgs {
+  AcaArgs A;
+  WideState* st;
+  int nw;
+  const int2* rchunks;  // (pair, chunk) over the rows of X
+  const int2* cchunks;  // (pair, chunk) over the rows of Y
+  int64_t nr;           // row chunks (column chunks follow them in ppiv, pdot)
+  Piv* ppiv;            // per chunk argmax partials: rows of X, then rows of Y
+  double* pdot;         // per chunk: dots of q = 0..cap (cap + 1 values)
+  double* svec;         // per pair: V(jp, q), q < cap
+  int cap;              // largest cap of the batch
+};
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < kWideT / 32; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// first row of every wide pair: the point of X with the smallest original index
+__global__ void __launch_bounds__(kWideT) k_winit(WideArgs W) {
+  __shared__ Piv red[kWideT / 32];
+  WideState& S = W.st[blockIdx.x];
+  const AcaArgs& A = W.A;
+  uint8_t* used = A.flags + S.fgoff;
+  const int64_t* G0 = A.perm + S.xs;
+  Piv best = piv_none();
+  for (int t = threadIdx.x; t < S.m; t += kWideT) {
+    used[t] = 0;
+    const Piv c{0.0, G0[t], t};
+    if (piv_better(c, best)) best = c;
+  }
+  best = block_piv<kWideT>(best, red);
+  if (threadIdx.x == 0) {
+    S.i = best.pos;
+    S.k = 0;
+    S.nused = 0;
+    S.S2 = 0.0;
+    S.active = S.cap > 0 && S.m > 0 ? 1 : 0;
+    S.conv = S.active ? 0 : (S.kfull == 0 ? 1 : 0);
+    S.skip = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kWideT) k_wrow(WideArgs W, int64_t nchunks) {
+  __shared__ Piv red[kWideT / 32];
+  __shared__ double s_u[256];
+  const int64_t b = blockIdx.x;
+  if (b >= nchunks) return;
+  const int2 pc = W.cchunks[b];
+  WideState& S = W.st[pc.x];
+  if (!S.active) return;
+  const AcaArgs& A = W.A;
+  const int k = S.k, i = S.i;
+  double* U = A.ws + S.wsoff;
+  double* V = U + (int64_t)S.m * S.cap;
+  for (int q = threadIdx.x; q < k; q += kWideT) s_u[q] = U[(int64_t)q * S.m + i];
+  __syncthreads();
+  const double xi = A.x[S.xs + i], yi = A.y[S.xs + i];
+  const int64_t gi = A.perm[S.xs + i];
+  const double* X1 = A.x + S.ys;
+  const double* Y1 = A.y + S.ys;
+  const int64_t* G1 = A.perm + S.ys;
+  double* Vk = V + (int64_t)k * S.n;
+  Piv jb = piv_none();
+  const int j0 = pc.y * kWideChunk, j1 = min(S.n, j0 + kWideChunk);
+  for (int j = j0 + threadIdx.x; j < j1; j += kWideT) {
+    double r = entry(A.kp, xi, yi, gi, X1[j], Y1[j], G1[j]);
+    for (int q = 0; q < k; ++q) r -= s_u[q] * V[(int64_t)q * S.n + j];
+    Vk[j] = r;
+    const Piv c{fabs(r), G1[j], j};
+    if (piv_better(c, jb)) jb = c;
+  }
+  jb = block_piv<kWideT>(jb, red);
+  if (threadIdx.x == 0) W.ppiv[W.nr + b] = jb;
+}
+
+__global__ void __launch_bounds__(kWideT) k_wpiv(WideArgs W) {
+  __shared__ Piv red[kWideT / 32];
+  WideState& S = W.st[blockIdx.x];
+  if (!S.active) return;
+  const AcaArgs& A = W.A;
+  // column pivot: the best of the column chunks, in chunk order
+  Piv jb = piv_none();
+  for (int c = threadIdx.x; c < S.ncn; c += kWideT) {
+    const Piv v = W.ppiv[W.nr + S.cn0 + c];
+    if (piv_better(v, jb)) jb = v;
+  }
+  jb = block_piv<kWideT>(jb, red);
+  uint8_t* used = A.flags + S.fgoff;
+  double* U = A.ws + S.wsoff;
+  double* V = U + (int64_t)S.m * S.cap;
+  const int k = S.k;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    used[S.i] = 1;
+    S.nused += 1;
+    S.skip = 0;
+  }
+  if (jb.pos < 0) {  // every residual entry is NaN: give up on this block
+    if (threadIdx.x == 0) {
+      S.active = 0;
+      S.conv = (S.k == S.kfull || S.nused == S.m) ? 1 : 0;
+    }
+    return;
+  }
+  const double piv = V[(int64_t)k * S.n + jb.pos];
+  __syncthreads();  // used[i] is set before the search below
+  if (piv == 0.0) {  // next unused row of smallest original index
+    const int64_t* G0 = A.perm + S.xs;
+    Piv nb = piv_none();
+    for (int t = threadIdx.x; t < S.m; t += kWideT)
+      if (!used[t]) {
+        const Piv c{0.0, G0[t], t};
+        if (piv_better(c, nb)) nb = c;
+      }
+    nb = block_piv<kWideT>(nb, red);
+    if (threadIdx.x == 0) {
+      S.skip = 1;
+      if (nb.pos < 0 || S.nused >= S.m) {
+        S.active = 0;
+        S.conv = (S.k == S.kfull || S.nused == S.m) ? 1 : 0;
+      } else {
+        S.i = nb.pos;
+      }
+    }
+    return;
+  }
+  // V(jp, q) of the scaled columns q < k, for the residual column
+  double* sv = W.svec + (int64_t)blockIdx.x * W.cap;
+  for (int q = threadIdx.x; q < k; q += kWideT) sv[q] = V[(int64_t)q * S.n + jb.pos];
+  if (threadIdx.x == 0) {
+    S.jp = jb.pos;
+    S.piv = piv;
+  }
+}
+
+// blocks [0, nr) over the rows of X, then [nr, nr + nc) over the rows of Y
+__global__ void __launch_bounds__(kWideT) k_wcol(WideArgs W, int64_t nc) {
+  __shared__ Piv red[kWideT / 32];
+  __shared__ double dred[kWideT / 32];
+  __shared__ double s_v[256];
+  const int64_t b = blockIdx.x, nr = W.nr;
+  if (b >= nr + nc) return;
+  const bool rows_x = b < nr;
+  const int2 pc = rows_x ? W.rchunks[b] : W.cchunks[b - nr];
+  WideState& S = W.st[pc.x];
+  if (!S.active || S.skip) return;
+  const AcaArgs& A = W.A;
+  const int k = S.k;
+  double* U = A.ws + S.wsoff;
+  double* V = U + (int64_t)S.m * S.cap;
+  double* out = W.pdot + b * (int64_t)(W.cap + 1);
+  if (rows_x) {
+    const double* sv = W.svec + (int64_t)pc.x * W.cap;
+    for (int q = threadIdx.x; q < k; q += kWideT) s_v[q] = sv[q];
+    __syncthreads();
+    const int64_t gjp = A.perm[S.ys + S.jp];
+    const double xj = A.x[S.ys + S.jp], yj = A.y[S.ys + S.jp];
+    const double* X0 = A.x + S.xs;
+    const double* Y0 = A.y + S.xs;
+    const int64_t* G0 = A.perm + S.xs;
+    const uint8_t* used = A.flags + S.fgoff;
+    double* Uk = U + (int64_t)k * S.m;
+    const int t0 = pc.y * kWideChunk, t1 = min(S.m, t0 + kWideChunk);
+    Piv nb = piv_none();
+    for (int t = t0 + threadIdx.x; t < t1; t += kWideT) {
+      double u = entry(A.kp, X0[t], Y0[t], G0[t], xj, yj, gjp);
+      for (int q = 0; q < k; ++q) u -= U[(int64_t)q * S.m + t] * s_v[q];
+      Uk[t] = u;
+      if (!used[t]) {
+        const Piv c{fabs(u), G0[t], t};
+        if (piv_better(c, nb)) nb = c;
+      }
+    }
+    nb = block_piv<kWideT>(nb, red);
+    if (threadIdx.x == 0) W.ppiv[b] = nb;
+    __syncthreads();
+    for (int q = 0; q <= k; ++q) {  // U_q . u over this chunk
+      double a = 0.0;
+      for (int t = t0 + threadIdx.x; t < t1; t += kWideT) a += U[(int64_t)q * S.m + t] * Uk[t];
+      a = block_sum(a, dred);
+      if (threadIdx.x == 0) out[q] = a;
+    }
+  } else {
+    double* Vk = V + (int64_t)k * S.n;
+    const int j0 = pc.y * kWideChunk, j1 = min(S.n, j0 + kWideChunk);
+    for (int j = j0 + threadIdx.x; j < j1; j += kWideT) Vk[j] = Vk[j] / S.piv;
+    __syncthreads();
+    for (int q = 0; q <= k; ++q) {  // V_q . v over this chunk
+      double a = 0.0;
+      for (int j = j0 + threadIdx.x; j < j1; j += kWideT) a += V[(int64_t)q * S.n + j] * Vk[j];
+      a = block_sum(a, dred);
+      if (threadIdx.x == 0) out[q] = a;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWideT) k_wfin(WideArgs W) {
+  __shared__ Piv red[kWideT / 32];
+  __shared__ double s_du[257], s_dv[257];
+  WideState& S = W.st[blockIdx.x];
+  if (!S.active || S.skip) return;
+  const int k = S.k;
+  const int64_t stride = W.cap + 1, nr = W.nr;
+  for (int q = threadIdx.x; q <= k; q += kWideT) {  // chunk partials in chunk order
+    double a = 0.0, v = 0.0;
+    for (int c = 0; c < S.ncm; ++c) a += W.pdot[(S.cm0 + c) * stride + q];
+    for (int c = 0; c < S.ncn; ++c) v += W.pdot[(nr + S.cn0 + c) * stride + q];
+    s_du[q] = a;
+    s_dv[q] = v;
+  }
+  Piv nb = piv_none();
+  for (int c = threadIdx.x; c < S.ncm; c += kWideT) {
+    const Piv v = W.ppiv[S.cm0 + c];
+    if (piv_better(v, nb)) nb = v;
+  }
+  nb = block_piv<kWideT>(nb, red);  // also publishes s_du / s_dv
+  if (threadIdx.x != 0) return;
+  double cross = 0.0;
+  for (int q = 0; q < k; ++q) cross += s_du[q] * s_dv[q];
+  const double uu = s_du[k], vv = s_dv[k];
+  S.S2 += 2.0 * cross + uu * vv;
+  S.k = k + 1;
+  if (sqrt(uu) * sqrt(vv) <= W.A.eps * sqrt(fmax(S.S2, 0.0))) {
+    S.active = 0;
+    S.conv = 1;
+    return;
+  }
+  if (S.k >= S.cap || S.nused >= S.m || nb.pos < 0) {
+    S.active = 0;
+    S.conv = (S.k == S.kfull || S.nused == S.m) ? 1 : 0;
+    return;
+  }
+  S.i = nb.pos;
+}
+
+__global__ void k_wdone(const WideState* __restrict__ st, int nw, int32_t* __restrict__ rank,
+                        int32_t* __restrict__ conv, int32_t* __restrict__ nactive) {
+  int a = 0;
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+    const WideState& S = st[w];
+    rank[S.p] = S.k;
+    conv[S.p] = S.active ? 0 : S.conv;
+    a += S.active;
+  }
+  a = __reduce_add_sync(0xffffffffu, a);
+  if (threadIdx.x == 0) *nactive = a;
+}
+
+// Runs the wide pairs of a batch to completion (states filled with p, wsoff,
+// fgoff, xs, m, ys, n, cap <= 256, kfull); fills rank[p] and conv[p] like
+// k_aca.
+static int aca_wide(const AcaArgs& A, std::vector<WideState> st, cudaStream_t s) {
+  const int nw = (int)st.size();
+  if (nw == 0) return HODLR2D_OK;
+  std::vector<int2> rch, cch;
+  int cap = 1;
+  int64_t max_rounds = 0;
+  for (int w = 0; w < nw; ++w) {
+    WideState& S = st[w];
+    S.ncm = (int32_t)((S.m + kWideChunk - 1) / kWideChunk);
+    S.ncn = (int32_t)((S.n + kWideChunk - 1) / kWideChunk);
+    S.cm0 = (int64_t)rch.size();
+    S.cn0 = (int64_t)cch.size();
+    for (int c = 0; c < S.ncm; ++c) rch.push_back(make_int2(w, c));
+    for (int c = 0; c < S.ncn; ++c) cch.push_back(make_int2(w, c));
+    cap = std::max(cap, S.cap);
+    // a term per round, or a used row without a term (zero pivot)
+    max_rounds = std::max<int64_t>(max_rounds, (int64_t)S.cap + S.m);
+  }
+  if (cap > 256) return HODLR2D_ERR_ARG;  // the shared vectors hold 256 terms
+  const int64_t nr = (int64_t)rch.size(), nc = (int64_t)cch.size();
+  WideArgs W;
+  W.A = A;
+  W.nw = nw;
+  W.cap = cap;
+  W.nr = nr;
+  WideState* d_st = nullptr;
+  int2 *d_r = nullptr, *d_c = nullptr;
+  Piv* d_piv = nullptr;
+  double *d_dot = nullptr, *d_sv = nullptr;
+  int32_t* d_na = nullptr;
+  int rc = HODLR2D_OK;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == HODLR2D_OK) {
+      (void)cudaGetLastError();
+      rc = e == cudaErrorMemoryAllocation ? HODLR2D_ERR_OOM : HODLR2D_ERR_CUDA;
+    }
+  };
+  ck(cudaMalloc(&d_st, sizeof(WideState) * nw));
+  ck(cudaMalloc(&d_r, sizeof(int2) * nr));
+  ck(cudaMalloc(&d_c, sizeof(int2) * nc));
+  ck(cudaMalloc(&d_piv, sizeof(Piv) * (nr + nc)));
+  ck(cudaMalloc(&d_dot, sizeof(double) * (nr + nc) * (cap + 1)));
+  ck(cudaMalloc(&d_sv, sizeof(double) * nw * cap));
+  ck(cudaMalloc(&d_na, sizeof(int32_t)));
+  int32_t* h_na = nullptr;
+  ck(cudaMallocHost(&h_na, sizeof(int32_t)));
+  if (rc == HODLR2D_OK) {
+    ck(cudaMemcpyAsync(d_st, st.data(), sizeof(WideState) * nw, cudaMemcpyHostToDevice, s));
+    ck(cudaMemcpyAsync(d_r, rch.data(), sizeof(int2) * nr, cudaMemcpyHostToDevice, s));
+    ck(cudaMemcpyAsync(d_c, cch.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+  }
+  W.st = d_st;
+  W.rchunks = d_r;
+  W.cchunks = d_c;
+  W.ppiv = d_piv;
+  W.pdot = d_dot;
+  W.svec = d_sv;
+  if (rc == HODLR2D_OK) {
+    k_winit<<<nw, kWideT, 0, s>>>(W);
+    ck(cudaGetLastError());
+  }
+  for (int64_t round = 0; rc == HODLR2D_OK && round < max_rounds; ++round) {
+    k_wrow<<<(unsigned)nc, kWideT, 0, s>>>(W, nc);
+    k_wpiv<<<nw, kWideT, 0, s>>>(W);
+    k_wcol<<<(unsigned)(nr + nc), kWideT, 0, s>>>(W, nc);
+    k_wfin<<<nw, kWideT, 0, s>>>(W);
+    ck(cudaGetLastError());
+    if (round % 4 == 3 || round + 1 == max_rounds) {  // poll every fourth round
+      k_wdone<<<1, 32, 0, s>>>(d_st, nw, A.rank, A.conv, d_na);
+      ck(cudaGetLastError());
+      ck(cudaMemcpyAsync(h_na, d_na, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      ck(cudaStreamSynchronize(s));
+      if (rc == HODLR2D_OK && *h_na == 0) break;
+    }
+  }
+  if (rc == HODLR2D_OK) {  // ranks of pairs that finished before the last poll
+    k_wdone<<<1, 32, 0, s>>>(d_st, nw, A.rank, A.conv, d_na);
+    ck(cudaGetLastError());
+    ck(cudaStreamSynchronize(s));
+  }
+  cudaFree(d_st);
+  cudaFree(d_r);
+  cudaFree(d_c);
+  cudaFree(d_piv);
+  cudaFree(d_dot);
+  cudaFree(d_sv);
+  cudaFree(d_na);
+  cudaFreeHost(h_na);
+  return rc;
+}
+
 int mlp_predict_device(hodlr2d_rank_model* M, const float* d_feats, int64_t n, float* d_out,
                        cudaStream_t s);
 
@@ -381,11 +759,19 @@ int aca_build(hodlr2d* h) {
         }
         const int64_t nbp = (int64_t)(b1 - b0);
         ws_peak = std::max(ws_peak, wtot);
+        // pairs for one block each first, then the wide ones
+        std::vector<int64_t> order(todo.begin() + b0, todo.begin() + b1);
+        auto is_wide = [&](int64_t p) {
+          return mm[p] + nn[p] >= kWideRows && caps[p] <= 256;
+        };
+        std::stable_partition(order.begin(), order.end(), [&](int64_t p) { return !is_wide(p); });
+        int64_t nnarrow = 0;
+        while (nnarrow < nbp && !is_wide(order[nnarrow])) ++nnarrow;
         std::vector<int64_t> plist(nbp), wsoff(nbp), fgoff(nbp);
         std::vector<int32_t> bcap(nbp);
         int64_t wo = 0, fo = 0;
         for (int64_t i = 0; i < nbp; ++i) {
-          const int64_t p = todo[b0 + i];
+          const int64_t p = order[i];
           plist[i] = p;
           bcap[i] = caps[p];
           wsoff[i] = wo;
@@ -429,11 +815,31 @@ int aca_build(hodlr2d* h) {
         A.conv = d_conv;
         A.plist = d_plist;
         A.bcap = d_bcap;
-        if (mean_rows <= 96)
-          k_aca<64><<<(unsigned)nbp, 64, smem, s>>>(A);
-        else
-          k_aca<256><<<(unsigned)nbp, 256, smem, s>>>(A);
-        H2D_CK(cudaGetLastError());
+        if (nnarrow > 0) {
+          if (mean_rows <= 96)
+            k_aca<64><<<(unsigned)nnarrow, 64, smem, s>>>(A);
+          else
+            k_aca<256><<<(unsigned)nnarrow, 256, smem, s>>>(A);
+          H2D_CK(cudaGetLastError());
+        }
+        if (nnarrow < nbp) {
+          std::vector<WideState> wst;
+          for (int64_t i = nnarrow; i < nbp; ++i) {
+            const int64_t p = plist[i];
+            WideState S{};
+            S.p = p;
+            S.wsoff = wsoff[i];
+            S.fgoff = fgoff[i];
+            S.xs = h->h_leaf_off[(int64_t)px[p] << sh];
+            S.ys = h->h_leaf_off[(int64_t)py[p] << sh];
+            S.m = (int32_t)mm[p];
+            S.n = (int32_t)nn[p];
+            S.kfull = (int32_t)std::min(mm[p], nn[p]);
+            S.cap = bcap[i];
+            wst.push_back(S);
+          }
+          H2D_TRY(aca_wide(A, std::move(wst), s));
+        }
         std::vector<int32_t> rk(np), cv(np);
         H2D_CK(cudaMemcpyAsync(rk.data(), L.d_rank, 4 * np, cudaMemcpyDeviceToHost, s));
         H2D_CK(cudaMemcpyAsync(cv.data(), d_conv, 4 * np, cudaMemcpyDeviceToHost, s));
