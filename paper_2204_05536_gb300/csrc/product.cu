@@ -45,8 +45,8 @@ constexpr int kChunk2 = 256;      // rows of one expansion task of the two-pass 
 constexpr int kExpMaxEnt = 64;    // largest list of a box (15 pairs, two sides, margin)
 constexpr int kChunkP = 512;      // rows of one projection task (16 per lane)
 // Two-pass levels whose boxes hold at most kDualRows points also get a pair
-// plan; binary32 / bfloat16 products with one right-hand side run them as
-// pairs (each factor value read once) instead of in two passes.
+// plan; products with one right-hand side (not binary64) run them as pairs
+// (each factor value read once) instead of in two passes.
 constexpr int kDualRows = 512 * 9;
 // With several right-hand sides, boxes of more than kMultiRows points run in
 // two passes (each factor value read twice for all of them); smaller ones run
@@ -1323,14 +1323,14 @@ static bool box_as_pairs(const hodlr2d* h, int l, int nrhs, int mode) {
 // First level that is not run in two passes by a product:
 //   binary64                    lfuse (pairs from there on)
 //   several right-hand sides    l2max (boxes of <= kMultiRows points as pairs)
-//   one, binary32 / bfloat16    ldual (the 512 x 9 register form holds the
-//                               boxes of [ldual, lfuse))
-//   one, float-float            lfuse
+//   one right-hand side         ldual (the 512 x 9 register forms hold the
+//                               boxes of [ldual, lfuse): two columns per
+//                               step in binary32, one in float-float)
 static int two_pass_end(const hodlr2d* h, int nrhs, int mode) {
   const V2Plan& V = h->v2;
   if (mode == HODLR2D_MODE_F64) return V.lfuse;
   if (nrhs > 1) return V.l2max;
-  return (mode == HODLR2D_MODE_F32 || mode == HODLR2D_MODE_BF16) ? V.ldual : V.lfuse;
+  return V.ldual;
 }
 
 static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
@@ -1689,6 +1689,8 @@ static int launch_pair_reg(const int2* work, int64_t nw, int rows, const ArgsV2&
     k_pairg<A, 512, 5, 2><<<nb, 512, 0, st>>>(P, work, xt, ppart);
   else if (rows <= kDualRows && b32) {
     if constexpr (b32) k_pairg<A, 512, 9, 2><<<nb, 512, 0, st>>>(P, work, xt, ppart);
+  } else if (rows <= kDualRows && !b32) {
+    if constexpr (!b32) k_pairg<A, 512, 9, 1><<<nb, 512, 0, st>>>(P, work, xt, ppart);
   } else
     return launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st);
   H2D_CK(cudaGetLastError());
