@@ -153,11 +153,12 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# ncu DRAM traffic (read + write bytes per launch) of the dominant kernel at
-# the headline workload, keyed by (phase, mode, n): k_proj2 (DF32) measured at
-# N = 2^17 (522.9 MB for 64.33e6 two-pass values) and scaled by the values of
-# a full N = 2^20 launch (846.1e6).  Remove an entry when its kernel changes.
-NCU_TRAFFIC = {("proj", "df32", 1 << 20): 6.878e9}
+# ncu DRAM traffic (read + write bytes) per algorithmic byte of a kernel,
+# keyed by (phase, mode): k_proj2 (DF32) measured at N = 2^17, 522.9 MB for
+# 514.6 MB of factor values.  Traffic grows with the values, so a launch's
+# traffic is this ratio times its algorithmic bytes.  Remove an entry when its
+# kernel changes.
+NCU_TRAFFIC_RATIO = {("proj", "df32"): 522.9 / 514.6}
 
 
 def cpu_baseline_leg(rows, x, pts, n):
@@ -648,7 +649,8 @@ def run_ours(args, ws, rank, local):
                      "peak_source": peak_src, "bytes_per_launch": bytes_step,
                      "ms_per_launch": round(per_launch_ms, 4),
                      "launches_per_product": d["launches"] // args.steps,
-                     "traffic": NCU_TRAFFIC.get((dom, mode, n))},
+                     "traffic": (round(NCU_TRAFFIC_RATIO[(dom, mode)] * bytes_step)
+                                 if (dom, mode) in NCU_TRAFFIC_RATIO else None)},
         "hbm_frac_product": round(hbm_frac_product, 4),
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms",
                 "h2d_bytes_per_step": 8 * n * R, "d2h_bytes_per_step": 8 * n * R},

@@ -37,7 +37,7 @@ namespace h2d {
 #define H2D_FUSE_ROWS 2048
 #endif
 #ifndef H2D_BOX_STAGE
-#define H2D_BOX_STAGE 1024
+#define H2D_BOX_STAGE 960
 #endif
 constexpr int kFuseRows = H2D_FUSE_ROWS;  // largest box handled by the single-read kernels
 constexpr int kSmallPair = 256;   // boxes up to this size: 64-thread pair blocks
@@ -674,13 +674,16 @@ __global__ void __launch_bounds__(128)
 // ---------------------------------------------------------------------------
 // box mode (finest levels, boxes of <= kBoxRows points): one warp per row box
 // X, its stored pairs one after another.  A pair that fits kBoxStage values is
-// copied to the warp's shared-memory slice (coalesced), then
+// copied to one of the warp's two shared-memory slices with asynchronous
+// copies (cp.async, 16 bytes per lane and copy) while the previous pair is
+// computed from the other slice, then
 //   lane q < 2k: one column's dot product (V columns -> t1, U columns -> t2),
 //                rows visited from q onwards (mod rows) so that the lanes hit
 //                distinct banks;
 //   lanes over rows: y_X += U t1 kept in registers, V t2 written as the
 //                partial of Y.
 // A larger pair is read from global memory with one warp per column instead.
+// The slices are dynamic shared memory (kBoxSmem bytes per block).
 // ---------------------------------------------------------------------------
 constexpr int kBoxRows = 64;
 constexpr int kBoxStage = H2D_BOX_STAGE;
@@ -689,26 +692,54 @@ constexpr int kBoxWarps = 4;
 
 constexpr int kBoxMaxPairs = 16;  // row pairs of one box (at most 15)
 
+// bytes per warp: two factor slices (8-byte values at most), two x_Y slices,
+// x_X, the 2k projections and the box's pair records
+constexpr int kBoxWarpSmem = 2 * kBoxStage * 8 + 2 * kBoxRows * 8 + kBoxRows * 8 +
+                             2 * kBoxK * 8 + kBoxMaxPairs * (int)sizeof(PairMeta);
+constexpr int kBoxSmem = kBoxWarps * kBoxWarpSmem;
+static_assert(kBoxStage % 2 == 0 && kBoxWarpSmem % 16 == 0, "16-byte aligned slices");
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+template <int B>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
+  static_assert(B == 4 || B == 8, "cp.async.ca copies 4 or 8 bytes here");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "n"(B)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 template <class A>
 __global__ void __launch_bounds__(32 * kBoxWarps)
     k_box(ArgsV2 P, const BoxWork* __restrict__ work, int64_t nwork,
           const typename A::val* __restrict__ xt, typename A::val* __restrict__ yl,
           typename A::val* __restrict__ ppart) {
   using V = typename A::val;
+  using F = typename A::fac;
   using Acc = typename A::acc;
-  __shared__ V st_all[kBoxWarps][kBoxStage];
-  __shared__ V xx_all[kBoxWarps][kBoxRows];
-  __shared__ V xy_all[kBoxWarps][kBoxRows];
-  __shared__ V ts_all[kBoxWarps][2 * kBoxK];
-  __shared__ PairMeta pm_all[kBoxWarps][kBoxMaxPairs];
+  static_assert(sizeof(F) <= 8 && sizeof(V) <= 8, "slice sizes assume 8-byte values at most");
+  extern __shared__ __align__(16) unsigned char box_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t wid = (int64_t)blockIdx.x * kBoxWarps + warp;
   if (wid >= nwork) return;
-  V* st = st_all[warp];
-  V* xx = xx_all[warp];
-  V* xy = xy_all[warp];
-  V* ts = ts_all[warp];
-  PairMeta* pm = pm_all[warp];
+  unsigned char* ws = box_smem + (size_t)warp * kBoxWarpSmem;
+  F* st2 = reinterpret_cast<F*>(ws);                        // [2][kBoxStage]
+  V* xy2 = reinterpret_cast<V*>(ws + 2 * kBoxStage * 8);  // [2][kBoxRows]
+  V* xx = xy2 + 2 * kBoxRows;
+  V* ts = xx + kBoxRows;
+  PairMeta* pm = reinterpret_cast<PairMeta*>(ts + 2 * kBoxK);
   const BoxWork wk = work[wid];
   const int l = wk.level;
   if (P.lmode[l] != LMODE_BOX) return;  // this level runs as pairs in this product
@@ -718,38 +749,63 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
   const int npb = wk.np;
   if (lane < npb) pm[lane] = L.meta[wk.p0 + lane];
   __syncwarp();
-  using F = typename A::fac;
   const F* fac = reinterpret_cast<const F*>(L.fac);
+  auto fits = [&](const PairMeta& PM) {
+    return (ldpad(PM.m) + ldpad(PM.n)) * (int64_t)PM.k <= kBoxStage && PM.k <= kBoxK;
+  };
   for (int c = 0; c < P.nrhs; ++c) {
     const V* xc = xt + (int64_t)c * P.n;
+    // copies of pair ip (factors if they fit, and x_Y) into slice b
+    auto issue = [&](int ip, int b) {
+      const PairMeta& PM = pm[ip];
+      F* st = st2 + b * kBoxStage;
+      V* xy = xy2 + b * kBoxRows;
+      if (fits(PM)) {
+        const F* Ug = fac + PM.foff;
+        const int64_t tot = (ldpad(m) + ldpad(PM.n)) * (int64_t)PM.k;
+        if constexpr (sizeof(F) == 8) {
+          // pairs start at even values and hold an even count: 16-byte units
+          for (int64_t e = lane; 2 * e < tot; e += 32) cp_async16(st + 2 * e, Ug + 2 * e);
+        } else {
+          for (int64_t e = lane; e < tot; e += 32) st[e] = Ug[e];
+        }
+      }
+      for (int j = lane; j < PM.n; j += 32) cp_async_small<sizeof(V)>(xy + j, xc + PM.ys + j);
+      cp_async_commit();
+    };
     for (int i = lane; i < m; i += 32) xx[i] = xc[xs + i];
+    if (npb > 0) issue(0, 0);
     Acc y0 = A::zero(), y1 = A::zero();  // rows lane and lane + 32
     for (int ip = 0; ip < npb; ++ip) {
+      const int b = ip & 1;
+      if (ip + 1 < npb) {
+        issue(ip + 1, b ^ 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();  // every lane's copies of slice b (and x_X) are visible
       const PairMeta& PM = pm[ip];
       const int k = PM.k;
-      const int32_t ys = PM.ys, n = PM.n;
+      const int32_t n = PM.n;
       const int64_t ln = ldpad(n);
       const F* Ug = fac + PM.foff;
       const F* Vg = Ug + lm * k;
+      const V* xy = xy2 + b * kBoxRows;
       V* outy = ppart + (int64_t)c * P.pstride + PM.ppy;
-      for (int j = lane; j < n; j += 32) xy[j] = xc[ys + j];
-      const int64_t tot = (lm + ln) * k;
-      __syncwarp();
-      if (tot <= kBoxStage && k <= kBoxK) {
-        for (int64_t e = lane; e < tot; e += 32) st[e] = A::ld(Ug[e]);
-        __syncwarp();
-        const V* Us = st;
-        const V* Vs = st + lm * k;
+      if (fits(PM)) {
+        const F* Us = st2 + b * kBoxStage;
+        const F* Vs = Us + lm * k;
         for (int job = lane; job < 2 * k; job += 32) {
           const bool isV = job < k;
           const int q = isV ? job : job - k;
           const int rows = isV ? n : m;
-          const V* col = isV ? Vs + q * ln : Us + q * lm;
+          const F* col = isV ? Vs + q * ln : Us + q * lm;
           const V* xv = isV ? xy : xx;
           Acc a = A::zero();
           int r = q;  // q < k <= rows
           for (int u = 0; u < rows; ++u) {
-            A::fma(a, col[r], xv[r]);
+            A::fma(a, A::ld(col[r]), xv[r]);
             if (++r == rows) r = 0;
           }
           ts[job] = A::fin(a);
@@ -758,11 +814,11 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
         for (int r = lane; r < m + n; r += 32) {
           const bool own = r < m;
           const int i = own ? r : r - m;
-          const V* M = own ? Us + i : Vs + i;
+          const F* M = own ? Us + i : Vs + i;
           const int64_t ld = own ? lm : ln;
           const V* tv = own ? ts : ts + k;
           Acc a = own ? (i < 32 ? y0 : y1) : A::zero();
-          for (int q = 0; q < k; ++q) A::fma(a, M[q * ld], tv[q]);
+          for (int q = 0; q < k; ++q) A::fma(a, A::ld(M[q * ld]), tv[q]);
           if (own) {
             if (i < 32) y0 = a;
             else y1 = a;
@@ -800,7 +856,7 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
           }
         }
       }
-      __syncwarp();
+      __syncwarp();  // slice b and ts are free for the next copies
     }
     V* own = yl + ((int64_t)l * P.nrhs + c) * P.n + xs;
     if (lane < m) own[lane] = A::fin(y0);
@@ -1365,6 +1421,11 @@ int plan_v2(hodlr2d* h) {
   V2Plan& V = h->v2;
   if (V.ready) return HODLR2D_OK;
   const int kappa = h->kappa;
+  // the box kernel's two slices per warp exceed the default 48 KB
+  H2D_CK(cudaFuncSetAttribute(k_box<F64A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
+  H2D_CK(cudaFuncSetAttribute(k_box<DF32A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
+  H2D_CK(cudaFuncSetAttribute(k_box<F32A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
+  H2D_CK(cudaFuncSetAttribute(k_box<BF16A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
   auto maxcount = [&](int l) {
     const int sh = 2 * (kappa - l);
     int64_t mx = 0;
@@ -1855,7 +1916,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
     if (P.lmode[l] == LMODE_BOX) box_vals += h->lev[l].nstored;
   if (V.nbw && box_vals) {
     PhaseScope ps(h, 7, 1, fs * box_vals, sf);
-    k_box<A><<<(unsigned)((V.nbw + kBoxWarps - 1) / kBoxWarps), 32 * kBoxWarps, 0, sf>>>(
+    k_box<A><<<(unsigned)((V.nbw + kBoxWarps - 1) / kBoxWarps), 32 * kBoxWarps, kBoxSmem, sf>>>(
         P, V.d_bw, V.nbw, xt, yl, ppart);
   }
   H2D_CK(cudaEventRecord(V.ev_far, sf));
