@@ -415,3 +415,34 @@ def test_gmres_mixed_refinement(h2d, oracle, mode):
     x, it, rr, code = g.gmres(torch.from_numpy(f).cuda(), tol=1e-10, inner_mode=mode)
     assert code == 0 and rr <= 1e-10
     assert rel(x.cpu().numpy(), lam) <= 1e-8
+
+
+@pytest.mark.parametrize("mode", ["f64", "df32"])
+def test_box_pairs_larger_than_a_slice(h2d, oracle, mode):
+    """Box-mode levels (boxes of <= 64 points in binary64, <= 48 in
+    float-float) whose pairs hold more values than one shared-memory slice of
+    the box kernel (960) are read from global memory instead of staged; with
+    eps = 1e-12 the finest pairs have ranks that force that path.  Checked
+    against the oracle's product on the same factors (P1)."""
+    if mode == "f64":  # exactly 64 points per leaf
+        pts, _ = inputs.jittered_grid(64, seed=0)
+        kind, a, leaf = "log", 0.0, 64
+    else:
+        pts = inputs.uniform(4096, seed=7)
+        kind, a, leaf = "imq", 1.0 / 64, 48
+    eps = 1e-12
+    o = oracle.Oracle(pts, oracle.kernel(kind, a), leaf, eps)
+    kappa = o.kappa
+    big = [d for d, U, V in o.pairs()
+           if d["level"] == kappa
+           and (U.shape[0] + U.shape[0] % 2 + V.shape[0] + V.shape[0] % 2) * d["rank"] > 960]
+    assert big, "no finest-level pair exceeds a slice: the case does not test the path"
+    g = h2d.HODLR2D(pts, h2d.kernel(kind, a), leaf, eps, compress=False)
+    g.import_factors(*o.export_factors())
+    if mode == "df32":
+        g.prepare("df32")
+    for nrhs in (1, 2):
+        x = inputs.rhs(len(pts), nrhs, seed=2)
+        y_o = o.matvec(x)
+        y_g = g.matvec(torch.from_numpy(np.ascontiguousarray(x)).cuda(), mode=mode).cpu().numpy()
+        assert rel(y_g, y_o) <= 1e-12
