@@ -141,6 +141,7 @@ static void free_handle(hodlr2d* h) {
     cudaFree(L.d_ent);
     cudaFree(L.d_prow);
     cudaFree(L.d_ppoff);
+    cudaFree(L.d_entpp);
     cudaFree(L.d_meta);
   }
   cudaFree(h->d_proj);

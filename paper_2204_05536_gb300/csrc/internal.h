@@ -62,6 +62,7 @@ struct Level {
   int32_t* d_ent_off = nullptr;  // 4^l + 1
   int32_t* d_ent = nullptr;
   int64_t nent = 0;
+  int64_t* d_entpp = nullptr;  // per entry: partial offset << 1 | side (pair-planned levels)
   std::vector<int32_t> h_rank;   // host copy of the ranks
   std::vector<int64_t> h_foff;
 };

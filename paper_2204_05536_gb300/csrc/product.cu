@@ -65,6 +65,7 @@ struct LevelV2 {
   const int32_t* ent;
   const void* fac;
   const PairMeta* meta;
+  const int64_t* entpp;  // per entry: partial offset << 1 | side
 };
 
 enum { LMODE_TWO = 0, LMODE_PAIR = 1, LMODE_BOX = 2 };
@@ -1334,15 +1335,25 @@ __global__ void k_combine2(ArgsV2 P, const typename A::val* __restrict__ yl,
       const LevelV2& L = P.lev[l];
       const uint32_t B = leaf >> (2 * (P.kappa - l));
       const int64_t loc = i - bstart(P.leaf_off, P.kappa, l, B);
-      for (int32_t e = L.ent_off[B]; e < L.ent_off[B + 1]; ++e) {
-        const int32_t code = L.ent[e];
-        const int side = code & 1;
-        if (mode == LMODE_BOX && side == 0) continue;  // own sums are in the slab
-        acc = A::add(acc, pc[L.ppoff[2 * (code >> 1) + side] + loc]);
+      const int32_t e1 = L.ent_off[B + 1];
+#pragma unroll 4
+      for (int32_t e = L.ent_off[B]; e < e1; ++e) {
+        const int64_t w = L.entpp[e];
+        if (mode == LMODE_BOX && (w & 1) == 0) continue;  // own sums are in the slab
+        acc = A::add(acc, pc[(w >> 1) + loc]);
       }
     }
     y[g + (int64_t)c * P.n] = A::to_double(acc);
   }
+}
+
+// entry e of a box list (pair * 2 + side) -> that side's partial offset << 1 | side
+__global__ void k_entpp(const int32_t* __restrict__ ent, int64_t nent,
+                        const int64_t* __restrict__ ppoff, int64_t* __restrict__ entpp) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nent) return;
+  const int32_t code = ent[e];
+  entpp[e] = (ppoff[code] << 1) | (code & 1);
 }
 
 __global__ void k_leaf_of(const int32_t* __restrict__ leaf_off, int64_t nleaf,
@@ -1395,7 +1406,7 @@ static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
     const Level& L = h->lev[l];
     const void* fac = mode == HODLR2D_MODE_F64 ? (const void*)L.d_fac : L.d_fac_mode[mode];
     P.lev[l] = LevelV2{L.d_px, L.d_py, L.d_rank, L.d_foff, L.d_prow, L.d_ppoff,
-                       L.d_toff, L.d_ent_off, L.d_ent, fac, L.d_meta};
+                       L.d_toff, L.d_ent_off, L.d_ent, fac, L.d_meta, L.d_entpp};
   }
   const int l2end = two_pass_end(h, nrhs, mode);
   for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) {
@@ -1577,6 +1588,11 @@ int plan_v2(hodlr2d* h) {
     pp[2 * np] = pp[2 * np + 1] = pbase;
     H2D_CK(cudaMalloc(&L.d_ppoff, sizeof(int64_t) * (2 * np + 2)));
     H2D_CK(cudaMemcpy(L.d_ppoff, pp.data(), sizeof(int64_t) * (2 * np + 2), cudaMemcpyHostToDevice));
+    H2D_CK(cudaMalloc(&L.d_entpp, sizeof(int64_t) * std::max<int64_t>(L.nent, 1)));
+    if (L.nent > 0) {
+      k_entpp<<<(unsigned)((L.nent + 255) / 256), 256>>>(L.d_ent, L.nent, L.d_ppoff, L.d_entpp);
+      H2D_CK(cudaGetLastError());
+    }
     if (V.lmode[l] == LMODE_TWO) {
       // dual level: pair plan only
     } else if (V.lmode[l] == LMODE_PAIR) {
