@@ -764,11 +764,13 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
       if (fits(PM)) {
         const F* Ug = fac + PM.foff;
         const int64_t tot = (ldpad(m) + ldpad(PM.n)) * (int64_t)PM.k;
+        // pairs start at even values and hold an even count: copies of two
+        // values (16, 8 or 4 bytes) stay aligned
         if constexpr (sizeof(F) == 8) {
-          // pairs start at even values and hold an even count: 16-byte units
           for (int64_t e = lane; 2 * e < tot; e += 32) cp_async16(st + 2 * e, Ug + 2 * e);
         } else {
-          for (int64_t e = lane; e < tot; e += 32) st[e] = Ug[e];
+          for (int64_t e = lane; 2 * e < tot; e += 32)
+            cp_async_small<2 * sizeof(F)>(st + 2 * e, Ug + 2 * e);
         }
       }
       for (int j = lane; j < PM.n; j += 32) cp_async_small<sizeof(V)>(xy + j, xc + PM.ys + j);
