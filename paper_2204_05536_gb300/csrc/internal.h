@@ -113,6 +113,7 @@ struct V2Plan {
   int lpair_small = 1 << 20;           // first pair level of boxes <= 256 points (profiling)
   BoxWork* d_bw = nullptr;     // box-mode work, boxes <= 64 points
   int64_t nbw = 0;
+  int nsm = 1;  // streaming multiprocessors of the device
   int2* d_nearw = nullptr;     // near-field work: (leaf, first target), <= 32 targets
   int64_t nnearw = 0;
   bool zero_partials = false;

@@ -44,10 +44,12 @@ constexpr int kSmallPair = 256;   // boxes up to this size: 64-thread pair block
 constexpr int kChunk2 = 256;      // rows of one expansion task of the two-pass levels
 constexpr int kExpMaxEnt = 64;    // largest list of a box (15 pairs, two sides, margin)
 constexpr int kChunkP = 512;      // rows of one projection task (16 per lane)
-// Two-pass levels whose boxes hold at most kDualRows points also get a pair
-// plan; products with one right-hand side (not binary64) run them as pairs
-// (each factor value read once) instead of in two passes.
+// Two-pass levels whose boxes hold at most kDualRows points (with ranks of
+// at most kDualKmax and at least two pairs per SM) also get a pair plan; products with one
+// right-hand side (not binary64) run them as pairs (each factor value read
+// once) instead of in two passes.
 constexpr int kDualRows = 512 * 9;
+constexpr int kDualKmax = 64;
 // With several right-hand sides, boxes of more than kMultiRows points run in
 // two passes (each factor value read twice for all of them); smaller ones run
 // with the multi-RHS register pair kernel.
@@ -1451,9 +1453,19 @@ int plan_v2(hodlr2d* h) {
     if (maxcount(l) <= kFuseRows) { V.lfuse = l; break; }
   for (int l = V.lfuse; l <= kappa; ++l)  // the pair kernel holds at most kPairKmax terms
     if (h->lev[l].max_rank > kPairKmax) V.lfuse = l + 1;
-  V.ldual = V.lfuse;  // two-pass levels that may also run as pairs: [ldual, lfuse)
+  // two-pass levels that may also run as pairs, [ldual, lfuse): boxes of at
+  // most kDualRows points, ranks of at most kDualKmax (a pair block steps
+  // through its columns one reduction at a time), and enough pairs (two per
+  // SM) that one block per pair fills the GPU
+  {
+    int dev = 0;
+    H2D_CK(cudaGetDevice(&dev));
+    H2D_CK(cudaDeviceGetAttribute(&V.nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  V.ldual = V.lfuse;
   while (V.ldual > 1 && maxcount(V.ldual - 1) <= kDualRows &&
-         h->lev[V.ldual - 1].max_rank <= kPairKmax)
+         h->lev[V.ldual - 1].max_rank <= kDualKmax &&
+         h->lev[V.ldual - 1].npairs >= 2 * (int64_t)V.nsm)
     --V.ldual;
   // pair levels with boxes of more than kMultiRows points also get a two-pass
   // plan, which several right-hand sides use: [lfuse, l2max)
