@@ -349,6 +349,30 @@ __device__ __forceinline__ __nv_bfloat16 fac_zero<__nv_bfloat16>() {
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
 
+// asynchronous global -> shared copies (cp.async): 16 bytes bypassing L1, or
+// 4 / 8 bytes through L1; each thread waits for its own groups
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+template <int B>
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
+  static_assert(B == 4 || B == 8, "cp.async.ca copies 4 or 8 bytes here");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "n"(B)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // v[NV] per lane -> the total over the W-lane group (W a power of two, W >=
 // NV) of column ((lane % W) >> (log2 W - log2 NV)), returned
 template <class A, int NV, int W = 32>
@@ -373,6 +397,19 @@ __device__ __forceinline__ typename A::val warp_reduce_scatter(typename A::val (
 #pragma unroll
   for (int o = (W / 2) >> LG; o > 0; o >>= 1) r = A::add(r, shfl_val(r, o));
   return r;
+}
+
+// k_pairg stages its factor loads through shared memory for float-float
+// factors in blocks of at most 128 threads (measured: these gain, the larger
+// blocks and the binary32 forms lose occupancy for nothing); bytes of dynamic
+// shared memory:
+template <class A, int T>
+__host__ __device__ constexpr bool pairg_async() {
+  return sizeof(typename A::fac) == 8 && sizeof(typename A::acc) == 8 && T <= 128;
+}
+template <class A, int T, int RM, int G>
+__host__ __device__ constexpr int pairg_smem() {
+  return pairg_async<A, T>() ? 2 * 2 * RM * G * T * (int)sizeof(typename A::fac) : 0;
 }
 
 template <class A, int T, int RM, int G>
@@ -406,9 +443,15 @@ __global__ void __launch_bounds__(T)
     yX[a] = A::zero();
     yY[a] = A::zero();
   }
-  int par = 0;
-  for (int q0 = 0; q0 < k; q0 += G) {
-    F u[RM][G], v[RM][G];
+  // staged forms: the next column group is copied to this thread's
+  // shared-memory slots (two stages) while the current one is computed
+  constexpr bool kAsync = pairg_async<A, T>();
+  extern __shared__ __align__(16) unsigned char pairg_smem[];
+  F* const stage = reinterpret_cast<F*>(pairg_smem);  // [2][u, v][RM][G][T]
+  auto slot = [&](int b, int uv, int a, int g) {
+    return stage + ((((b * 2 + uv) * RM + a) * G + g) * T + tid);
+  };
+  auto issue = [&](int q0, int b) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const bool qok = q0 + g < k;
@@ -417,8 +460,50 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
       for (int a = 0; a < RM; ++a) {
         const int i = tid + a * T;
-        u[a][g] = (qok && i < m) ? uc[i] : fac_zero<F>();
-        v[a][g] = (qok && i < n) ? vc[i] : fac_zero<F>();
+        if constexpr (kAsync) {
+          if (qok && i < m) cp_async_small<sizeof(F)>(slot(b, 0, a, g), uc + i);
+          if (qok && i < n) cp_async_small<sizeof(F)>(slot(b, 1, a, g), vc + i);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  if constexpr (kAsync) {
+    if (k > 0) issue(0, 0);
+  }
+  int par = 0, stb = 0;
+  for (int q0 = 0; q0 < k; q0 += G) {
+    F u[RM][G], v[RM][G];
+    if constexpr (kAsync) {
+      if (q0 + G < k) {
+        issue(q0 + G, stb ^ 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const bool qok = q0 + g < k;
+#pragma unroll
+        for (int a = 0; a < RM; ++a) {
+          const int i = tid + a * T;
+          u[a][g] = (qok && i < m) ? *slot(stb, 0, a, g) : fac_zero<F>();
+          v[a][g] = (qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>();
+        }
+      }
+      stb ^= 1;
+    } else {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const bool qok = q0 + g < k;
+        const F* uc = Ug + (int64_t)(q0 + g) * lm;
+        const F* vc = Vg + (int64_t)(q0 + g) * ln;
+#pragma unroll
+        for (int a = 0; a < RM; ++a) {
+          const int i = tid + a * T;
+          u[a][g] = (qok && i < m) ? uc[i] : fac_zero<F>();
+          v[a][g] = (qok && i < n) ? vc[i] : fac_zero<F>();
+        }
       }
     }
     // s[g] = partial t1_{q0+g} (V), s[G+g] = partial t2_{q0+g} (U)
@@ -701,28 +786,6 @@ constexpr int kBoxWarpSmem = 2 * kBoxStage * 8 + 2 * kBoxRows * 8 + kBoxRows * 8
                              2 * kBoxK * 8 + kBoxMaxPairs * (int)sizeof(PairMeta);
 constexpr int kBoxSmem = kBoxWarps * kBoxWarpSmem;
 static_assert(kBoxStage % 2 == 0 && kBoxWarpSmem % 16 == 0, "16-byte aligned slices");
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-template <int B>
-__device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
-  static_assert(B == 4 || B == 8, "cp.async.ca copies 4 or 8 bytes here");
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src), "n"(B)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 template <class A>
 __global__ void __launch_bounds__(32 * kBoxWarps)
@@ -1757,6 +1820,23 @@ static int launch_pair_plain(const int2* work, int64_t nw, int rows, const ArgsV
   return HODLR2D_OK;
 }
 
+// one launch of k_pairg<A, T, RM, G> with its staging slots (more than the
+// default 48 KB of dynamic shared memory is opted into once per instantiation)
+template <class A, int T, int RM, int G>
+static void launch_pairg(unsigned nb, const ArgsV2& P, const int2* work,
+                         const typename A::val* xt, typename A::val* ppart, cudaStream_t st) {
+  constexpr int smem = pairg_smem<A, T, RM, G>();
+  if constexpr (smem > 48 * 1024) {
+    static bool opted = false;
+    if (!opted) {
+      if (cudaFuncSetAttribute(k_pairg<A, T, RM, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem) == cudaSuccess)
+        opted = true;
+    }
+  }
+  k_pairg<A, T, RM, G><<<nb, T, smem, st>>>(P, work, xt, ppart);
+}
+
 template <class A>
 static int launch_pair_reg(const int2* work, int64_t nw, int rows, const ArgsV2& P,
                            const typename A::val* xt, typename A::val* ppart, cudaStream_t st) {
@@ -1769,19 +1849,19 @@ static int launch_pair_reg(const int2* work, int64_t nw, int rows, const ArgsV2&
   else if (rows <= 64)  // 8 pairs per block
     k_pairs<A, 16, 4, GS><<<(unsigned)((nw + 7) / 8), 128, 0, st>>>(P, work, nw, xt, ppart);
   else if (rows <= 128)
-    k_pairg<A, 32, 4, GS><<<nb, 32, 0, st>>>(P, work, xt, ppart);
+    launch_pairg<A, 32, 4, GS>(nb, P, work, xt, ppart, st);
   else if (rows <= 256)
-    k_pairg<A, 64, 4, GS><<<nb, 64, 0, st>>>(P, work, xt, ppart);
+    launch_pairg<A, 64, 4, GS>(nb, P, work, xt, ppart, st);
   else if (rows <= 384)
-    k_pairg<A, 128, 3, GS><<<nb, 128, 0, st>>>(P, work, xt, ppart);
+    launch_pairg<A, 128, 3, GS>(nb, P, work, xt, ppart, st);
   else if (rows <= 1280)
-    k_pairg<A, 256, 5, 2><<<nb, 256, 0, st>>>(P, work, xt, ppart);
+    launch_pairg<A, 256, 5, 2>(nb, P, work, xt, ppart, st);
   else if (rows <= 2560)
-    k_pairg<A, 512, 5, 2><<<nb, 512, 0, st>>>(P, work, xt, ppart);
+    launch_pairg<A, 512, 5, 2>(nb, P, work, xt, ppart, st);
   else if (rows <= kDualRows && b32) {
-    if constexpr (b32) k_pairg<A, 512, 9, 2><<<nb, 512, 0, st>>>(P, work, xt, ppart);
+    if constexpr (b32) launch_pairg<A, 512, 9, 2>(nb, P, work, xt, ppart, st);
   } else if (rows <= kDualRows && !b32) {
-    if constexpr (!b32) k_pairg<A, 512, 9, 1><<<nb, 512, 0, st>>>(P, work, xt, ppart);
+    if constexpr (!b32) launch_pairg<A, 512, 9, 1>(nb, P, work, xt, ppart, st);
   } else
     return launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st);
   H2D_CK(cudaGetLastError());
