@@ -407,9 +407,10 @@ template <class A, int T>
 __host__ __device__ constexpr bool pairg_async() {
   return sizeof(typename A::fac) == 8 && sizeof(typename A::acc) == 8 && T <= 128;
 }
+constexpr int kPairgStages = 2;  // column groups in flight: kPairgStages - 1 (3 measured slower)
 template <class A, int T, int RM, int G>
 __host__ __device__ constexpr int pairg_smem() {
-  return pairg_async<A, T>() ? 2 * 2 * RM * G * T * (int)sizeof(typename A::fac) : 0;
+  return pairg_async<A, T>() ? kPairgStages * 2 * RM * G * T * (int)sizeof(typename A::fac) : 0;
 }
 
 template <class A, int T, int RM, int G>
@@ -443,15 +444,16 @@ __global__ void __launch_bounds__(T)
     yX[a] = A::zero();
     yY[a] = A::zero();
   }
-  // staged forms: the next column group is copied to this thread's
-  // shared-memory slots (two stages) while the current one is computed
+  // staged forms: the next column groups are copied to this thread's
+  // shared-memory slots (kPairgStages stages) while the current one is
+  // computed; every step commits one copy group (empty past the last column)
   constexpr bool kAsync = pairg_async<A, T>();
   extern __shared__ __align__(16) unsigned char pairg_smem[];
-  F* const stage = reinterpret_cast<F*>(pairg_smem);  // [2][u, v][RM][G][T]
+  F* const stage = reinterpret_cast<F*>(pairg_smem);  // [stage][u, v][RM][G][T]
   auto slot = [&](int b, int uv, int a, int g) {
     return stage + ((((b * 2 + uv) * RM + a) * G + g) * T + tid);
   };
-  auto issue = [&](int q0, int b) {
+  auto issue = [&](int q0, int b) {  // columns q0 .. q0 + G - 1 (those < k)
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const bool qok = q0 + g < k;
@@ -469,18 +471,16 @@ __global__ void __launch_bounds__(T)
     cp_async_commit();
   };
   if constexpr (kAsync) {
-    if (k > 0) issue(0, 0);
+#pragma unroll
+    for (int sidx = 0; sidx < kPairgStages - 1; ++sidx) issue(sidx * G, sidx);
   }
   int par = 0, stb = 0;
   for (int q0 = 0; q0 < k; q0 += G) {
     F u[RM][G], v[RM][G];
     if constexpr (kAsync) {
-      if (q0 + G < k) {
-        issue(q0 + G, stb ^ 1);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
+      // group q0 + (S - 1) G into the slot freed by the previous step
+      issue(q0 + (kPairgStages - 1) * G, (stb + kPairgStages - 1) % kPairgStages);
+      cp_async_wait<kPairgStages - 1>();  // this step's group has landed
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const bool qok = q0 + g < k;
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(T)
           v[a][g] = (qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>();
         }
       }
-      stb ^= 1;
+      stb = (stb + 1) % kPairgStages;
     } else {
 #pragma unroll
       for (int g = 0; g < G; ++g) {
