@@ -1820,20 +1820,12 @@ static int launch_pair_plain(const int2* work, int64_t nw, int rows, const ArgsV
   return HODLR2D_OK;
 }
 
-// one launch of k_pairg<A, T, RM, G> with its staging slots (more than the
-// default 48 KB of dynamic shared memory is opted into once per instantiation)
+// one launch of k_pairg<A, T, RM, G> with its staging slots
 template <class A, int T, int RM, int G>
 static void launch_pairg(unsigned nb, const ArgsV2& P, const int2* work,
                          const typename A::val* xt, typename A::val* ppart, cudaStream_t st) {
   constexpr int smem = pairg_smem<A, T, RM, G>();
-  if constexpr (smem > 48 * 1024) {
-    static bool opted = false;
-    if (!opted) {
-      if (cudaFuncSetAttribute(k_pairg<A, T, RM, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               smem) == cudaSuccess)
-        opted = true;
-    }
-  }
+  static_assert(smem <= 48 * 1024, "staging slots within the default dynamic shared memory");
   k_pairg<A, T, RM, G><<<nb, T, smem, st>>>(P, work, xt, ppart);
 }
 
