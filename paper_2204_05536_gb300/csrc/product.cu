@@ -669,6 +669,17 @@ __global__ void __launch_bounds__(T)
 // points): S lanes per pair, 32 / S pairs per warp, rows t, t + S, ... (at
 // most RM) of X and Y per lane.  The column loop runs to the largest rank of
 // the warp's pairs; the sums reduce within each S-lane group.
+// k_pairs stages its factor loads like k_pairg for float-float factors (the
+// binary32 forms measured slower with the slots):
+template <class A, int S>
+__host__ __device__ constexpr bool pairs_async() {
+  return sizeof(typename A::fac) == 8 && sizeof(typename A::acc) == 8;
+}
+template <class A, int S, int RM, int G>
+__host__ __device__ constexpr int pairs_smem() {
+  return pairs_async<A, S>() ? 2 * 2 * RM * G * 128 * (int)sizeof(typename A::fac) : 0;
+}
+
 template <class A, int S, int RM, int G>
 __global__ void __launch_bounds__(128)
     k_pairs(ArgsV2 P, const int2* __restrict__ work, int64_t nwork,
@@ -708,8 +719,16 @@ __global__ void __launch_bounds__(128)
     yX[a] = A::zero();
     yY[a] = A::zero();
   }
-  for (int q0 = 0; q0 < kw; q0 += G) {
-    F u[RM][G], v[RM][G];
+  // staged forms: the next column group goes to this thread's shared-memory
+  // slots (two stages, one commit group per step) while the current one is
+  // computed
+  constexpr bool kAsync = pairs_async<A, S>();
+  extern __shared__ __align__(16) unsigned char pairs_smem_buf[];
+  F* const stage = reinterpret_cast<F*>(pairs_smem_buf);  // [2][u, v][RM][G][128]
+  auto slot = [&](int b, int uv, int a, int g) {
+    return stage + ((((b * 2 + uv) * RM + a) * G + g) * 128 + threadIdx.x);
+  };
+  auto issue = [&](int q0, int b) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const bool qok = q0 + g < k;
@@ -718,8 +737,44 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int a = 0; a < RM; ++a) {
         const int i = sl + a * S;
-        u[a][g] = (qok && i < m) ? uc[i] : fac_zero<F>();
-        v[a][g] = (qok && i < n) ? vc[i] : fac_zero<F>();
+        if constexpr (kAsync) {
+          if (qok && i < m) cp_async_small<sizeof(F)>(slot(b, 0, a, g), uc + i);
+          if (qok && i < n) cp_async_small<sizeof(F)>(slot(b, 1, a, g), vc + i);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  if constexpr (kAsync) issue(0, 0);
+  int stb = 0;
+  for (int q0 = 0; q0 < kw; q0 += G) {
+    F u[RM][G], v[RM][G];
+    if constexpr (kAsync) {
+      issue(q0 + G, stb ^ 1);
+      cp_async_wait<1>();
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const bool qok = q0 + g < k;
+#pragma unroll
+        for (int a = 0; a < RM; ++a) {
+          const int i = sl + a * S;
+          u[a][g] = (qok && i < m) ? *slot(stb, 0, a, g) : fac_zero<F>();
+          v[a][g] = (qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>();
+        }
+      }
+      stb ^= 1;
+    } else {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const bool qok = q0 + g < k;
+        const F* uc = Ug + (int64_t)(q0 + g) * lm;
+        const F* vc = Vg + (int64_t)(q0 + g) * ln;
+#pragma unroll
+        for (int a = 0; a < RM; ++a) {
+          const int i = sl + a * S;
+          u[a][g] = (qok && i < m) ? uc[i] : fac_zero<F>();
+          v[a][g] = (qok && i < n) ? vc[i] : fac_zero<F>();
+        }
       }
     }
     V s[NV];
@@ -1837,9 +1892,11 @@ static int launch_pair_reg(const int2* work, int64_t nw, int rows, const ArgsV2&
   constexpr int GS = b32 ? 4 : 2;
   const unsigned nb = (unsigned)nw;
   if (rows <= 48)  // 16 pairs per 128-thread block
-    k_pairs<A, 8, 6, GS><<<(unsigned)((nw + 15) / 16), 128, 0, st>>>(P, work, nw, xt, ppart);
+    k_pairs<A, 8, 6, GS><<<(unsigned)((nw + 15) / 16), 128, pairs_smem<A, 8, 6, GS>(), st>>>(
+        P, work, nw, xt, ppart);
   else if (rows <= 64)  // 8 pairs per block
-    k_pairs<A, 16, 4, GS><<<(unsigned)((nw + 7) / 8), 128, 0, st>>>(P, work, nw, xt, ppart);
+    k_pairs<A, 16, 4, GS><<<(unsigned)((nw + 7) / 8), 128, pairs_smem<A, 16, 4, GS>(), st>>>(
+        P, work, nw, xt, ppart);
   else if (rows <= 128)
     launch_pairg<A, 32, 4, GS>(nb, P, work, xt, ppart, st);
   else if (rows <= 256)
