@@ -1499,14 +1499,15 @@ __global__ void k_near_f64(const double* __restrict__ xs, const double* __restri
                            int kappa, KernelParams kp, const double* __restrict__ xt, int64_t n,
                            int nrhs, double* __restrict__ yout);
 
-// A box level runs as pairs outside binary64: with several right-hand sides
-// (multi-RHS register kernel), and for one in the binary32 and bfloat16
-// modes and in float-float when its boxes exceed 48 points (sub-warp register
-// kernel; below that the box kernel is faster in float-float).
+// A box level runs the box kernel in binary64 only; the other modes run it as
+// pairs (the sub-warp register kernel for one right-hand side, staged in
+// float-float, measured faster than the box kernel; the multi-RHS register
+// kernel for several).
 static bool box_as_pairs(const hodlr2d* h, int l, int nrhs, int mode) {
-  if (mode == HODLR2D_MODE_F64) return false;
-  if (nrhs > 1) return true;  // the multi-RHS register kernel
-  return mode != HODLR2D_MODE_DF32 || h->v2.plev[l].max_rows > 48;
+  (void)h;
+  (void)l;
+  (void)nrhs;
+  return mode != HODLR2D_MODE_F64;
 }
 
 // First level that is not run in two passes by a product:
