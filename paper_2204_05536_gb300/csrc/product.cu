@@ -15,11 +15,12 @@
 //     of X) and V t2 (rows of Y).  The pairs of a level are split into size
 //     classes, one launch each: k_pairs / k_pairg (one right-hand side) and
 //     k_pairm (several) keep each thread's rows of U and V in registers
-//     between the two uses, so each factor value is read once; k_pair
-//     (binary64) reads a pair twice;
-//   box (boxes of <= kBoxRows points): one warp per row box, the box's pairs
-//     staged in shared memory; own sums to the slab, partials for the column
-//     side.
+//     between the two uses, so each factor value is read once (in
+//     float-float the small forms stage the next column group through
+//     shared memory with cp.async); k_pair (binary64) reads a pair twice;
+//   box (binary64, boxes of <= kBoxRows points): one warp per row box, the
+//     box's pairs staged in shared memory; own sums to the slab, partials for
+//     the column side.
 // Near field: every leaf against itself and its edge sharers in work items of
 // at most 32 targets, entries evaluated from the points.  The combine pass
 // adds the near field, the slabs and the partials of each point in a fixed
