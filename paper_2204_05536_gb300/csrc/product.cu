@@ -132,7 +132,9 @@ __global__ void k_gather2(const double* __restrict__ x, const int64_t* __restric
 // ---------------------------------------------------------------------------
 constexpr int kNearWarps = 4;
 
+// kMinBlocks: resident blocks per SM the near kernel asks the compiler for
 struct NearDF32 {  // float-float points, entries and sums
+  static constexpr int kMinBlocks = 10;
   typedef float2 pt;
   typedef KernelFF K;
   typedef DF32A A;
@@ -142,6 +144,7 @@ struct NearDF32 {  // float-float points, entries and sums
   }
 };
 struct NearF32 {  // binary32 points, entries and sums (mixed form)
+  static constexpr int kMinBlocks = 10;
   typedef float pt;
   typedef KernelF32 K;
   typedef F32A A;
@@ -150,12 +153,23 @@ struct NearF32 {  // binary32 points, entries and sums (mixed form)
     return entry_f32(k, xi, yi, gi, xj, yj, gj);
   }
 };
+struct NearF64 {  // binary64 points, entries and sums (bound by the binary64 pipe, not occupancy)
+  static constexpr int kMinBlocks = 4;
+  typedef double pt;
+  typedef KernelParams K;
+  typedef F64A A;
+  static __device__ __forceinline__ double entry(const K& k, pt xi, pt yi, int64_t gi, pt xj,
+                                                 pt yj, int64_t gj) {
+    return h2d::entry(k, xi, yi, gi, xj, yj, gj);
+  }
+};
 
 // NRH right-hand sides per pass (each entry evaluated once per pass).  At
-// least 10 blocks (40 warps) per SM: the float-float entry chains need the
-// occupancy more than registers (measured 0.85 -> 0.68 ms at N = 2^20).
+// least NP::kMinBlocks blocks per SM: 10 (40 warps) for the float-float and
+// binary32 entry chains, which need the occupancy more than registers
+// (measured 0.85 -> 0.68 ms at N = 2^20).
 template <class NP, int NRH>
-__global__ void __launch_bounds__(32 * kNearWarps, 10)
+__global__ void __launch_bounds__(32 * kNearWarps, NP::kMinBlocks)
     k_near_warp(const typename NP::pt* __restrict__ xf, const typename NP::pt* __restrict__ yf,
                 const int32_t* __restrict__ leaf_off, int kappa, const int2* __restrict__ work,
                 int64_t nwork, typename NP::K kp, const typename NP::A::val* __restrict__ xt,
@@ -1495,10 +1509,6 @@ __global__ void k_to_ff(const double* __restrict__ a, float2* __restrict__ out, 
 // host side
 // ---------------------------------------------------------------------------
 // FP64 near field (defined with the first-generation product)
-__global__ void k_near_f64(const double* __restrict__ xs, const double* __restrict__ ys,
-                           const int64_t* __restrict__ perm, const int32_t* __restrict__ leaf_off,
-                           int kappa, KernelParams kp, const double* __restrict__ xt, int64_t n,
-                           int nrhs, double* __restrict__ yout);
 
 // A box level runs the box kernel in binary64 only; the other modes run it as
 // pairs (the sub-warp register kernel for one right-hand side, staged in
@@ -2005,12 +2015,11 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   H2D_CK(cudaStreamWaitEvent(sn, V.ev_in, 0));
   H2D_CK(cudaStreamWaitEvent(sf, V.ev_in, 0));
   {
-    const unsigned nleaf = (unsigned)(1u << (2 * h->kappa));
     PhaseScope ps(h, 1, 1, 24 * n + 2 * vb, sn);
     if (mode == HODLR2D_MODE_F64)
-      k_near_f64<<<nleaf, 64, 0, sn>>>(h->d_x, h->d_y, h->d_perm, h->d_leaf_off, h->kappa, h->kp,
-                                       reinterpret_cast<const double*>(xt), n, nrhs,
-                                       reinterpret_cast<double*>(yl));
+      launch_near<NearF64, 4>(V, h, sn, h->d_x, h->d_y, h->kp,
+                              reinterpret_cast<const double*>(xt), nrhs,
+                              reinterpret_cast<double*>(yl));
     else if (mode == HODLR2D_MODE_DF32)
       launch_near<NearDF32, 4>(V, h, sn, reinterpret_cast<const float2*>(V.d_xf),
                                reinterpret_cast<const float2*>(V.d_yf), V.kff,
