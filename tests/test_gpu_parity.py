@@ -446,3 +446,24 @@ def test_box_pairs_larger_than_a_slice(h2d, oracle, mode):
         y_o = o.matvec(x)
         y_g = g.matvec(torch.from_numpy(np.ascontiguousarray(x)).cuda(), mode=mode).cpu().numpy()
         assert rel(y_g, y_o) <= 1e-12
+
+
+def test_rank_one_blocks_exact(h2d, oracle):
+    """Four clusters of coincident points, one per quadrant: every stored
+    pair (the two diagonal pairs of level 1) couples two clusters, a block
+    with identical columns, so the GPU ACA returns rank 1 exactly (the
+    residual after one term is exactly zero) and the product equals the
+    direct one to rounding."""
+    centres = np.array([[-0.5, -0.5], [0.5, -0.5], [0.5, 0.5], [-0.5, 0.5]])
+    pts = np.repeat(centres, 50, axis=0)
+    n = len(pts)
+    g = h2d.HODLR2D(pts, h2d.kernel("mq", 0.01), 64, 1e-12, root=(-1.0, -1.0, 2.0))
+    st = g.stats()
+    assert st["kappa"] == 1
+    gp = g.pairs()
+    assert len(gp) == 2
+    assert np.all(gp[:, 5] == 1)
+    x = inputs.rhs(n, seed=3)
+    y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    yd = oracle.direct_matvec(pts, oracle.kernel("mq", 0.01), x)
+    assert rel(y, yd) <= 1e-13

@@ -122,6 +122,26 @@ def test_aca_full_rank_and_degenerate(oracle):
     np.testing.assert_allclose(U @ V.T, A[:1], rtol=2e-16 * 4, atol=0)
 
 
+@pytest.mark.parametrize("kind,a", [("imq", 0.01), ("mq", 0.01), ("inv_r", 0.0)])
+def test_aca_rank_one_block_exact(oracle, kind, a):
+    """All points of Y coincide, so every column of A(X, Y) is the same and
+    the block has rank 1.  The first row's residual is constant, so the first
+    pivot scales it to v = 1 exactly and u is a column of A exactly; every
+    later residual row is exactly zero (zero-pivot rule) until the rows run
+    out.  ACA returns rank 1 and U V^T equals A bit for bit."""
+    rng = np.random.default_rng(11)
+    X = rng.uniform(0.0, 1.0, (40, 2))
+    Y = np.repeat(np.array([[2.5, 1.5]]), 25, axis=0)
+    pts = np.concatenate([X, Y])
+    I, J = np.arange(40), np.arange(40, 65)
+    k = oracle.kernel(kind, a=a)
+    A = oracle.dense_matrix(pts, k)[np.ix_(I, J)]
+    U, V = oracle.aca(pts, k, I, J, 1e-12)
+    assert U.shape[1] == 1
+    np.testing.assert_array_equal(V[:, 0], np.ones(25))
+    np.testing.assert_array_equal(U @ V.T, A)
+
+
 def _c1_like(oracle, n=4096, seed=0, leaf=64, eps=1e-10, kind="imq"):
     pts = inputs.uniform(n, seed=seed)
     a = 1.0 / np.sqrt(n)
