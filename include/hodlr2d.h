@@ -183,11 +183,13 @@ typedef struct {
 int hodlr2d_get_stats(hodlr2d_t h, hodlr2d_stats* s);
 
 /* ----- tracing: per-phase device time of the product -----
- * Phases of one product (one kernel each): 0 gather x, 1 near field,
- * 2 far-field projection (coarse levels), 3 projection sums, 4 far-field
- * expansion (coarse levels), 5 combine and scatter y, 6 single-read far
- * field, one block per pair (mid levels), 7 single-read far field, one warp
- * per box (finest levels), 8 as 6 for smaller boxes, 9 unused.  While
+ * Phases of one product (one kernel, or one per pair size class): 0 gather
+ * x, 1 near field, 2 far-field projection (coarse levels), 3 projection
+ * sums, 4 far-field expansion (coarse levels), 5 combine and scatter y,
+ * 6 single-read far field, one block per pair (mid levels), 7 single-read
+ * far field of the finest levels (boxes of at most 64 points: one warp per
+ * box in binary64, sub-warp pairs otherwise), 8 as 6 for smaller boxes,
+ * 9 unused.  While
  * enabled, each phase is bracketed by CUDA events and the product runs on the
  * handle's stream alone (no side streams), so each time is that of its
  * kernel running by itself.  hodlr2d_profile(h, 1) resets and starts
