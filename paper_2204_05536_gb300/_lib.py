@@ -11,7 +11,7 @@ from . import build as _build
 
 MAX_LEVELS = 15
 NPHASE = 10
-PHASES = ["gather", "near", "proj", "tsum", "exp", "combine", "pair_big", "box", "pair_small",
+PHASES = ["gather", "near", "proj", "tsum", "exp", "combine", "pair_big", "finest", "pair_small",
           "unused"]
 
 OK = 0
