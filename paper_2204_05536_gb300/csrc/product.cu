@@ -124,11 +124,12 @@ __global__ void k_gather2(const double* __restrict__ x, const int64_t* __restric
 }
 
 // ---------------------------------------------------------------------------
-// near field, float-float: one warp per leaf.  With G = 32 / (targets per
-// round) lanes per target (G = 4 for <= 8 points, 2 for <= 16, else 1), lane
-// group h takes the sources s = h (mod G) of the concatenated source list
-// (the leaf itself, then its edge sharers in ascending Morton order); the G
-// partial sums meet in a fixed shuffle tree.
+// near field, every mode: one warp per work item (a leaf, at most 32 of its
+// targets; point, entry and sum types come from the policy).  With
+// G = 32 / (targets per round) lanes per target (G = 4 for <= 8 points, 2 for
+// <= 16, else 1), lane group h takes the sources s = h (mod G) of the
+// concatenated source list (the leaf itself, then its edge sharers in
+// ascending Morton order); the G partial sums meet in a fixed shuffle tree.
 // ---------------------------------------------------------------------------
 constexpr int kNearWarps = 4;
 
@@ -1508,8 +1509,6 @@ __global__ void k_to_ff(const double* __restrict__ a, float2* __restrict__ out, 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// FP64 near field (defined with the first-generation product)
-
 // A box level runs the box kernel in binary64 only; the other modes run it as
 // pairs (the sub-warp register kernel for one right-hand side, staged in
 // float-float, measured faster than the box kernel; the multi-RHS register
