@@ -200,6 +200,14 @@ int hodlr2d_get_stats(hodlr2d_t h, hodlr2d_stats* s);
 #define HODLR2D_NPHASE 10
 int hodlr2d_profile(hodlr2d_t h, int enable);
 int hodlr2d_get_profile(hodlr2d_t h, double* ms, int64_t* launches, int64_t* bytes);
+/* Per phase, the summed algorithmic floating-point operations of the
+ * recorded launches (flops: HODLR2D_NPHASE entries): 4 per stored factor
+ * value and right-hand side in the far field (each value takes part in one
+ * multiply-add of a projection and one of an expansion), and per near-field
+ * entry c_K + 2 per right-hand side, c_K the operations of the kernel's
+ * formula with each elementary function (sqrt, log, a division) counted as
+ * one: 7 for MQ, INV_R, LOG and PHI2, 8 for IMQ and PHI1. */
+int hodlr2d_get_profile_flops(hodlr2d_t h, int64_t* flops);
 
 /* Queue the handle's work on a cudaStream_t (passed as void*). */
 int hodlr2d_set_stream(hodlr2d_t h, void* stream);
@@ -281,10 +289,12 @@ void hodlr2d_batch_free(hodlr2d_batch_t b);
  * that cannot take the implicit device-wide synchronisation of cudaMalloc /
  * cudaFree, or a host framework that owns the device-memory budget and
  * forbids allocations outside its own pool.  hodlr2d_matvec_noalloc computes
- * the same F64 product (same kernels, same summation order) with its working
- * memory in one statically sized device array of
- * HODLR2D_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
- * until the process exits.  It never calls cudaMalloc, cudaFree or any
+ * the same Alg. 2 product in binary64, within rounding of hodlr2d_matvec's F64
+ * mode but not bit for bit: it runs a simpler, slower set of binary64 kernels
+ * (near field, per-chunk projections, chunk sums, expansions) whose sums run
+ * in another order.  Its working memory is one statically sized device array
+ * of HODLR2D_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library
+ * holds until the process exits.  It never calls cudaMalloc, cudaFree or any
  * allocating routine.
  *   h:    a handle with factors; its device must be the current device.
  *   x, y: DEVICE pointers only, n x nrhs column-major (host pointers: ARG).

@@ -88,6 +88,7 @@ def _load():
             "orc_coverage": (None, [C.c_void_p, _ip]),
             "orc_pair_info": (None, [C.c_void_p, i64, _ip, C.POINTER(i64), C.POINTER(i64)]),
             "orc_pair_factors": (None, [C.c_void_p, i64, _dp, _dp]),
+            "orc_export_factors": (None, [C.c_void_p, _ip, _lp, C.c_void_p]),
             "orc_aca": (C.c_int, [K, _dp, i64, _lp, i64, _lp, dbl, _dp, _dp]),
         }
         for name, (res, args) in sig.items():
@@ -290,14 +291,9 @@ class Oracle:
         reads: info (npairs x 6 int32: level, ixX, iyX, ixY, iyY, rank),
         offsets (npairs+1 int64) and values (for each pair U then V, each
         column-major, rows in ascending original point index)."""
-        info = np.zeros((self.npairs, 6), dtype=np.int32)
+        info = np.zeros((max(self.npairs, 1), 6), dtype=np.int32)
         offs = np.zeros(self.npairs + 1, dtype=np.int64)
-        chunks = []
-        for p in range(self.npairs):
-            d, U, V = self.pair(p)
-            info[p] = [d["level"], d["x"][0], d["x"][1], d["y"][0], d["y"][1], d["rank"]]
-            chunks.append(np.ascontiguousarray(U.T).reshape(-1))
-            chunks.append(np.ascontiguousarray(V.T).reshape(-1))
-            offs[p + 1] = offs[p] + U.size + V.size
-        vals = np.concatenate(chunks) if chunks else np.zeros(0)
-        return info, offs, vals
+        self._lib.orc_export_factors(self._h, info, offs, None)
+        vals = np.zeros(max(int(offs[-1]), 1))
+        self._lib.orc_export_factors(self._h, info, offs, C.c_void_p(vals.ctypes.data))
+        return info[: self.npairs], offs, vals[: int(offs[-1])]

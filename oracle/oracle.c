@@ -723,3 +723,14 @@ void orc_pair_factors(const orc_h2d* h, int64_t p, double* U, double* V) {
   memcpy(U, pp->U, (size_t)(pp->nx * pp->rank) * sizeof(double));
   memcpy(V, pp->V, (size_t)(pp->ny * pp->rank) * sizeof(double));
 }
+
+void orc_export_factors(const orc_h2d* h, int32_t* info, int64_t* offsets, double* values) {
+  offsets[0] = 0;
+  for (int64_t p = 0; p < h->npairs; ++p) {
+    const orc_pair* pp = &h->pairs[p];
+    orc_pair_info(h, p, info + 6 * p, NULL, NULL);
+    const int64_t nu = pp->nx * pp->rank, nv = pp->ny * pp->rank;
+    if (values) orc_pair_factors(h, p, values + offsets[p], values + offsets[p] + nu);
+    offsets[p + 1] = offsets[p] + nu + nv;
+  }
+}

@@ -101,6 +101,11 @@ void orc_pair_info(const orc_h2d* h, int64_t p, int32_t* info6, int64_t* nx,
                    int64_t* ny);
 /* U (nX x k) and V (nY x k), column-major, rows in ascending original index */
 void orc_pair_factors(const orc_h2d* h, int64_t p, double* U, double* V);
+/* every stored pair in one flat layout: info[6p..6p+5] as orc_pair_info,
+ * values[offsets[p] .. offsets[p+1]) = U then V of pair p as orc_pair_factors
+ * gives them; offsets has npairs + 1 entries.  values may be NULL (sizes
+ * only). */
+void orc_export_factors(const orc_h2d* h, int32_t* info, int64_t* offsets, double* values);
 
 /* Stand-alone ACA of A(I,J) (rows I, columns J given as point indices).
  * U: m x kmax, V: n x kmax column-major (caller sized with kmax=min(m,n)).

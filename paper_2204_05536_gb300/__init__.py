@@ -196,14 +196,18 @@ class HODLR2D:
         check(self._lib.hodlr2d_profile(self._h, int(bool(enable))), "hodlr2d_profile")
 
     def get_profile(self) -> dict:
-        """Per phase: summed device ms, launches and algorithmic bytes."""
+        """Per phase: summed device ms, launches, algorithmic bytes and flops."""
         ms = np.zeros(_lib.NPHASE)
         nl = np.zeros(_lib.NPHASE, dtype=np.int64)
         by = np.zeros(_lib.NPHASE, dtype=np.int64)
         check(self._lib.hodlr2d_get_profile(self._h, C.c_void_p(ms.ctypes.data),
                                             C.c_void_p(nl.ctypes.data),
                                             C.c_void_p(by.ctypes.data)), "hodlr2d_get_profile")
-        return {name: {"ms": float(ms[i]), "launches": int(nl[i]), "bytes": int(by[i])}
+        fl = np.zeros(_lib.NPHASE, dtype=np.int64)
+        check(self._lib.hodlr2d_get_profile_flops(self._h, C.c_void_p(fl.ctypes.data)),
+              "hodlr2d_get_profile_flops")
+        return {name: {"ms": float(ms[i]), "launches": int(nl[i]), "bytes": int(by[i]),
+                       "flops": int(fl[i])}
                 for i, name in enumerate(_lib.PHASES)}
 
     def perm(self) -> np.ndarray:

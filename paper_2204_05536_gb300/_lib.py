@@ -68,6 +68,7 @@ SIGNATURES = {
     "hodlr2d_set_stream": (C.c_int, [_P, _P]),
     "hodlr2d_profile": (C.c_int, [_P, C.c_int]),
     "hodlr2d_get_profile": (C.c_int, [_P, _P, _P, _P]),
+    "hodlr2d_get_profile_flops": (C.c_int, [_P, _P]),
     "hodlr2d_get_perm": (C.c_int, [_P, _P]),
     "hodlr2d_get_pairs": (C.c_int, [_P, _i64p, _P]),
     "hodlr2d_import_factors": (C.c_int, [_P, C.c_int64, _P, _P, _P]),

@@ -571,6 +571,7 @@ int hodlr2d_profile(hodlr2d_t h, int enable) {
       h->prof_ms[p] = 0.0;
       h->prof_launches[p] = 0;
       h->prof_bytes[p] = 0;
+      h->prof_flops[p] = 0;
     }
   }
   h->prof_on = enable != 0;
@@ -592,6 +593,12 @@ int hodlr2d_get_profile(hodlr2d_t h, double* ms, int64_t* launches, int64_t* byt
     if (launches) launches[p] = h->prof_launches[p];
     if (bytes) bytes[p] = h->prof_bytes[p];
   }
+  return HODLR2D_OK;
+}
+
+int hodlr2d_get_profile_flops(hodlr2d_t h, int64_t* flops) {
+  if (!h || !flops) return HODLR2D_ERR_ARG;
+  for (int p = 0; p < HODLR2D_NPHASE; ++p) flops[p] = h->prof_flops[p];
   return HODLR2D_OK;
 }
 

@@ -116,6 +116,7 @@ struct V2Plan {
   int nsm = 1;  // streaming multiprocessors of the device
   int2* d_nearw = nullptr;     // near-field work: (leaf, first target), <= 32 targets
   int64_t nnearw = 0;
+  int64_t near_entries = 0;    // dense leaf entries of one product
   bool zero_partials = false;
   int64_t pstride = 1;
   int32_t* d_leaf_of = nullptr;
@@ -195,6 +196,7 @@ struct hodlr2d {
   double prof_ms[HODLR2D_NPHASE] = {};
   int64_t prof_launches[HODLR2D_NPHASE] = {};
   int64_t prof_bytes[HODLR2D_NPHASE] = {};
+  int64_t prof_flops[HODLR2D_NPHASE] = {};
 };
 
 namespace h2d {
@@ -214,6 +216,10 @@ struct PhaseScope {
   }
   PhaseScope(hodlr2d* h_, int phase_, int nlaunch_, int64_t bytes)
       : PhaseScope(h_, phase_, nlaunch_, bytes, h_->stream) {}
+  // algorithmic floating-point operations of the phase's launches
+  void flops(int64_t f) {
+    if (h->prof_on) h->prof_flops[phase] += f;
+  }
   ~PhaseScope() {
     if (!h->prof_on || !a || !b) return;
     cudaEventRecord(b, st);

@@ -1831,9 +1831,23 @@ int plan_v2(hodlr2d* h) {
   {
     std::vector<int2> nw;
     const int64_t nl = (int64_t)1 << (2 * kappa);
-    for (int64_t b = 0; b < nl; ++b)
-      for (int32_t t = 0; t < h->h_leaf_off[b + 1] - h->h_leaf_off[b]; t += 32)
-        nw.push_back(make_int2((int)b, t));
+    const int side = 1 << kappa;
+    V.near_entries = 0;
+    for (int64_t b = 0; b < nl; ++b) {
+      const int64_t m = h->h_leaf_off[b + 1] - h->h_leaf_off[b];
+      for (int32_t t = 0; t < m; t += 32) nw.push_back(make_int2((int)b, t));
+      int cx, cy;
+      morton_decode((uint32_t)b, cx, cy);
+      int64_t cols = m;
+      const int ex[4] = {-1, 1, 0, 0}, ey[4] = {0, 0, -1, 1};
+      for (int e = 0; e < 4; ++e) {
+        const int qx = cx + ex[e], qy = cy + ey[e];
+        if (qx < 0 || qy < 0 || qx >= side || qy >= side) continue;
+        const uint32_t q = morton_encode((uint32_t)qx, (uint32_t)qy);
+        cols += h->h_leaf_off[q + 1] - h->h_leaf_off[q];
+      }
+      V.near_entries += m * cols;
+    }
     V.nnearw = (int64_t)nw.size();
     H2D_CK(cudaMalloc(&V.d_nearw, sizeof(int2) * std::max<int64_t>(V.nnearw, 1)));
     if (V.nnearw)
@@ -1986,6 +2000,17 @@ static void launch_near(const V2Plan& V, const hodlr2d* h, cudaStream_t sn,
                                                        V.d_nearw, V.nnearw, kp, xt, h->n, nrhs, yl);
 }
 
+// Operations of one kernel entry's formula, each elementary function (sqrt,
+// log, division) counted as one: the algorithmic cost c_K of a near-field
+// entry, before the multiply-add with x.
+static int64_t near_formula_ops(int kind) {
+  switch (kind) {
+    case HODLR2D_IMQ: return 8;   // dx, dy, dx^2, dy^2, +, + a^2, sqrt, 1/
+    case HODLR2D_PHI1: return 8;  // dx, dy, dx^2, dy^2, +, sqrt, log, / (either branch)
+    default: return 7;            // MQ: ..., + a^2, sqrt; INV_R, PHI2: sqrt, /; LOG: log, * 0.5
+  }
+}
+
 template <class A>
 static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   using Val = typename A::val;
@@ -2015,6 +2040,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   H2D_CK(cudaStreamWaitEvent(sf, V.ev_in, 0));
   {
     PhaseScope ps(h, 1, 1, 24 * n + 2 * vb, sn);
+    ps.flops(V.near_entries * (near_formula_ops(h->kp.kind) + 2 * (int64_t)nrhs));
     if (mode == HODLR2D_MODE_F64)
       launch_near<NearF64, 4>(V, h, sn, h->d_x, h->d_y, h->kp,
                               reinterpret_cast<const double*>(xt), nrhs,
@@ -2041,6 +2067,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   if (nproj) {
     {
       PhaseScope ps(h, 2, 1, fs * two_pass_vals + vs * npart * nrhs);
+      ps.flops(2 * two_pass_vals * nrhs);
       const int64_t thr = npart * 32;  // one warp per (task, column)
       if (std::is_same<A, BF16A>::value && nrhs > 1)  // tensor cores
         k_proj_tc<<<(unsigned)nproj, 128, 0, s>>>(P, V.d_proj,
@@ -2063,6 +2090,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   }
   if (nexp) {
     PhaseScope ps(h, 4, 1, fs * two_pass_vals + vb * (l2end - 1));
+    ps.flops(2 * two_pass_vals * nrhs);
     if (std::is_same<A, BF16A>::value && nrhs > 1)  // tensor cores
       k_exp_tc<<<(unsigned)nexp, 256, 0, s>>>(P, V.d_exp, reinterpret_cast<const float*>(V.d_t),
                                               reinterpret_cast<float*>(yl));
@@ -2078,6 +2106,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
     int nlaunch = 0;  // one launch per non-empty size class
     for (int c = 0; c < kPairClasses; ++c) nlaunch += V.plev[l].off[c + 1] > V.plev[l].off[c];
     PhaseScope ps(h, phase, nlaunch, fs * h->lev[l].nstored, sf);
+    ps.flops(4 * h->lev[l].nstored * nrhs);
     H2D_TRY(launch_pairs<A>(h, l, P, xt, ppart, sf));
   }
   int64_t box_vals = 0;  // levels left to the box kernel in this product
@@ -2085,6 +2114,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
     if (P.lmode[l] == LMODE_BOX) box_vals += h->lev[l].nstored;
   if (V.nbw && box_vals) {
     PhaseScope ps(h, 7, 1, fs * box_vals, sf);
+    ps.flops(4 * box_vals * nrhs);
     k_box<A><<<(unsigned)((V.nbw + kBoxWarps - 1) / kBoxWarps), 32 * kBoxWarps, kBoxSmem, sf>>>(
         P, V.d_bw, V.nbw, xt, yl, ppart);
   }

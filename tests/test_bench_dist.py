@@ -44,10 +44,11 @@ def test_max_over_ranks_and_barrier(tmp_path):
 
 def test_reference_arm_prints_once():
     r = torchrun(["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
-                  "--warmup", "0"])
+                  "--warmup", "0", "--points", "16384"])
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["unit"] == "ms"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["config"]["n"] == 16384 and d["dtype"] == "f64"

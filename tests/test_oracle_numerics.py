@@ -41,6 +41,30 @@ def test_kernel_closed_forms(oracle):
         assert oracle.entry(q, k, 0, 3) == pytest.approx(1.0, abs=1e-10)
 
 
+def test_phi1_interior_values_and_diagonal(oracle):
+    """phi_1 of Sec. 5.2 away from r = a, where a slip in either branch (a
+    sign, log a for log r, a swapped numerator) changes the value.  Expected
+    values are closed forms evaluated in 40-digit arithmetic (mpmath), not
+    the oracle's formula:
+      r > a:  log(0.75) / log(0.5) = 2 - log2(3)     = 0.41503749927884381855
+      r < a:  (r log r - 1)/(a log a - 1), a = 1e-3, r = 5e-4
+                                                     = 0.99691401319244962943
+      r = 0:  the limit r log r -> 0 gives -1/(a log a - 1), a = 1e-3
+                                                     = 0.99313963444737972287
+    A swapped sign, (r log r + 1)/(a log a + 1), would give 1.00313...; the
+    diagonal is also checked as the limit of the entries at r -> 0."""
+    p = np.array([[0.0, 0.0], [0.75, 0.0], [0.0, 5e-4], [1e-12, 0.0]])
+    assert oracle.entry(p, oracle.kernel("phi1", a=0.5), 0, 1) == pytest.approx(
+        0.41503749927884381855, rel=1e-15)
+    k = oracle.kernel("phi1", a=1e-3)
+    assert oracle.entry(p, k, 0, 2) == pytest.approx(0.99691401319244962943, rel=1e-15)
+    d = oracle.entry(p, k, 1, 1)
+    assert d == pytest.approx(0.99313963444737972287, rel=1e-15)
+    assert oracle.entry(p, k, 0, 3) == pytest.approx(d, rel=1e-10)  # continuity at r = 0
+    # phi_2 below a: r / a
+    assert oracle.entry(p, oracle.kernel("phi2", a=1e-3), 0, 2) == 0.5
+
+
 def test_direct_is_symmetric_matrix_product(oracle):
     pts = inputs.uniform(200, seed=2)
     k = oracle.kernel("imq", a=0.05)
