@@ -107,6 +107,10 @@ struct V2Plan {
   ExpTask* d_exp = nullptr;
   int64_t* d_red = nullptr;
   int64_t nproj = 0, nexp = 0, proj_partials = 0, nsides = 0, ntsum = 0;
+  // binary64 projection work (task, first column) per column group, and the
+  // groups of the tasks below each level
+  int2* d_pgrp = nullptr;
+  int64_t pre_pgrp[HODLR2D_MAX_LEVELS + 1] = {};
   int32_t* d_wtask = nullptr;  // task of each projection warp
   int64_t* d_sideq = nullptr;  // (pair side, column) of each chunk-sum warp
   int lmode[HODLR2D_MAX_LEVELS] = {};  // per level: base mode (two-pass, pair or box)

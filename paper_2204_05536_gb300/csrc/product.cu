@@ -259,6 +259,151 @@ __global__ void __launch_bounds__(32 * kNearWarps, NP::kMinBlocks)
 }
 
 // ---------------------------------------------------------------------------
+// near field in binary64: one warp per work item (a leaf, at most 32 of its
+// targets).  A binary64 warp instruction costs the same whatever its active
+// lanes, so the targets are spread over all lanes: with m targets the item
+// runs m G units (target i, slice g), G in [1, 8] chosen for the fewest idle
+// lanes over at most two passes, and unit (i, g) sums the sources whose
+// index in the concatenated source list (the leaf, then its edge sharers in
+// ascending Morton order) is g mod G.  Sources are staged in shared memory
+// kNearChunk at a time (coordinates and x), so the lanes of one slice read
+// the same source (a broadcast).  The G partials of a target are added in
+// slice order.  The multiquadric and inverse multiquadric form r^2 + a^2 as
+// dx dx + (dy dy + a^2) with two fused multiply-adds.
+// ---------------------------------------------------------------------------
+constexpr int kNear64Warps = 4;
+constexpr int kNearChunk = 128;
+
+__device__ __forceinline__ double near64_entry(const KernelParams& k, double dx, double dy) {
+  if (k.kind == HODLR2D_MQ) return sqrt(fma(dx, dx, fma(dy, dy, k.a2)));
+  if (k.kind == HODLR2D_IMQ) return 1.0 / sqrt(fma(dx, dx, fma(dy, dy, k.a2)));
+  return phi_r2(k, dx * dx + dy * dy);
+}
+
+template <int NRH>
+__global__ void __launch_bounds__(32 * kNear64Warps)
+    k_near64(const double* __restrict__ xf, const double* __restrict__ yf,
+             const int32_t* __restrict__ leaf_off, int kappa, const int2* __restrict__ work,
+             int64_t nwork, KernelParams kp, const double* __restrict__ xt, int64_t n, int nrhs,
+             double* __restrict__ yout) {
+  __shared__ double s_x[kNear64Warps][kNearChunk], s_y[kNear64Warps][kNearChunk];
+  __shared__ double s_v[kNear64Warps][NRH][kNearChunk];
+  __shared__ double s_p[kNear64Warps][NRH][64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t wi = (int64_t)blockIdx.x * kNear64Warps + w;
+  if (wi >= nwork) return;
+  const int2 wk = work[wi];
+  const uint32_t b = (uint32_t)wk.x;
+  const int32_t s0 = leaf_off[b] + wk.y;
+  const int m = min(leaf_off[b + 1] - s0, 32);
+  if (m <= 0) return;
+  int cx, cy;
+  morton_decode(b, cx, cy);
+  const int side = 1 << kappa;
+  int32_t sb[5], se[5];
+  sb[0] = leaf_off[b];
+  se[0] = leaf_off[b + 1];
+  int ns = 1;
+  uint32_t nb[4];
+  int nn = 0;
+  const int dxs[4] = {-1, 1, 0, 0}, dys[4] = {0, 0, -1, 1};
+  for (int e = 0; e < 4; ++e) {
+    const int qx = cx + dxs[e], qy = cy + dys[e];
+    if (qx < 0 || qy < 0 || qx >= side || qy >= side) continue;
+    nb[nn++] = morton_encode((uint32_t)qx, (uint32_t)qy);
+  }
+  for (int i = 1; i < nn; ++i) {
+    const uint32_t v = nb[i];
+    int j = i - 1;
+    while (j >= 0 && nb[j] > v) { nb[j + 1] = nb[j]; --j; }
+    nb[j + 1] = v;
+  }
+  for (int i = 0; i < nn; ++i) {
+    sb[ns] = leaf_off[nb[i]];
+    se[ns] = leaf_off[nb[i] + 1];
+    ++ns;
+  }
+  int total = 0;
+  for (int q = 0; q < ns; ++q) total += se[q] - sb[q];
+  // slices: the fewest idle lanes over at most 64 units (two passes)
+  int G = 1, bu = m, bp = (m + 31) / 32;
+  for (int g = 2; g <= 8 && m * g <= 64; ++g) {
+    const int u = m * g, pss = (u + 31) / 32;
+    if ((int64_t)u * bp > (int64_t)bu * pss) {
+      G = g;
+      bu = u;
+      bp = pss;
+    }
+  }
+  const int units = m * G;
+  int ui[2], ug[2];
+  double xi[2], yi[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int u = lane + 32 * p;
+    ui[p] = u < units ? u % m : 0;
+    ug[p] = u < units ? u / m : 0;
+    xi[p] = xf[s0 + ui[p]];
+    yi[p] = yf[s0 + ui[p]];
+  }
+  double* sx = s_x[w];
+  double* sy = s_y[w];
+  for (int c0 = 0; c0 < nrhs; c0 += NRH) {
+    const int nc = min(NRH, nrhs - c0);
+    double acc[2][NRH];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int r = 0; r < NRH; ++r) acc[p][r] = 0.0;
+    for (int base = 0; base < total; base += kNearChunk) {
+      const int cnt = min(kNearChunk, total - base);
+      for (int sl = lane; sl < cnt; sl += 32) {  // source base + sl -> tree position
+        int gsrc = base + sl, q = 0;
+        while (gsrc >= se[q] - sb[q]) {
+          gsrc -= se[q] - sb[q];
+          ++q;
+        }
+        const int64_t pos = sb[q] + gsrc;
+        sx[sl] = xf[pos];
+        sy[sl] = yf[pos];
+#pragma unroll
+        for (int r = 0; r < NRH; ++r)
+          if (r < nc) s_v[w][r][sl] = xt[(int64_t)(c0 + r) * n + pos];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        if (lane + 32 * p >= units) continue;
+        const int g = ug[p];
+        const int diag = wk.y + ui[p] - base;  // the target's own index in this chunk
+        int sl = (g - base % G + G) % G;
+        for (; sl < cnt; sl += G) {
+          const double e =
+              sl == diag ? kp.diag : near64_entry(kp, xi[p] - sx[sl], yi[p] - sy[sl]);
+#pragma unroll
+          for (int r = 0; r < NRH; ++r)
+            if (r < nc) acc[p][r] = fma(e, s_v[w][r][sl], acc[p][r]);
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+      if (lane + 32 * p < units)
+#pragma unroll
+        for (int r = 0; r < NRH; ++r) s_p[w][r][lane + 32 * p] = acc[p][r];
+    __syncwarp();
+    if (lane < m)
+      for (int r = 0; r < nc; ++r) {
+        double y = s_p[w][r][lane];
+        for (int g = 1; g < G; ++g) y += s_p[w][r][lane + m * g];
+        yout[(int64_t)(c0 + r) * n + s0 + lane] = y;
+      }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // pair mode (mid levels): one block per stored pair (X,Y).  Phase 1: one warp
 // per column computes t1 = V^T x_Y and t2 = U^T x_X (rows over lanes, shuffle
 // sum).  Phase 2: one thread per row writes U t1 (rows of X) and V t2 (rows of
@@ -1005,6 +1150,247 @@ __global__ void __launch_bounds__(32 * kBoxWarps)
 }
 
 // ---------------------------------------------------------------------------
+// binary64 far field.  GB300 runs binary64 at 2 FMA per clock per SM, and a
+// binary64 warp instruction costs the same whatever its active lanes, so the
+// binary64 kernels are shaped to keep every lane of every binary64
+// instruction useful and to spend as few additions as possible on sums
+// across lanes:
+//   - two-pass projection (k_proj64): one warp per (task, group of <= 32
+//     columns); lanes over rows (coalesced loads), each lane accumulating all
+//     columns of the group over its 16 rows, then one halving exchange sums
+//     the group (NV - 1 additions for NV columns, against 5 per column for
+//     a butterfly per column);
+//   - small boxes (k_pair64): one warp per stored pair, the pair's factors
+//     and vectors staged in shared memory; the projection is split into
+//     units of one column and one row segment, one unit per lane, summed by
+//     its lane alone (then the few segment partials of a column by one
+//     lane); the expansion runs one lane per row.
+// ---------------------------------------------------------------------------
+// Row segments per column for `jobs` dot products of `rows` rows on one warp:
+// the S in [1, 8] with the fewest binary64 instructions (passes over the
+// units times the segment length, plus the S - 1 additions per column), at
+// most 256 units.
+__device__ __forceinline__ int f64_segments(int jobs, int rows, int& seglen) {
+  int best = 1, bl = rows, bc = 1 << 30;
+  for (int S = 1; S <= 8 && jobs * S <= 256; ++S) {
+    const int L = (rows + S - 1) / S;
+    if (S > 1 && (S - 1) * L >= rows) break;  // the last segment would be empty
+    const int cost = ((jobs * S + 31) >> 5) * L + (S - 1) * ((jobs + 31) >> 5);
+    if (cost < bc) {
+      bc = cost;
+      best = S;
+      bl = L;
+    }
+  }
+  seglen = bl;
+  return best;
+}
+
+// One column group of a two-pass projection task: NV >= c columns q0 ..
+// q0 + c - 1 of `mat` (leading dimension ld) against x over the task's rows
+// [r0, r0 + nr), 16 rows per lane (x kept in registers); the columns are
+// visited one after another, so the warp's loads stream one contiguous
+// column slice at a time; column q0 + j's total goes to out[j].
+template <int NV>
+__device__ __forceinline__ void proj64_group(const double* __restrict__ mat, int64_t ld, int c,
+                                             const double* __restrict__ xv, int r0, int nr,
+                                             int lane, double* __restrict__ out) {
+  constexpr int R = kChunkP / 32;
+  double xr[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int r = lane + 32 * u;
+    xr[u] = r < nr ? xv[r0 + r] : 0.0;
+  }
+  double acc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    acc[j] = 0.0;
+    if (j < c) {
+      const double* col = mat + j * ld + r0;
+      if (nr == kChunkP) {  // a whole chunk: no row checks
+#pragma unroll
+        for (int u = 0; u < R; ++u) acc[j] = fma(__ldg(col + lane + 32 * u), xr[u], acc[j]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          const int r = lane + 32 * u;
+          if (32 * u < nr) acc[j] = fma(r < nr ? __ldg(col + r) : 0.0, xr[u], acc[j]);
+        }
+      }
+    }
+  }
+  const double s = warp_reduce_scatter<F64A, NV>(acc, lane);
+  constexpr int per = 32 / NV;  // lanes holding each column's total
+  const int col = lane / per;
+  if (lane % per == 0 && col < c) out[col] = s;
+}
+
+// Two-pass projection in binary64: one warp per (task, group of <= 8
+// columns) of the work list pg (task index, first column); the task's k
+// partial sums per right-hand side go where k_proj2 puts them.  Eight
+// columns per warp keep the registers low enough for 24 resident warps per
+// SM (the loads need them in flight) at 9 additions per 8 columns.
+constexpr int kProj64Cols = 8;
+__global__ void __launch_bounds__(256)
+    k_proj64(ArgsV2 P, const ProjTask* __restrict__ tasks, const int2* __restrict__ pg,
+             int64_t ngroups, const double* __restrict__ xt, double* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (w >= ngroups) return;
+  const int2 g = pg[w];
+  const ProjTask T = tasks[g.x];
+  const int q0 = g.y, k = T.k;
+  const int c = min(kProj64Cols, k - q0);
+  const double* mat = reinterpret_cast<const double*>(P.lev[T.level].fac) + T.mat +
+                      (int64_t)q0 * T.ld;
+  for (int rc = 0; rc < P.nrhs; ++rc) {
+    const double* xv = xt + (int64_t)rc * P.n + T.base;
+    double* out = part + T.out * P.nrhs + (int64_t)rc * k + q0;
+    if (c <= 4)
+      proj64_group<4>(mat, T.ld, c, xv, T.r0, T.nr, lane, out);
+    else
+      proj64_group<kProj64Cols>(mat, T.ld, c, xv, T.r0, T.nr, lane, out);
+  }
+}
+
+// Chunk sums of the two-pass levels in binary64 for pair sides of at most
+// kTsumThread chunks: one thread per (pair side, column), the chunk partials
+// added in chunk order (no cross-lane sums); sides of more chunks are left
+// to k_tsum2 (lanes over chunks, then a shuffle tree).
+constexpr int kTsumThread = 32;
+__global__ void __launch_bounds__(256)
+    k_tsum64(ArgsV2 P, const ProjTask* __restrict__ tasks, const int64_t* __restrict__ red,
+             const int64_t* __restrict__ sideq, int64_t nwork, const double* __restrict__ part,
+             double* __restrict__ t) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w >= nwork) return;
+  const int64_t s = sideq[2 * w];
+  const int q = (int)sideq[2 * w + 1];
+  const int64_t first = red[2 * s], count = red[2 * s + 1];
+  if (count > kTsumThread) return;
+  const ProjTask T0 = tasks[first];
+  const LevelV2& L = P.lev[T0.level];
+  const int k = L.rank[T0.pair];
+  double* out = t + L.toff[T0.pair] * P.nrhs + (int64_t)T0.side * k * P.nrhs;
+  for (int c = 0; c < P.nrhs; ++c) {
+    double acc = part[tasks[first].out * P.nrhs + c * k + q];
+    for (int64_t j = 1; j < count; ++j) acc += part[tasks[first + j].out * P.nrhs + c * k + q];
+    out[c * k + q] = acc;
+  }
+}
+
+// Pair levels of small boxes in binary64: one warp per stored pair (X,Y).
+// x_X and x_Y are copied to the warp's shared-memory slice; then, block by
+// block of cb columns (as many as fit kP64Slice values), the columns of U
+// and V are copied there too, and their projections t1 = V^T x_Y and
+// t2 = U^T x_X run as lane-owned (column, segment) units, each lane starting
+// its segment at its own offset (mod the segment length) so that the lanes
+// spread over the banks.  Then U t1 (rows of X) and V t2 (rows of Y), one
+// lane per row with the factors read from global memory (coalesced), are
+// written as the pair's partial results.
+constexpr int kPair64Warps = 8;
+constexpr int kP64Slice = 512;  // factor values staged per warp and column block
+constexpr int kP64Rows = 128;   // largest box of a level run by this kernel
+constexpr int kP64Kmax = 64;    // largest rank of a level run by this kernel
+constexpr int kP64Warp = kP64Slice + 2 * kP64Rows + 256 + 2 * kP64Kmax;  // doubles per warp
+constexpr int kPair64Smem = kPair64Warps * kP64Warp * 8;
+__device__ __forceinline__ double f64_dot_rot(const double* __restrict__ col,
+                                              const double* __restrict__ x, int len, int rot) {
+  double a0 = 0.0, a1 = 0.0;
+  int t = rot % len;
+  int i = 0;
+  for (; i + 1 < len; i += 2) {
+    a0 = fma(col[t], x[t], a0);
+    if (++t == len) t = 0;
+    a1 = fma(col[t], x[t], a1);
+    if (++t == len) t = 0;
+  }
+  if (i < len) a0 = fma(col[t], x[t], a0);
+  return a0 + a1;
+}
+
+__global__ void __launch_bounds__(32 * kPair64Warps)
+    k_pair64(ArgsV2 P, const int2* __restrict__ work, int64_t nw, const double* __restrict__ xt,
+             double* __restrict__ ppart) {
+  extern __shared__ __align__(16) double p64_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t wi = (int64_t)blockIdx.x * kPair64Warps + warp;
+  if (wi >= nw) return;
+  double* fs = p64_smem + (size_t)warp * kP64Warp;  // column block of U, then of V
+  double* xx = fs + kP64Slice;                      // x_X
+  double* xy = xx + kP64Rows;                       // x_Y
+  double* sp = xy + kP64Rows;                       // segment partials
+  double* tw = sp + 256;                            // t1 (k), t2 (k)
+  const int2 wk = work[wi];
+  const LevelV2& Lv = P.lev[wk.x];
+  const PairMeta PM = Lv.meta[wk.y];
+  const int32_t xs = PM.xs, m = PM.m, ys = PM.ys, n = PM.n;
+  const int lm = (int)ldpad(m), ln = (int)ldpad(n);
+  const int k = PM.k;
+  const double* Ug = reinterpret_cast<const double*>(Lv.fac) + PM.foff;
+  const double* Vg = Ug + (int64_t)lm * k;
+  const int cb = max(1, min(k, kP64Slice / (lm + ln)));  // columns per block
+  int L;
+  const int S = f64_segments(2 * cb, max(m, n), L);
+  for (int c = 0; c < P.nrhs; ++c) {
+    const double* xc = xt + (int64_t)c * P.n;
+    for (int i = lane; i < m; i += 32) cp_async_small<8>(xx + i, xc + xs + i);
+    for (int i = lane; i < n; i += 32) cp_async_small<8>(xy + i, xc + ys + i);
+    for (int q0 = 0; q0 < k; q0 += cb) {
+      const int nc = min(cb, k - q0);
+      // columns q0 .. q0 + nc - 1 of U, then of V (16-byte copies: columns
+      // start on 16-byte boundaries and hold an even count)
+      const double* us = Ug + (int64_t)q0 * lm;
+      const double* vs = Vg + (int64_t)q0 * ln;
+      for (int e = lane; 2 * e < nc * lm; e += 32) cp_async16(fs + 2 * e, us + 2 * e);
+      for (int e = lane; 2 * e < nc * ln; e += 32) cp_async16(fs + nc * lm + 2 * e, vs + 2 * e);
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncwarp();
+      for (int u = lane; u < 2 * nc * S; u += 32) {
+        const int job = u / S, sg = u - job * S;
+        const bool isV = job < nc;  // V columns against x_Y give t1
+        const int q = isV ? job : job - nc;
+        const int rows = isV ? n : m;
+        const double* col = isV ? fs + nc * lm + q * ln : fs + q * lm;
+        const int r0 = sg * L, len = min(rows - r0, L);
+        sp[u] = len > 0 ? f64_dot_rot(col + r0, (isV ? xy : xx) + r0, len, u) : 0.0;
+      }
+      __syncwarp();
+      for (int j = lane; j < 2 * nc; j += 32) {
+        double a = sp[j * S];
+        for (int sg = 1; sg < S; ++sg) a += sp[j * S + sg];
+        tw[j < nc ? q0 + j : k + q0 + j - nc] = a;
+      }
+      __syncwarp();
+    }
+    double* outx = ppart + (int64_t)c * P.pstride + PM.ppx;
+    double* outy = ppart + (int64_t)c * P.pstride + PM.ppy;
+    for (int r = lane; r < m + n; r += 32) {
+      const bool own = r < m;
+      const int i = own ? r : r - m;
+      const double* M = own ? Ug + i : Vg + i;
+      const int64_t ld = own ? lm : ln;
+      const double* tv = own ? tw : tw + k;  // U pairs with t1, V with t2
+      double a = 0.0;
+      int q = 0;
+      for (; q + 4 <= k; q += 4) {
+        const double m0 = __ldg(M + q * ld), m1 = __ldg(M + (q + 1) * ld),
+                     m2 = __ldg(M + (q + 2) * ld), m3 = __ldg(M + (q + 3) * ld);
+        a = fma(m0, tv[q], a);
+        a = fma(m1, tv[q + 1], a);
+        a = fma(m2, tv[q + 2], a);
+        a = fma(m3, tv[q + 3], a);
+      }
+      for (; q < k; ++q) a = fma(__ldg(M + q * ld), tv[q], a);
+      (own ? outx : outy)[i] = a;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // two-pass far field (levels < lfuse)
 // ---------------------------------------------------------------------------
 // One warp per (task, column): lanes read rows r0 + lane + 32 u (coalesced),
@@ -1337,7 +1723,8 @@ template <class A>
 __global__ void __launch_bounds__(256)
     k_tsum2(ArgsV2 P, const ProjTask* __restrict__ tasks, const int64_t* __restrict__ red,
             const int64_t* __restrict__ sideq, int64_t nwork,
-            const typename A::val* __restrict__ part, typename A::val* __restrict__ t) {
+            const typename A::val* __restrict__ part, typename A::val* __restrict__ t,
+            int64_t min_count = 0) {
   using V = typename A::val;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -1345,6 +1732,7 @@ __global__ void __launch_bounds__(256)
   const int64_t s = sideq[2 * w];
   const int q = (int)sideq[2 * w + 1];
   const int64_t first = red[2 * s], count = red[2 * s + 1];
+  if (count < min_count) return;  // left to a thread-per-column form
   const ProjTask T0 = tasks[first];
   const LevelV2& L = P.lev[T0.level];
   const int k = L.rank[T0.pair];
@@ -1570,6 +1958,8 @@ int plan_v2(hodlr2d* h) {
   H2D_CK(cudaFuncSetAttribute(k_box<DF32A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
   H2D_CK(cudaFuncSetAttribute(k_box<F32A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
   H2D_CK(cudaFuncSetAttribute(k_box<BF16A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
+  H2D_CK(cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kPair64Smem));
   auto maxcount = [&](int l) {
     const int sh = 2 * (kappa - l);
     int64_t mx = 0;
@@ -1662,6 +2052,25 @@ int plan_v2(hodlr2d* h) {
     V.pre_exp[l] = V.nexp;
     V.pre_part[l] = out;
     pre_sides[l] = (int64_t)red.size() / 2;
+  }
+  {  // binary64 projection work: (task, first column) per group of kProj64Cols columns
+    std::vector<int2> pg;
+    for (int64_t t = 0; t < (int64_t)proj.size(); ++t) {
+      for (int q0 = 0; q0 < proj[t].k; q0 += kProj64Cols) pg.push_back(make_int2((int)t, q0));
+    }
+    // groups of the tasks below level l (the task list is level-ordered)
+    {
+      int64_t gi = 0;
+      int l = 1;
+      for (int64_t t = 0; t <= (int64_t)proj.size(); ++t) {
+        while (l <= HODLR2D_MAX_LEVELS && V.pre_proj[l] <= t) V.pre_pgrp[l++] = gi;
+        if (t < (int64_t)proj.size()) gi += (proj[t].k + kProj64Cols - 1) / kProj64Cols;
+      }
+      while (l <= HODLR2D_MAX_LEVELS) V.pre_pgrp[l++] = gi;
+    }
+    H2D_CK(cudaMalloc(&V.d_pgrp, sizeof(int2) * std::max<size_t>(pg.size(), 1)));
+    if (!pg.empty())
+      H2D_CK(cudaMemcpy(V.d_pgrp, pg.data(), sizeof(int2) * pg.size(), cudaMemcpyHostToDevice));
   }
   {
     std::vector<int32_t> wt(std::max<int64_t>(out, 1));
@@ -1968,12 +2377,22 @@ template <class A>
 static int launch_pairs(hodlr2d* h, int l, const ArgsV2& P, const typename A::val* xt,
                         typename A::val* ppart, cudaStream_t st) {
   const PairLevel& G = h->v2.plev[l];
+  if constexpr (std::is_same<A, F64A>::value) {
+    // binary64, small boxes: one warp per pair, every size class at once
+    if (G.max_rows <= kP64Rows && h->lev[l].max_rank <= kP64Kmax) {
+      if (G.nwork)
+        k_pair64<<<(unsigned)((G.nwork + kPair64Warps - 1) / kPair64Warps), 32 * kPair64Warps,
+                   kPair64Smem, st>>>(P, G.d_work, G.nwork, xt, ppart);
+      H2D_CK(cudaGetLastError());
+      return HODLR2D_OK;
+    }
+  }
   for (int c = 0; c < kPairClasses; ++c) {
     const int64_t nw = G.off[c + 1] - G.off[c];
     if (nw == 0) continue;
     const int2* work = G.d_work + G.off[c];
     const int rows = G.cls_rows[c];
-    if constexpr (std::is_same<typename A::acc, double>::value) {
+    if constexpr (std::is_same<A, F64A>::value) {  // binary64: warp per column, two reads
       H2D_TRY(launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st));
     } else if (P.nrhs == 1) {
       H2D_TRY(launch_pair_reg<A>(work, nw, rows, P, xt, ppart, st));
@@ -2041,10 +2460,17 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   {
     PhaseScope ps(h, 1, 1, 24 * n + 2 * vb, sn);
     ps.flops(V.near_entries * (near_formula_ops(h->kp.kind) + 2 * (int64_t)nrhs));
-    if (mode == HODLR2D_MODE_F64)
-      launch_near<NearF64, 4>(V, h, sn, h->d_x, h->d_y, h->kp,
-                              reinterpret_cast<const double*>(xt), nrhs,
-                              reinterpret_cast<double*>(yl));
+    if (mode == HODLR2D_MODE_F64) {
+      const unsigned gn = (unsigned)((V.nnearw + kNear64Warps - 1) / kNear64Warps);
+      if (nrhs == 1)
+        k_near64<1><<<gn, 32 * kNear64Warps, 0, sn>>>(
+            h->d_x, h->d_y, h->d_leaf_off, h->kappa, V.d_nearw, V.nnearw, h->kp,
+            reinterpret_cast<const double*>(xt), h->n, nrhs, reinterpret_cast<double*>(yl));
+      else
+        k_near64<4><<<gn, 32 * kNear64Warps, 0, sn>>>(
+            h->d_x, h->d_y, h->d_leaf_off, h->kappa, V.d_nearw, V.nnearw, h->kp,
+            reinterpret_cast<const double*>(xt), h->n, nrhs, reinterpret_cast<double*>(yl));
+    }
     else if (mode == HODLR2D_MODE_DF32)
       launch_near<NearDF32, 4>(V, h, sn, reinterpret_cast<const float2*>(V.d_xf),
                                reinterpret_cast<const float2*>(V.d_yf), V.kff,
@@ -2076,13 +2502,27 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
       else if (nrhs >= 24 && sizeof(Val) == 4)  // binary32 sums: tiled over many right-hand sides
         k_projm<A><<<(unsigned)nproj, 256, 0, s>>>(P, V.d_proj, xt,
                                                    reinterpret_cast<Val*>(V.d_part));
+      else if (std::is_same<A, F64A>::value) {  // binary64: column groups, halving exchange
+        const int64_t ng = V.pre_pgrp[l2end];
+        k_proj64<<<(unsigned)((ng * 32 + 255) / 256), 256, 0, s>>>(
+            P, V.d_proj, V.d_pgrp, ng, reinterpret_cast<const double*>(xt),
+            reinterpret_cast<double*>(V.d_part));
+      }
       else
         k_proj2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
             P, V.d_proj, V.d_wtask, npart, xt, reinterpret_cast<Val*>(V.d_part));
     }
     {
-      PhaseScope ps(h, 3, 1, vs * (npart + h->t_total) * nrhs);
+      PhaseScope ps(h, 3, std::is_same<A, F64A>::value ? 2 : 1, vs * (npart + h->t_total) * nrhs);
       const int64_t thr = ntsum * 32;
+      if (std::is_same<A, F64A>::value) {  // binary64: one thread per (side, column)
+        k_tsum64<<<(unsigned)((ntsum + 255) / 256), 256, 0, s>>>(
+            P, V.d_proj, V.d_red, V.d_sideq, ntsum, reinterpret_cast<const double*>(V.d_part),
+            reinterpret_cast<double*>(V.d_t));
+        k_tsum2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
+            P, V.d_proj, V.d_red, V.d_sideq, ntsum, reinterpret_cast<const Val*>(V.d_part),
+            reinterpret_cast<Val*>(V.d_t), kTsumThread + 1);
+      } else
       k_tsum2<A><<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(
           P, V.d_proj, V.d_red, V.d_sideq, ntsum, reinterpret_cast<const Val*>(V.d_part),
           reinterpret_cast<Val*>(V.d_t));
@@ -2103,8 +2543,11 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   for (int l = l2end; l <= h->kappa; ++l) {
     if (P.lmode[l] != LMODE_PAIR || V.plev[l].nwork == 0) continue;
     const int phase = V.lmode[l] == LMODE_BOX ? 7 : l < V.lpair_small ? 6 : 8;
-    int nlaunch = 0;  // one launch per non-empty size class
+    int nlaunch = 0;  // one launch per non-empty size class (binary64: one per level)
     for (int c = 0; c < kPairClasses; ++c) nlaunch += V.plev[l].off[c + 1] > V.plev[l].off[c];
+    if (std::is_same<A, F64A>::value && V.plev[l].max_rows <= kP64Rows &&
+        h->lev[l].max_rank <= kP64Kmax)
+      nlaunch = 1;
     PhaseScope ps(h, phase, nlaunch, fs * h->lev[l].nstored, sf);
     ps.flops(4 * h->lev[l].nstored * nrhs);
     H2D_TRY(launch_pairs<A>(h, l, P, xt, ppart, sf));
@@ -2229,6 +2672,7 @@ void free_v2(hodlr2d* h) {
   cudaFree(V.d_red);
   cudaFree(V.d_wtask);
   cudaFree(V.d_sideq);
+  cudaFree(V.d_pgrp);
   cudaFree(V.d_bw);
   cudaFree(V.d_nearw);
   cudaFree(V.d_leaf_of);

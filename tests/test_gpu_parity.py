@@ -467,3 +467,23 @@ def test_rank_one_blocks_exact(h2d, oracle):
     y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     yd = oracle.direct_matvec(pts, oracle.kernel("mq", 0.01), x)
     assert rel(y, yd) <= 1e-13
+
+
+def test_gmres_tiny_system_breakdown(h2d, oracle):
+    """A 7-point system (kappa = 0: one dense block): the Krylov space is
+    exhausted after at most 7 steps, so the Arnoldi process breaks down
+    (|v_{j+1}| = 0 up to rounding) inside the first cycle; the solution must
+    still equal the dense solve of the oracle's matrix."""
+    n = 7
+    pts = inputs.uniform(n, seed=21)
+    k = oracle.kernel("imq", 0.3)
+    A = oracle.dense_matrix(pts, k)
+    b = inputs.rhs(n, seed=22)
+    want = np.linalg.solve(A, b)
+    g = h2d.HODLR2D(pts, h2d.kernel("imq", 0.3), 64, 1e-12)
+    for mode in ("f64", "df32"):
+        if mode != "f64":
+            g.prepare(mode)
+        x, it, rr, code = g.gmres(b, tol=1e-13, restart=50, inner_mode=mode)
+        assert code == 0 and rr <= 1e-13, (mode, it, rr)
+        assert rel(x, want) <= 1e-10, mode
