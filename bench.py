@@ -283,10 +283,12 @@ def extra_gmres_nrhs(pkg, inputs, n, stream):
     lam = torch.from_numpy(inputs.rhs(n, seed=2)).cuda()
     f = g.matvec(lam, mode="f64")
     gm = {}
-    g.gmres(f, tol=1e-2, restart=50, maxit=50)  # allocates the Krylov workspace (untimed)
     for mode in ("f64", "f32", "bf16", "df32"):
         if mode != "f64":
             g.prepare(mode)
+        # one untimed solve per mode first: the Krylov workspace, the pinned
+        # residual buffer and the first launch of every kernel on the path
+        g.gmres(f, tol=1e-8, restart=50, maxit=2000, inner_mode=mode)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         xs, it, rr, code = g.gmres(f, tol=1e-8, restart=50, maxit=2000, inner_mode=mode)
@@ -501,8 +503,8 @@ def extra_panel_system(pkg, inputs, stream):
         y = torch.empty_like(b)
         for mode in ("f64", "df32", "f32"):
             res["matvec_ms_" + mode] = round(timed(g, b, y, mode, 5, 2, stream), 3)
-        g.gmres(b, tol=1e-2, restart=50, maxit=50)  # Krylov workspace (untimed)
         for mode in ("f64", "df32", "f32"):
+            g.gmres(b, tol=1e-8, restart=50, maxit=min(maxit, 60), inner_mode=mode)  # untimed
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             xs, it, rr, code = g.gmres(b, tol=1e-8, restart=50, maxit=maxit, inner_mode=mode)
@@ -567,8 +569,8 @@ def extra_paper_replay(pkg, inputs, stream):
                                              np.arange(n))).cuda()
         res = {"kappa": st["kappa"], "r_m": st["max_rank"], "cr": round(st["compression_ratio"], 4),
                "t_i_s": round(t_i, 3)}
-        g.gmres(f, tol=1e-2, restart=50, maxit=50)  # Krylov workspace (untimed)
         for mode in ("f64", "df32"):
+            g.gmres(f, tol=1e-10, restart=50, maxit=2000, inner_mode=mode)  # untimed
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             xs, it, rr, code = g.gmres(f, tol=1e-10, restart=50, maxit=2000, inner_mode=mode)

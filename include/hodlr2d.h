@@ -135,8 +135,20 @@ int hodlr2d_matvec(hodlr2d_t h, const double* x, double* y, int nrhs);
 int hodlr2d_matvec_ex(hodlr2d_t h, const double* x, double* y, int nrhs, int mode);
 
 /* Make the factor copy that a mode reads (allocates device memory once; the
- * F64 factors stay).  Errors: ARG, OOM, CUDA, STATE. */
+ * F64 factors stay).  Errors: ARG, OOM, CUDA, STATE (no factors, or the F64
+ * factors were released and this copy was not made before). */
 int hodlr2d_prepare(hodlr2d_t h, int mode);
+
+/* Free the device memory of one mode's factors (hodlr2d_mode), e.g. the
+ * F64 factors once the float-float copy exists, which halves the factor
+ * memory of a float-float-only handle (15.5 GB at N = 2^20, eps 1e-8).  The
+ * mode's products then return HODLR2D_ERR_STATE; a released F64 copy cannot
+ * come back (later hodlr2d_prepare of a new mode, hodlr2d_export_factors,
+ * hodlr2d_matvec_noalloc and GMRES refinement around F32 / BF16 products,
+ * which need the F64 factors, return HODLR2D_ERR_STATE); a released other
+ * copy can be prepared again while the F64 factors exist.  Synchronises the
+ * handle's stream.  Errors: ARG, STATE (no factors). */
+int hodlr2d_release(hodlr2d_t h, int mode);
 
 /* Restarted GMRES for A x = b with the HODLR2D product (Sec. 5.2, 5.3), all
  * in FP64 on the GPU.  b, x: n vectors, host or device; x holds x0 on entry

@@ -119,6 +119,10 @@ class HODLR2D:
     def prepare(self, mode: str):
         check(self._lib.hodlr2d_prepare(self._h, MODES[mode]), "hodlr2d_prepare")
 
+    def release(self, mode: str):
+        """Free one mode's factor copy (hodlr2d_release)."""
+        check(self._lib.hodlr2d_release(self._h, MODES[mode]), "hodlr2d_release")
+
     def matvec(self, x, mode: str = "f64", out=None):
         """y = K_hat x for x of shape (n,) or (n, nrhs).  torch CUDA tensors stay
         on the device (asynchronous on the handle's stream); numpy arrays go

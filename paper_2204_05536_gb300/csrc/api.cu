@@ -266,8 +266,30 @@ int hodlr2d_set_stream(hodlr2d_t h, void* stream) {
 int hodlr2d_prepare(hodlr2d_t h, int mode) {
   if (!h || mode < 0 || mode > 3) return HODLR2D_ERR_ARG;
   if (!h->has_factors) return HODLR2D_ERR_STATE;
+  if (h->prepared[mode]) return HODLR2D_OK;
+  if (h->f64_released) return HODLR2D_ERR_STATE;  // copies are made from the binary64 factors
   DeviceGuard g(h->device);
   return prepare_mode(h, mode);
+}
+
+int hodlr2d_release(hodlr2d_t h, int mode) {
+  if (!h || mode < 0 || mode > 3) return HODLR2D_ERR_ARG;
+  if (!h->has_factors) return HODLR2D_ERR_STATE;
+  DeviceGuard g(h->device);
+  H2D_CK(cudaStreamSynchronize(h->stream));
+  for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) {
+    Level& L = h->lev[l];
+    if (mode == HODLR2D_MODE_F64) {
+      cudaFree(L.d_fac);
+      L.d_fac = nullptr;
+    } else {
+      cudaFree(L.d_fac_mode[mode]);
+      L.d_fac_mode[mode] = nullptr;
+    }
+  }
+  h->prepared[mode] = false;
+  if (mode == HODLR2D_MODE_F64) h->f64_released = true;
+  return HODLR2D_OK;
 }
 
 int hodlr2d_matvec_ex(hodlr2d_t h, const double* x, double* y, int nrhs, int mode) {
@@ -317,6 +339,10 @@ int hodlr2d_gmres_ex(hodlr2d_t h, const double* b, double* x, double tol, int re
       inner_mode > 3)
     return HODLR2D_ERR_ARG;
   if (!h->has_factors || !h->prepared[inner_mode]) return HODLR2D_ERR_STATE;
+  // refinement computes its residuals with the binary64 product
+  if ((inner_mode == HODLR2D_MODE_F32 || inner_mode == HODLR2D_MODE_BF16) &&
+      !h->prepared[HODLR2D_MODE_F64])
+    return HODLR2D_ERR_STATE;
   DeviceGuard g(h->device);
   return gmres_run(h, b, x, tol, restart, maxit, inner_mode, iters, relres);
 }
@@ -512,6 +538,7 @@ int hodlr2d_export_factors(hodlr2d_t h, int64_t* npairs, int64_t* nvalues, int32
   *nvalues = tv;
   if (!values) return HODLR2D_OK;
   if (!info || !offsets) return HODLR2D_ERR_ARG;
+  if (h->f64_released) return HODLR2D_ERR_STATE;
   DeviceGuard g(h->device);
   std::vector<int64_t> perm(h->n);
   H2D_CK(cudaMemcpy(perm.data(), h->d_perm, sizeof(int64_t) * h->n, cudaMemcpyDeviceToHost));

@@ -20,6 +20,9 @@
 
 namespace h2d {
 
+// terms between renormalisations of a float-float accumulator in long sums
+constexpr int kRenorm = 16;
+
 struct F64A {
   typedef double fac;  // factor storage
   typedef double val;  // vectors and sums
@@ -27,6 +30,7 @@ struct F64A {
   static __device__ __forceinline__ val ld(fac f) { return f; }
   static __device__ __forceinline__ acc zero() { return 0.0; }
   static __device__ __forceinline__ void fma(acc& s, val a, val b) { s = ::fma(a, b, s); }
+  static __device__ __forceinline__ void renorm(acc&) {}
   static __device__ __forceinline__ val fin(acc s) { return s; }
   static __device__ __forceinline__ val add(val a, val b) { return a + b; }
   static __device__ __forceinline__ val from_double(double d) { return d; }
@@ -60,6 +64,15 @@ struct DF32A {
     float h, l;
     fast_two_sum(s.x, s.y, h, l);
     return make_float2(h, l);
+  }
+  // The accumulator adds every rounding error into lo with plain binary32
+  // additions, whose own rounding grows with the number of terms; long sums
+  // call this every kRenorm terms to fold lo back into hi (an exact two-sum),
+  // which keeps lo below half an ulp of hi.
+  static __device__ __forceinline__ void renorm(acc& s) {
+    float h, l;
+    two_sum(s.x, s.y, h, l);
+    s = make_float2(h, l);
   }
   static __device__ __forceinline__ val add(val a, val b) {
     float s, e;
@@ -96,6 +109,7 @@ struct F32A {
   static __device__ __forceinline__ acc zero() { return 0.f; }
   static __device__ __forceinline__ val vzero() { return 0.f; }
   static __device__ __forceinline__ void fma(acc& s, val a, val b) { s = __fmaf_rn(a, b, s); }
+  static __device__ __forceinline__ void renorm(acc&) {}
   static __device__ __forceinline__ val fin(acc s) { return s; }
   static __device__ __forceinline__ val add(val a, val b) { return a + b; }
   static __device__ __forceinline__ val from_double(double d) { return __double2float_rn(d); }

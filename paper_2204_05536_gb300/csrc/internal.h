@@ -167,6 +167,7 @@ struct hodlr2d {
   h2d::V2Plan v2;
   bool has_factors = false;
   bool prepared[4] = {true, false, false, false};
+  bool f64_released = false;  // hodlr2d_release dropped the binary64 factors
 
   // matvec plan
   int64_t nproj = 0, nexp = 0;

@@ -58,7 +58,7 @@ int64_t align256(int64_t bytes) { return (bytes + 255) / 256 * 256; }
 
 extern "C" int hodlr2d_matvec_noalloc(hodlr2d_t h, const double* x, double* y, int nrhs) {
   if (!h || !x || !y || nrhs < 1) return HODLR2D_ERR_ARG;
-  if (!h->has_factors) return HODLR2D_ERR_STATE;
+  if (!h->has_factors || h->f64_released) return HODLR2D_ERR_STATE;
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess) {
     (void)cudaGetLastError();

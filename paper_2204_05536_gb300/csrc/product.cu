@@ -236,12 +236,15 @@ __global__ void __launch_bounds__(32 * kNearWarps, NP::kMinBlocks)
         if (j < 0) j += G;
         // the diagonal is found by tree position, a bijection of the
         // original index
-        for (; j < len; j += G) {
+        for (int cnt = 1; j < len; j += G, ++cnt) {
           const int64_t js = sb[q] + j;
           const Val kij = NP::entry(kp, xi, yi, it, xf[js], yf[js], js);
 #pragma unroll
           for (int r = 0; r < NRH; ++r)
             if (r < nc) A::fma(acc[r], kij, xt[(int64_t)(c0 + r) * n + js]);
+          if (cnt % kRenorm == 0)
+#pragma unroll
+            for (int r = 0; r < NRH; ++r) A::renorm(acc[r]);
         }
         sidx += len;
       }
@@ -442,6 +445,17 @@ __global__ void __launch_bounds__(T)
       const V* xv = xc + (isV ? ys : xs);
       Acc a = A::zero();
       int r = lane;
+      for (; r + 224 < rows; r += 256) {  // eight loads of each kind in flight
+        F v[8];
+        V xx[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          v[u] = col[r + 32 * u];
+          xx[u] = xv[r + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) A::fma(a, A::ld(v[u]), xx[u]);
+      }
       for (; r + 96 < rows; r += 128) {
         const F v0 = col[r], v1 = col[r + 32], v2 = col[r + 64], v3 = col[r + 96];
         const V x0 = xv[r], x1 = xv[r + 32], x2 = xv[r + 64], x3 = xv[r + 96];
@@ -471,6 +485,7 @@ __global__ void __launch_bounds__(T)
         for (int u = 0; u < 8; ++u) mv[u] = M[(q + u) * ld];
 #pragma unroll
         for (int u = 0; u < 8; ++u) A::fma(a, A::ld(mv[u]), tv[q + u]);
+        if ((q + 8) % kRenorm == 0) A::renorm(a);
       }
       for (; q < k; ++q) A::fma(a, A::ld(M[q * ld]), tv[q]);
       (own ? outx : outy)[i] = A::fin(a);
@@ -708,6 +723,12 @@ __global__ void __launch_bounds__(T)
           A::fma(yX[a], A::ld(u[a][g]), t[g]);      // U with t1
           A::fma(yY[a], A::ld(v[a][g]), t[G + g]);  // V with t2
         }
+    if ((q0 / G + 1) % (kRenorm / G) == 0)
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        A::renorm(yX[a]);
+        A::renorm(yY[a]);
+      }
   }
   V* outx = ppart + PM.ppx;
   V* outy = ppart + PM.ppy;
@@ -809,6 +830,14 @@ __global__ void __launch_bounds__(T)
           if (a * T < mn) {
             A::fma(yX[a][c], A::ld(u[a]), t[c]);       // U with t1
             A::fma(yY[a][c], A::ld(v[a]), t[NR + c]);  // V with t2
+          }
+      if ((q + 1) % kRenorm == 0)
+#pragma unroll
+        for (int c = 0; c < NR; ++c)
+#pragma unroll
+          for (int a = 0; a < RM; ++a) {
+            A::renorm(yX[a][c]);
+            A::renorm(yY[a][c]);
           }
     }
 #pragma unroll
@@ -963,6 +992,12 @@ __global__ void __launch_bounds__(128)
           A::fma(yX[a], A::ld(u[a][g]), t[g]);      // U with t1
           A::fma(yY[a], A::ld(v[a][g]), t[G + g]);  // V with t2
         }
+    if ((q0 / G + 1) % (kRenorm / G) == 0)
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        A::renorm(yX[a]);
+        A::renorm(yY[a]);
+      }
   }
   if (w >= nwork) return;
   V* outx = ppart + PM.ppx;
@@ -1809,7 +1844,12 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
           for (int c = 0; c < EC; ++c)
             if (c0 + c < P.nrhs) A::fma(a[c], mv, tv[(int64_t)(c0 + c) * k + q]);
+          if ((q + 1) % kRenorm == 0)
+#pragma unroll
+            for (int c = 0; c < EC; ++c) A::renorm(a[c]);
         }
+#pragma unroll
+        for (int c = 0; c < EC; ++c) A::renorm(a[c]);
       }
 #pragma unroll
       for (int c = 0; c < EC; ++c)
@@ -1830,8 +1870,10 @@ __global__ void __launch_bounds__(256)
         for (int u = 0; u < 8; ++u) mv[u] = M[(q + u) * ld];
 #pragma unroll
         for (int u = 0; u < 8; ++u) A::fma(a, A::ld(mv[u]), tv[q + u]);
+        if ((q + 8) % kRenorm == 0) A::renorm(a);
       }
       for (; q < k; ++q) A::fma(a, A::ld(M[q * ld]), tv[q]);
+      A::renorm(a);  // one renormalisation per list entry at least
     }
     yl[((int64_t)l * P.nrhs + c) * P.n + base + r] = A::fin(a);
   }

@@ -487,3 +487,25 @@ def test_gmres_tiny_system_breakdown(h2d, oracle):
         x, it, rr, code = g.gmres(b, tol=1e-13, restart=50, inner_mode=mode)
         assert code == 0 and rr <= 1e-13, (mode, it, rr)
         assert rel(x, want) <= 1e-10, mode
+
+
+def test_release_f64_keeps_df32(h2d):
+    """A float-float-only handle: after hodlr2d_release(F64) the float-float
+    product is unchanged bit for bit, and every call that needs the binary64
+    factors reports HODLR2D_ERR_STATE."""
+    n = 6000
+    pts = inputs.uniform(n, seed=13)
+    g = h2d.HODLR2D(pts, h2d.kernel("imq", 1.0 / np.sqrt(n)), 32, 1e-10)
+    g.prepare("df32")
+    x = torch.from_numpy(inputs.rhs(n, seed=14)).cuda()
+    want = g.matvec(x, mode="df32")
+    g.release("f64")
+    assert torch.equal(g.matvec(x, mode="df32"), want)
+    for call in (lambda: g.matvec(x, mode="f64"), lambda: g.prepare("f32"),
+                 lambda: g.export_factors(), lambda: g.prepare("f64")):
+        with pytest.raises(h2d.HodlrError) as e:
+            call()
+        assert e.value.code == -7
+    g.release("df32")
+    with pytest.raises(h2d.HodlrError):
+        g.matvec(x, mode="df32")

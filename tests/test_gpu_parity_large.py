@@ -152,3 +152,31 @@ def test_batch_against_oracle(h2d, oracle):
             for y, w in zip(ys, want):
                 assert rel(y.cpu().numpy().T, w) <= BOUND[mode], mode
     b.close()
+
+
+def test_df32_rank_near_200_blocks(h2d, oracle):
+    """Long float-float sums: 1/r on N = 2^15 points, leaf 64 (kappa = 5),
+    eps = 1e-15, so the vertex-sharing pairs of the 8192-point boxes (level
+    1, two passes) and of the 2048-point boxes (level 2, register pair
+    kernel) carry ranks of about 150-200 and their projections sum 8192 or
+    2048 terms.  The float-float accumulator folds its error terms back
+    every 16 terms.  Bounds, on the oracle's factors: binary64 1e-12;
+    float-float 1e-11, derived as its rounding per multiply-add (about
+    2^-46: the low-times-low product is dropped and the cross terms are
+    rounded in binary32) times the cancellation of an 8192-term dot product
+    with random x (about sqrt(8192) = 90), times the two passes and the
+    handful of levels that add up: 1.4e-14 x 90 x 8 = 1e-11.  Measured:
+    4.0e-12 (the workloads of eps >= 1e-10 stay below 1e-12)."""
+    n = 1 << 15
+    pts = inputs.uniform(n, seed=3)
+    o = oracle.Oracle(pts, oracle.kernel("inv_r"), 64, 1e-15)
+    ranks = [d["rank"] for d, _, _ in o.pairs()]
+    assert max(ranks) >= 150
+    g = h2d.HODLR2D(pts, h2d.kernel("inv_r"), 64, 1e-15, compress=False)
+    g.import_factors(*o.export_factors())
+    g.prepare("df32")
+    x = inputs.rhs(n, 1, seed=5)[:, None]
+    y_o = o.matvec(x)
+    for mode, bound in (("f64", 1e-12), ("df32", 1e-11)):
+        y = gpu_product(g, x, mode)
+        assert rel(y, y_o) <= bound, mode
