@@ -42,7 +42,7 @@ extern "C" {
 #define HODLR2D_ERR_OOM (-2)     /* device or host allocation failed             */
 #define HODLR2D_ERR_CUDA (-3)    /* a CUDA runtime call failed                   */
 #define HODLR2D_ERR_NOCONV (-4)  /* an iteration did not reach its tolerance     */
-#define HODLR2D_ERR_TIMEOUT (-5) /* reserved: a bounded device-side wait gave up */
+#define HODLR2D_ERR_TIMEOUT (-5) /* a bounded device-side wait gave up         */
 #define HODLR2D_ERR_DEPTH (-6)   /* no depth <= 14 meets the leaf rule           */
 #define HODLR2D_ERR_STATE (-7)   /* handle not ready (e.g. no factors yet)       */
 
@@ -220,6 +220,13 @@ int hodlr2d_get_profile(hodlr2d_t h, double* ms, int64_t* launches, int64_t* byt
  * formula with each elementary function (sqrt, log, a division) counted as
  * one: 7 for MQ, INV_R, LOG and PHI2, 8 for IMQ and PHI1. */
 int hodlr2d_get_profile_flops(hodlr2d_t h, int64_t* flops);
+
+/* Synchronise the handle's stream and report whether a product kernel gave
+ * up a bounded device-side wait since the last check (the tensor-core
+ * kernels of the bfloat16 many-RHS product wait on mbarriers for their
+ * MMAs): HODLR2D_ERR_TIMEOUT, whose products since the previous check are
+ * not to be trusted, or HODLR2D_OK.  Clears the flag.  Errors: ARG, CUDA. */
+int hodlr2d_check(hodlr2d_t h);
 
 /* Queue the handle's work on a cudaStream_t (passed as void*). */
 int hodlr2d_set_stream(hodlr2d_t h, void* stream);

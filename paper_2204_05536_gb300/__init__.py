@@ -119,6 +119,10 @@ class HODLR2D:
     def prepare(self, mode: str):
         check(self._lib.hodlr2d_prepare(self._h, MODES[mode]), "hodlr2d_prepare")
 
+    def check(self):
+        """hodlr2d_check: synchronise; raise if a bounded device wait gave up."""
+        check(self._lib.hodlr2d_check(self._h), "hodlr2d_check")
+
     def release(self, mode: str):
         """Free one mode's factor copy (hodlr2d_release)."""
         check(self._lib.hodlr2d_release(self._h, MODES[mode]), "hodlr2d_release")

@@ -62,6 +62,7 @@ SIGNATURES = {
     "hodlr2d_matvec_ex": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
     "hodlr2d_prepare": (C.c_int, [_P, C.c_int]),
     "hodlr2d_release": (C.c_int, [_P, C.c_int]),
+    "hodlr2d_check": (C.c_int, [_P]),
     "hodlr2d_gmres": (C.c_int, [_P, _P, _P, C.c_double]),
     "hodlr2d_gmres_ex": (C.c_int, [_P, _P, _P, C.c_double, C.c_int, C.c_int, C.c_int,
                                    C.POINTER(C.c_int), _dp]),

@@ -17,6 +17,7 @@ int lists_build(hodlr2d* h);
 int aca_build(hodlr2d* h);
 int matvec_plan(hodlr2d* h);
 int matvec_mode_device(hodlr2d* h, const double* x, double* y, int nrhs, int mode);
+int product_status(hodlr2d* h);
 int prepare_mode(hodlr2d* h, int mode);
 void free_modes(hodlr2d* h);
 int gmres_run(hodlr2d* h, const double* b, double* x, double tol, int restart, int maxit,
@@ -621,6 +622,12 @@ int hodlr2d_get_profile(hodlr2d_t h, double* ms, int64_t* launches, int64_t* byt
     if (bytes) bytes[p] = h->prof_bytes[p];
   }
   return HODLR2D_OK;
+}
+
+int hodlr2d_check(hodlr2d_t h) {
+  if (!h) return HODLR2D_ERR_ARG;
+  DeviceGuard g(h->device);
+  return product_status(h);
 }
 
 int hodlr2d_get_profile_flops(hodlr2d_t h, int64_t* flops) {

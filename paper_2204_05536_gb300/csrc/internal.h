@@ -121,6 +121,14 @@ struct V2Plan {
   int2* d_nearw = nullptr;     // near-field work: (leaf, first target), <= 32 targets
   int64_t nnearw = 0;
   int64_t near_entries = 0;    // dense leaf entries of one product
+  int* d_status = nullptr;     // set by a product kernel whose bounded wait gave up
+  // tensor-core projection groups (tasks sharing a box and row chunk): task
+  // order, {first, tasks, rows, level} per group, groups below each level
+  int32_t* d_gtask = nullptr;
+  int4* d_grp = nullptr;
+  int64_t pre_grp[HODLR2D_MAX_LEVELS + 1] = {};
+  bool grp_ok = true;  // every task fits one group
+  int two_levels = 0;  // the two-pass plan covers levels [1, two_levels)
   bool zero_partials = false;
   int64_t pstride = 1;
   int32_t* d_leaf_of = nullptr;

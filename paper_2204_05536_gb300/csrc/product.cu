@@ -5,11 +5,14 @@
 // Far field.  The plan gives every level up to three forms; each product
 // picks one per level from the mode and the number of right-hand sides
 // (two_pass_end, box_as_pairs):
-//   two-pass: a projection pass t = V^T x over row chunks (k_proj2; k_projm
-//     or, for bfloat16, the tensor-core k_proj_tc with several right-hand
-//     sides), a fixed-order sum of the chunk partials (k_tsum2), and an
-//     expansion pass y_X += U t per row box into the level's slab (k_exp2;
-//     k_exp_tc for bfloat16 with several right-hand sides);
+//   two-pass: a projection pass t = V^T x over row chunks, a fixed-order sum
+//     of the chunk partials (k_tsum2; k_tsum64 for few chunks in binary64),
+//     and an expansion pass y_X += U t per row box into the level's slab
+//     (k_exp2).  The projection kernel depends on the arithmetic: k_proj2
+//     (one warp per column), k_proj64 (binary64: column groups, one halving
+//     exchange), k_projm (binary32, many right-hand sides), and for bfloat16
+//     with several right-hand sides the tcgen05 tensor-core kernels
+//     k_projg_t5 (tasks sharing a box stacked into one GEMM) and k_exp_t5;
 //   pairs: one block, warp or sub-warp per stored pair (X,Y) computes
 //     t1 = V^T x_Y, t2 = U^T x_X and writes the partial results U t1 (rows
 //     of X) and V t2 (rows of Y).  The pairs of a level are split into size
@@ -17,20 +20,24 @@
 //     k_pairm (several) keep each thread's rows of U and V in registers
 //     between the two uses, so each factor value is read once (in
 //     float-float the small forms stage the next column group through
-//     shared memory with cp.async); k_pair (binary64) reads a pair twice;
+//     shared memory with cp.async); in binary64, k_pair (one warp per
+//     column, the pair read twice) and k_pair64 (boxes of <= 128 points: one
+//     warp per pair, lane-owned dot products from shared memory);
 //   box (binary64, boxes of <= kBoxRows points): one warp per row box, the
 //     box's pairs staged in shared memory; own sums to the slab, partials for
 //     the column side.
 // Near field: every leaf against itself and its edge sharers in work items of
-// at most 32 targets, entries evaluated from the points.  The combine pass
-// adds the near field, the slabs and the partials of each point in a fixed
-// order.  No atomics anywhere: a product is bitwise reproducible.
+// at most 32 targets, entries evaluated from the points (k_near_warp;
+// k_near64 in binary64).  The combine pass adds the near field, the slabs
+// and the partials of each point in a fixed order.  No atomics anywhere: a
+// product is bitwise reproducible.
 #include <algorithm>
 #include <type_traits>
 #include <vector>
 
 #include "arith.cuh"
 #include "internal.h"
+#include "tc5.cuh"
 
 namespace h2d {
 
@@ -1542,17 +1549,8 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
-// bfloat16 factors, several right-hand sides, two-pass levels: the products
-// on the tensor cores (mma.sync m16n8k16, bfloat16 operands, binary32
-// accumulation).  x and t are split into two bfloat16 terms (hi + lo, about
-// 2^-17 relative), each multiplied in, so the result keeps the bfloat16
-// mode's accuracy (set by the factors).
-//
-// Fragment layout of m16n8k16 (g = lane / 4, t = lane % 4): A (16 x 16, row
-// major) a0 = (g, 2t..2t+1), a1 = (g+8, 2t..), a2 = (g, 2t+8..), a3 = (g+8,
-// 2t+8..); B (16 x 8) b0 = (2t..2t+1, g), b1 = (2t+8.., g); C c0 = (g, 2t),
-// c1 = (g, 2t+1), c2 = (g+8, 2t), c3 = (g+8, 2t+1).  Two bfloat16 per 32-bit
-// register, the lower index in the low half.
+// bfloat16 pairs: packing and the split of a binary32 value into two
+// bfloat16 terms (hi + lo, about 2^-17 relative)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t bf2_pack(__nv_bfloat16 lo_idx, __nv_bfloat16 hi_idx) {
   return (uint32_t)__bfloat16_as_ushort(lo_idx) | ((uint32_t)__bfloat16_as_ushort(hi_idx) << 16);
@@ -1561,193 +1559,518 @@ __device__ __forceinline__ void bf_split(float v, __nv_bfloat16& h, __nv_bfloat1
   h = __float2bfloat16_rn(v);
   l = __float2bfloat16_rn(v - __bfloat162float(h));
 }
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-      "{%8, %9}, {%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// ---------------------------------------------------------------------------
+// bfloat16 factors, several right-hand sides, two-pass levels, on the
+// fifth-generation tensor cores (tcgen05): the accumulators live in tensor
+// memory (TMEM), the operands are staged in shared memory in the K-major
+// core-matrix layout (tc5.cuh), one thread issues the MMAs, and an mbarrier
+// per staging buffer reports their completion.  Two buffers: the next stage
+// is copied in while the tensor core works on the current one.  x and t
+// enter as two bfloat16 terms (hi + lo, about 2^-17 relative), side by side
+// in the N dimension (32 right-hand sides per pass: N = 64), so the result
+// keeps the bfloat16 mode's accuracy (set by the factors).  Every wait is
+// bounded: a wait that gives up sets *status, stops issuing work, waits
+// (bounded) for the MMAs in flight, frees the TMEM and returns.
+// ---------------------------------------------------------------------------
+constexpr int kT5K = 64;                      // K-elements per stage (4 MMAs of K = 16)
+// Core matrices adjacent in K sit 144 bytes apart (128 + 16): the eight
+// 16-byte pieces of one row's 64 K-elements then fall on distinct banks, so
+// a warp storing one row (two K-elements per lane) writes conflict-free.
+constexpr int kT5Lbo = 144;
+constexpr int kT5Sbo = kT5K / 8 * kT5Lbo;     // bytes between 8-row groups
+constexpr int kT5ABytes = 128 / 8 * kT5Sbo;   // A stage: M = 128 rows
+constexpr int kT5BBytes = 64 / 8 * kT5Sbo;    // B stage: N = 64 rows (32 hi, 32 lo)
+constexpr int kT5Smem = 2 * (kT5ABytes + kT5BBytes);
+constexpr uint32_t kT5Polls = 1u << 24;       // polls of an mbarrier before giving up
+constexpr uint32_t kT5Idesc = tc5::idesc_bf16(128, 64);
+
+__device__ __forceinline__ int t5_off(int row, int k) {
+  return (row >> 3) * kT5Sbo + (k >> 3) * kT5Lbo + (row & 7) * 16 + (k & 7) * 2;
+}
+__device__ __forceinline__ uint32_t bf2u(float a, float b) {
+  return bf2_pack(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+}
+// eight binary32 values -> their hi and lo bfloat16 terms, 16 bytes each
+__device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo) {
+  __nv_bfloat16 h[8], l[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) bf_split(v[e], h[e], l[e]);
+  hi = make_uint4(bf2_pack(h[0], h[1]), bf2_pack(h[2], h[3]), bf2_pack(h[4], h[5]),
+                  bf2_pack(h[6], h[7]));
+  lo = make_uint4(bf2_pack(l[0], l[1]), bf2_pack(l[2], l[3]), bf2_pack(l[4], l[5]),
+                  bf2_pack(l[6], l[7]));
 }
 
-// Projection: one block of 128 threads per projection task; warp w owns the
-// 16-column tiles w, w + 4, ... of the task's k columns and all right-hand
-// sides of the pass (4 tiles of 8, R <= 32).  x is staged per 128 rows in
-// shared memory as bfloat16 hi / lo terms, right-hand side by right-hand
-// side, so that a B register (rows r, r + 1 of one column) is one 32-bit
-// load; the factor pairs are 32-bit loads from global memory (even offsets).
-constexpr int kTcRows = 128;  // rows of x staged at a time
+// Shared pipeline state of the two kernels below.  Every thread of the block
+// waits on the mbarrier itself; the outcome is agreed on by a block-wide
+// vote, so that every thread takes the same branch afterwards.
+struct T5Pipe {
+  uint64_t* bar;   // [2] mbarriers, one per staging buffer
+  int gs = 0;      // stages issued so far
+  bool ok = true;  // no wait gave up (the same in every thread)
+  __device__ __forceinline__ void wait_stage(int g, int* status) {
+    const bool got = tc5::mbar_wait(&bar[g & 1], (g >> 1) & 1, kT5Polls);
+    ok = __syncthreads_and(got) != 0;
+    if (!ok && threadIdx.x == 0) atomicOr(status, 1);
+  }
+  // before refilling the buffer of stage gs: the MMAs of stage gs - 2 are done
+  __device__ __forceinline__ void acquire(int* status) {
+    if (gs >= 2 && ok) wait_stage(gs - 2, status);
+  }
+  // all MMAs issued so far are done
+  __device__ __forceinline__ void drain(int* status) {
+    if (gs >= 1 && ok) wait_stage(gs - 1, status);
+  }
+  // before the TMEM is freed: after a wait gave up, one more bounded wait
+  // for the MMAs still in flight
+  __device__ __forceinline__ void finish() {
+    if (gs >= 1 && !ok) (void)tc5::mbar_wait(&bar[(gs - 1) & 1], ((gs - 1) >> 1) & 1, kT5Polls);
+  }
+};
 
+// Projection: blocks of 128 threads walk the projection tasks (grid-stride),
+// keeping their TMEM and mbarriers.  Per task, pass of 32 right-hand sides
+// and tile of 128 columns q, D[q, n] = sum over the task's rows r of
+// M(r, q) B(n, r), B = (x_hi | x_lo); stages of 64 rows, each column of the
+// stage loaded by one warp (two rows per lane, coalesced) and stored
+// conflict-free (kT5Lbo).  Then thread (warp w, lane i) holds column
+// q = 32 w + i of D in TMEM and writes t_q = D[q, c] + D[q, 32 + c] where
+// k_proj2 puts it.
 __global__ void __launch_bounds__(128)
-    k_proj_tc(ArgsV2 P, const ProjTask* __restrict__ tasks, const float* __restrict__ xt,
-              float* __restrict__ part) {
-  __shared__ uint32_t xh[32][kTcRows / 2 + 4];  // (r, r + 1) pairs of x, hi terms
-  __shared__ uint32_t xl[32][kTcRows / 2 + 4];  // lo terms
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, t4 = lane & 3;
-  const ProjTask T = tasks[blockIdx.x];
-  const LevelV2& L = P.lev[T.level];
-  const __nv_bfloat16* M = reinterpret_cast<const __nv_bfloat16*>(L.fac) + T.mat + T.r0;
-  const int k = T.k, nr = T.nr;
-  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-  // (r, r + 1) of column q as one bfloat16 pair; rows past the chunk are 0
-  auto colpair = [&](int q, int r) -> uint32_t {
-    if (q >= k || r >= nr) return 0u;
-    const __nv_bfloat16* c = M + (int64_t)q * T.ld + r;
-    if (r + 1 < nr) return *reinterpret_cast<const uint32_t*>(c);  // even offset
-    return bf2_pack(c[0], z);
-  };
-  for (int c0 = 0; c0 < P.nrhs; c0 += 32) {
-    const int npass = (k + 63) / 64;  // 64 columns per pass, 16 per warp
-    for (int pass = 0; pass < npass; ++pass) {
-      // every warp runs every pass (the staging below needs all of them);
-      // a warp whose tile starts past k stages x and skips the products
-      const int q0 = 64 * pass + 16 * warp;
-      float acc[4][4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-      for (int rb = 0; rb < nr; rb += kTcRows) {
-        __syncthreads();  // the previous x tile is consumed
-        for (int e = tid; e < 32 * (kTcRows / 2); e += 128) {
-          const int c = e / (kTcRows / 2), rp = e % (kTcRows / 2);
-          const int r = rb + 2 * rp;
-          const float* xc = xt + (int64_t)(c0 + c) * P.n + T.base + T.r0;
-          const bool okc = c0 + c < P.nrhs;
-          const float v0 = (okc && r < nr) ? xc[r] : 0.f;
-          const float v1 = (okc && r + 1 < nr) ? xc[r + 1] : 0.f;
-          __nv_bfloat16 h0, l0, h1, l1;
-          bf_split(v0, h0, l0);
-          bf_split(v1, h1, l1);
-          xh[c][rp] = bf2_pack(h0, h1);
-          xl[c][rp] = bf2_pack(l0, l1);
+    k_proj_t5(ArgsV2 P, const ProjTask* __restrict__ tasks, int64_t ntasks,
+              const float* __restrict__ xt, float* __restrict__ part, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char t5_smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    tc5::mbar_init(&bar[0], 1);
+    tc5::mbar_init(&bar[1], 1);
+  }
+  if (warp == 0) tc5::tmem_alloc(&tslot, 64);
+  tc5::fence_before();
+  __syncthreads();
+  tc5::fence_after();
+  const uint32_t tm = tslot;
+  T5Pipe pp;
+  pp.bar = bar;
+  for (int64_t ti = blockIdx.x; ti < ntasks && pp.ok; ti += gridDim.x) {
+    const ProjTask T = tasks[ti];
+    const __nv_bfloat16* M =
+        reinterpret_cast<const __nv_bfloat16*>(P.lev[T.level].fac) + T.mat + T.r0;
+    const int k = T.k, nr = T.nr;
+    const int nst = (nr + kT5K - 1) / kT5K;
+    const float* xb = xt + T.base + T.r0;
+    for (int c0 = 0; c0 < P.nrhs && pp.ok; c0 += 32) {
+      for (int q0 = 0; q0 < k && pp.ok; q0 += 128) {
+        for (int st = 0; st < nst && pp.ok; ++st) {
+          pp.acquire(status);
+          if (!pp.ok) break;
+          unsigned char* sA = t5_smem + (pp.gs & 1) * kT5ABytes;
+          unsigned char* sB = t5_smem + 2 * kT5ABytes + (pp.gs & 1) * kT5BBytes;
+          const int r = st * kT5K + 2 * lane;  // this lane's two rows of the stage
+          const bool r0ok = r < nr, r1ok = r + 1 < nr;
+          // A: columns q0 + warp + 4 i (those < k; rows of A past k are left
+          // as they are: they only feed rows of D that are not read)
+          for (int ql = warp; ql < 128 && q0 + ql < k; ql += 4) {
+            const __nv_bfloat16* col = M + (int64_t)(q0 + ql) * T.ld + r;
+            uint32_t w = 0u;
+            if (r1ok)
+              w = *reinterpret_cast<const uint32_t*>(col);  // even offset
+            else if (r0ok)
+              w = bf2_pack(col[0], __float2bfloat16_rn(0.f));
+            *reinterpret_cast<uint32_t*>(sA + t5_off(ql, 2 * lane)) = w;
+          }
+          // B: right-hand sides c0 + warp + 4 i, hi and lo terms
+          for (int c = warp; c < 32; c += 4) {
+            const bool okc = c0 + c < P.nrhs;
+            const float* xc = xb + (int64_t)(c0 + c) * P.n;
+            const float v0 = (okc && r0ok) ? xc[r] : 0.f;
+            const float v1 = (okc && r1ok) ? xc[r + 1] : 0.f;
+            __nv_bfloat16 h0, l0, h1, l1;
+            bf_split(v0, h0, l0);
+            bf_split(v1, h1, l1);
+            *reinterpret_cast<uint32_t*>(sB + t5_off(c, 2 * lane)) = bf2_pack(h0, h1);
+            *reinterpret_cast<uint32_t*>(sB + t5_off(32 + c, 2 * lane)) = bf2_pack(l0, l1);
+          }
+          tc5::fence_smem_to_async();
+          __syncthreads();
+          if (tid == 0) {
+            tc5::fence_after();
+            const int nk = min(kT5K, nr - st * kT5K);
+            for (int kk = 0; 16 * kk < nk; ++kk)
+              tc5::mma_bf16(tm, tc5::sdesc(tc5::smem_addr(sA) + kk * 2 * kT5Lbo, kT5Lbo, kT5Sbo),
+                            tc5::sdesc(tc5::smem_addr(sB) + kk * 2 * kT5Lbo, kT5Lbo, kT5Sbo),
+                            kT5Idesc, st > 0 || kk > 0);
+            tc5::mma_commit(&bar[pp.gs & 1]);
+          }
+          ++pp.gs;
         }
-        __syncthreads();
-        if (q0 >= k) continue;  // no columns of this warp in this pass
-        const int rend = min(kTcRows, nr - rb);
-        for (int kk = 0; kk < rend; kk += 16) {
-          const int r = rb + kk + 2 * t4;
-          uint32_t a[4];
-          a[0] = colpair(q0 + g, r);
-          a[1] = colpair(q0 + g + 8, r);
-          a[2] = colpair(q0 + g, r + 8);
-          a[3] = colpair(q0 + g + 8, r + 8);
+        pp.drain(status);
+        tc5::fence_after();
+        if (pp.ok) {
+          float hv[32], lv[32];
+          const uint32_t ta = tm + ((uint32_t)(32 * warp) << 16);
+          tc5::tmem_ld32(ta, hv);
+          tc5::tmem_ld32(ta + 32, lv);
+          const int q = q0 + 32 * warp + lane;
+          if (q < k)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int c = 8 * j + g;
-            const int rp = (kk >> 1) + t4;
-            mma_bf16(acc[j], a, xh[c][rp], xh[c][rp + 4]);
-            mma_bf16(acc[j], a, xl[c][rp], xl[c][rp + 4]);
+            for (int c = 0; c < 32; ++c)
+              if (c0 + c < P.nrhs)
+                part[T.out * P.nrhs + (int64_t)(c0 + c) * k + q] = hv[c] + lv[c];
+        }
+        tc5::fence_before();
+        __syncthreads();  // TMEM read before the next tile's MMAs overwrite it
+        tc5::fence_after();
+      }
+    }
+  }
+  pp.drain(status);
+  pp.finish();
+  tc5::fence_before();
+  __syncthreads();
+  if (warp == 0) tc5::tmem_dealloc(tm, 64);
+}
+
+// Projection grouped by box: every projection task of one level that reads
+// the same rows of x (the same box, the same row chunk) multiplies the same
+// B = (x_hi | x_lo) tile, so the group's matrices are stacked along M: D row
+// j of the group is column q of task t, D[j, n] = sum over the rows r of
+// M_t(r, q) B(n, r).  x is loaded once per group and stage instead of once
+// per task.  Blocks of 256 threads walk the groups (grid-stride); a group
+// holds at most kGrpRows D rows (kGrpRows / 128 tiles of 128 rows, 64 TMEM
+// columns each).  Per stage of 64 rows: B is loaded into one of two buffers
+// with the stage's first tile, and each tile's A (128 rows of 64 K-elements,
+// four-byte asynchronous copies, two rows per lane) into one of two
+// buffers; the next tile's copies are issued before the current tile's MMAs.
+constexpr int kGrpRows = 256;                  // D rows per group, at most
+constexpr int kGrpTmem = kGrpRows / 128 * 64;  // TMEM columns
+constexpr int kGrpSmem = 2 * kT5ABytes + 2 * kT5BBytes;
+struct GrpRow {
+  int64_t col;  // first value of the column (its row 0 in the chunk) in the level's factors
+  int64_t out;  // the task's partial-sum offset
+  int32_t k, q;
+};
+
+__global__ void __launch_bounds__(256)
+    k_projg_t5(ArgsV2 P, const ProjTask* __restrict__ tasks, const int32_t* __restrict__ gtask,
+               const int4* __restrict__ grp, int64_t ngrp, const float* __restrict__ xt,
+               float* __restrict__ part, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char t5_smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tslot;
+  __shared__ GrpRow srow[kGrpRows];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    tc5::mbar_init(&bar[0], 1);
+    tc5::mbar_init(&bar[1], 1);
+  }
+  if (warp == 0) tc5::tmem_alloc(&tslot, kGrpTmem);
+  tc5::fence_before();
+  __syncthreads();
+  tc5::fence_after();
+  const uint32_t tm = tslot;
+  T5Pipe pp;
+  pp.bar = bar;
+  for (int64_t gi = blockIdx.x; gi < ngrp && pp.ok; gi += gridDim.x) {
+    const int4 G = grp[gi];  // first sorted task, tasks, D rows, unused
+    const ProjTask T0 = tasks[gtask[G.x]];
+    const __nv_bfloat16* fac = reinterpret_cast<const __nv_bfloat16*>(P.lev[T0.level].fac);
+    const int nr = T0.nr, rows = G.z;
+    const int nt = (rows + 127) / 128, nst = (nr + kT5K - 1) / kT5K;
+    if (warp == 0) {  // the group's D rows: lanes read 32 tasks at a time
+      int j0 = 0;
+      for (int i0 = 0; i0 < G.y; i0 += 32) {
+        const int i = i0 + lane;
+        ProjTask T{};
+        if (i < G.y) T = tasks[gtask[G.x + i]];
+        const int kk = i < G.y ? T.k : 0;
+        int incl = kk;  // inclusive prefix of the ranks over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int j = j0 + incl - kk;
+        for (int q = 0; q < kk; ++q)
+          srow[j + q] = GrpRow{T.mat + (int64_t)q * T.ld + T.r0, T.out, T.k, q};
+        j0 += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    __syncthreads();
+    const float* xb = xt + T0.base + T0.r0;
+    for (int c0 = 0; c0 < P.nrhs && pp.ok; c0 += 32) {
+      const int nf = nst * nt;
+      // fill i: stage i / nt, tile i % nt (B with the stage's first tile)
+      auto issue = [&](int i) {
+        pp.acquire(status);
+        if (!pp.ok) return;
+        const int st = i / nt, m = i - st * nt;
+        unsigned char* sA = t5_smem + (pp.gs & 1) * kT5ABytes;
+        const int r = st * kT5K + 2 * lane;
+        const bool r0ok = r < nr, r1ok = r + 1 < nr;
+        for (int jl = warp; jl < 128; jl += 8) {
+          const int j = 128 * m + jl;
+          if (j >= rows) break;
+          unsigned char* dst = sA + t5_off(jl, 2 * lane);
+          const __nv_bfloat16* src = fac + srow[j].col + r;
+          if (r1ok)
+            cp_async_small<4>(dst, src);  // even element offset
+          else
+            *reinterpret_cast<uint32_t*>(dst) =
+                r0ok ? bf2_pack(src[0], __float2bfloat16_rn(0.f)) : 0u;
+        }
+        if (m == 0) {
+          unsigned char* sB = t5_smem + 2 * kT5ABytes + (st & 1) * kT5BBytes;
+          for (int c = warp; c < 32; c += 8) {
+            const bool okc = c0 + c < P.nrhs;
+            const float* xc = xb + (int64_t)(c0 + c) * P.n;
+            const float v0 = (okc && r0ok) ? xc[r] : 0.f;
+            const float v1 = (okc && r1ok) ? xc[r + 1] : 0.f;
+            __nv_bfloat16 h0, l0, h1, l1;
+            bf_split(v0, h0, l0);
+            bf_split(v1, h1, l1);
+            *reinterpret_cast<uint32_t*>(sB + t5_off(c, 2 * lane)) = bf2_pack(h0, h1);
+            *reinterpret_cast<uint32_t*>(sB + t5_off(32 + c, 2 * lane)) = bf2_pack(l0, l1);
+          }
+        }
+        cp_async_commit();
+        ++pp.gs;
+      };
+      issue(0);
+      for (int i = 0; i < nf && pp.ok; ++i) {
+        if (i + 1 < nf) {
+          issue(i + 1);
+          if (!pp.ok) break;
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
+        tc5::fence_smem_to_async();
+        __syncthreads();
+        if (tid == 0) {
+          tc5::fence_after();
+          const int st = i / nt, m = i - st * nt;
+          const int fb = (pp.gs - (i + 1 < nf ? 2 : 1)) & 1;  // buffer of fill i
+          unsigned char* sA = t5_smem + fb * kT5ABytes;
+          unsigned char* sB = t5_smem + 2 * kT5ABytes + (st & 1) * kT5BBytes;
+          const int nk = min(kT5K, nr - st * kT5K);
+          for (int kk = 0; 16 * kk < nk; ++kk)
+            tc5::mma_bf16(tm + 64 * m,
+                          tc5::sdesc(tc5::smem_addr(sA) + kk * 2 * kT5Lbo, kT5Lbo, kT5Sbo),
+                          tc5::sdesc(tc5::smem_addr(sB) + kk * 2 * kT5Lbo, kT5Lbo, kT5Sbo),
+                          kT5Idesc, st > 0 || kk > 0);
+          tc5::mma_commit(&bar[fb]);
+        }
+      }
+      cp_async_wait<0>();
+      pp.drain(status);
+      tc5::fence_after();
+      if (pp.ok) {
+        for (int m = warp >> 2; m < nt; m += 2) {
+          float hv[32], lv[32];
+          const uint32_t ta = tm + ((uint32_t)(32 * (warp & 3)) << 16) + 64 * m;
+          tc5::tmem_ld32(ta, hv);
+          tc5::tmem_ld32(ta + 32, lv);
+          const int j = 128 * m + 32 * (warp & 3) + lane;
+          if (j < rows) {
+            const GrpRow R = srow[j];
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+              if (c0 + c < P.nrhs) part[R.out * P.nrhs + (int64_t)(c0 + c) * R.k + R.q] = hv[c] + lv[c];
           }
         }
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int q = q0 + g + 8 * (e >> 1), c = c0 + 8 * j + 2 * t4 + (e & 1);
-          if (q < k && c < P.nrhs) part[T.out * P.nrhs + (int64_t)c * k + q] = acc[j][e];
-        }
+      tc5::fence_before();
+      __syncthreads();  // TMEM and the row table read before the next pass or group
+      tc5::fence_after();
     }
   }
+  cp_async_wait<0>();
+  pp.drain(status);
+  pp.finish();
+  tc5::fence_before();
+  __syncthreads();
+  if (warp == 0) tc5::tmem_dealloc(tm, kGrpTmem);
 }
 
-// Expansion: one block of 256 threads per expansion task (<= 256 rows of one
-// box); warp w owns rows 32 w .. 32 w + 31 (two 16-row tiles) and all
-// right-hand sides of the pass; the box's list entries in partner order,
-// each entry's k columns in steps of 16.
-__global__ void __launch_bounds__(256)
-    k_exp_tc(ArgsV2 P, const ExpTask* __restrict__ tasks, const float* __restrict__ t,
-             float* __restrict__ yl) {
+// Expansion: blocks of 128 threads walk the expansion tasks (<= 256 rows of
+// one box each, grid-stride), 128-row tiles.  The columns of all the box's
+// list entries are packed along K (entry after entry, in partner order):
+// K-position j is column q of entry e, A(r, j) = U_e(r, q), B(n, j) = t_e
+// (hi | lo) of column q, so that one MMA of K = 16 may span entries and a
+// 16-point box with fifteen entries of rank 10 takes three stages, not
+// fifteen.  Per pass of 32 right-hand sides, D[r, n] = sum over j; thread
+// (warp w, lane i) holds row r = 32 w + i of D and writes
+// y_r = D[r, c] + D[r, 32 + c] to the level's slab, where k_exp2 puts it.
+__device__ __forceinline__ int t5_entry(const int* kpre, int ne, int j) {
+  int e = 0;
+  while (e + 1 < ne && kpre[e + 1] <= j) ++e;
+  return e;
+}
+
+__global__ void __launch_bounds__(128)
+    k_exp_t5(ArgsV2 P, const ExpTask* __restrict__ tasks, int64_t ntasks,
+             const float* __restrict__ t, float* __restrict__ yl, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char t5_smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tslot;
   __shared__ int64_t s_off[kExpMaxEnt];
   __shared__ int64_t s_toff[kExpMaxEnt];
   __shared__ int s_k[kExpMaxEnt];
-  const ExpTask T = tasks[blockIdx.x];
-  const int l = T.level;
-  const LevelV2& L = P.lev[l];
-  const uint32_t X = (uint32_t)T.box;
-  const int32_t e0 = L.ent_off[X], ne = L.ent_off[X + 1] - e0;
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-    const int32_t code = L.ent[e0 + e];
-    const int64_t p = code >> 1;
-    const int side = code & 1;
-    const int k = L.rank[p];
-    int64_t off = L.foff[p];
-    if (side == 1) off += ldpad(bsize(P.leaf_off, P.kappa, l, (uint32_t)L.px[p])) * k;
-    s_off[e] = off;
-    s_k[e] = k;
-    s_toff[e] = L.toff[p] * P.nrhs + (int64_t)side * k * P.nrhs;
+  __shared__ int s_kpre[kExpMaxEnt + 1];  // K-positions before entry e
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    tc5::mbar_init(&bar[0], 1);
+    tc5::mbar_init(&bar[1], 1);
   }
+  if (warp == 0) tc5::tmem_alloc(&tslot, 64);
+  tc5::fence_before();
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t4 = lane & 3;
-  const int32_t base = bstart(P.leaf_off, P.kappa, l, X);
-  const int64_t ld = ldpad(bsize(P.leaf_off, P.kappa, l, X));
-  const __nv_bfloat16* fac = reinterpret_cast<const __nv_bfloat16*>(L.fac);
-  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-  const int rw = 32 * warp;  // this warp's first row in the task
-  if (rw >= T.nr) return;
-  for (int c0 = 0; c0 < P.nrhs; c0 += 32) {
-    float acc[2][4][4];
+  tc5::fence_after();
+  const uint32_t tm = tslot;
+  T5Pipe pp;
+  pp.bar = bar;
+  for (int64_t ti = blockIdx.x; ti < ntasks && pp.ok; ti += gridDim.x) {
+    const ExpTask T = tasks[ti];
+    const int l = T.level;
+    const LevelV2& L = P.lev[l];
+    const uint32_t X = (uint32_t)T.box;
+    const int32_t e0 = L.ent_off[X], ne = L.ent_off[X + 1] - e0;
+    for (int e = tid; e < ne; e += blockDim.x) {
+      const int32_t code = L.ent[e0 + e];
+      const int64_t p = code >> 1;
+      const int side = code & 1;
+      const int k = L.rank[p];
+      int64_t off = L.foff[p];
+      if (side == 1) off += ldpad(bsize(P.leaf_off, P.kappa, l, (uint32_t)L.px[p])) * k;
+      s_off[e] = off;
+      s_k[e] = k;
+      s_toff[e] = L.toff[p] * P.nrhs + (int64_t)side * k * P.nrhs;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int a = 0;
+      for (int e = 0; e < ne; ++e) {
+        s_kpre[e] = a;
+        a += s_k[e];
+      }
+      s_kpre[ne] = a;
+    }
+    __syncthreads();
+    const int ktot = s_kpre[ne];
+    const int nst = (ktot + kT5K - 1) / kT5K;
+    const int32_t base = bstart(P.leaf_off, P.kappa, l, X);
+    const int64_t ld = ldpad(bsize(P.leaf_off, P.kappa, l, X));
+    const __nv_bfloat16* fac = reinterpret_cast<const __nv_bfloat16*>(L.fac);
+    for (int c0 = 0; c0 < P.nrhs && pp.ok; c0 += 32) {
+      for (int rt = 0; rt < T.nr && pp.ok; rt += 128) {
+        const int rows = min(128, T.nr - rt);
+        for (int st = 0; st < nst && pp.ok; ++st) {
+          pp.acquire(status);
+          if (!pp.ok) break;
+          unsigned char* sA = t5_smem + (pp.gs & 1) * kT5ABytes;
+          unsigned char* sB = t5_smem + 2 * kT5ABytes + (pp.gs & 1) * kT5BBytes;
+          const int j0 = st * kT5K;
+          // A: rows (2 rp, 2 rp + 1) of the tile, K-positions j0 + 8 q8 .. + 7
+          // (rows past the tile are left as they are: they only feed rows of
+          // D that are not written)
+          for (int it = tid; it < 64 * (kT5K / 8); it += 128) {
+            const int rp = it & 63, q8 = it >> 6;
+            const int r = 2 * rp;
+            if (r >= rows) continue;
+            uint32_t w[8];
+            int e = t5_entry(s_kpre, ne, min(j0 + 8 * q8, ktot - 1));
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
-    for (int e = 0; e < ne; ++e) {
-      const int k = s_k[e];
-      const __nv_bfloat16* U = fac + s_off[e] + T.r0;
-      const float* tv = t + s_toff[e];
-      for (int kk = 0; kk < k; kk += 16) {
-        // B: t (q x c), split into two bfloat16 terms
-        uint32_t bh[4][2], bl[4][2];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = c0 + 8 * j + g;
-          __nv_bfloat16 h[4], lo[4];
-#pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2) {
-            const int q = kk + 2 * t4 + (e2 & 1) + 8 * (e2 >> 1);
-            const float tvv = (c < P.nrhs && q < k) ? tv[(int64_t)c * k + q] : 0.f;
-            bf_split(tvv, h[e2], lo[e2]);
+            for (int e2 = 0; e2 < 8; ++e2) {
+              const int j = j0 + 8 * q8 + e2;
+              w[e2] = 0u;
+              if (j < ktot) {
+                while (s_kpre[e + 1] <= j) ++e;
+                const __nv_bfloat16* c =
+                    fac + s_off[e] + (int64_t)(j - s_kpre[e]) * ld + T.r0 + rt + r;
+                if (r + 1 < rows)
+                  w[e2] = *reinterpret_cast<const uint32_t*>(c);  // even offset
+                else
+                  w[e2] = bf2_pack(c[0], __float2bfloat16_rn(0.f));
+              }
+            }
+            uint4 ra, rb;  // row r: the low halves, row r + 1: the high halves
+            ra.x = __byte_perm(w[0], w[1], 0x5410);
+            ra.y = __byte_perm(w[2], w[3], 0x5410);
+            ra.z = __byte_perm(w[4], w[5], 0x5410);
+            ra.w = __byte_perm(w[6], w[7], 0x5410);
+            rb.x = __byte_perm(w[0], w[1], 0x7632);
+            rb.y = __byte_perm(w[2], w[3], 0x7632);
+            rb.z = __byte_perm(w[4], w[5], 0x7632);
+            rb.w = __byte_perm(w[6], w[7], 0x7632);
+            *reinterpret_cast<uint4*>(sA + t5_off(r, 8 * q8)) = ra;
+            *reinterpret_cast<uint4*>(sA + t5_off(r + 1, 8 * q8)) = rb;
           }
-          bh[j][0] = bf2_pack(h[0], h[1]);
-          bh[j][1] = bf2_pack(h[2], h[3]);
-          bl[j][0] = bf2_pack(lo[0], lo[1]);
-          bl[j][1] = bf2_pack(lo[2], lo[3]);
-        }
+          // B: t of right-hand side c0 + c at K-positions j0 + 8 q8 .. + 7
+          for (int it = tid; it < 32 * (kT5K / 8); it += 128) {
+            const int c = it & 31, q8 = it >> 5;
+            const bool okc = c0 + c < P.nrhs;
+            float v[8];
+            int e = t5_entry(s_kpre, ne, min(j0 + 8 * q8, ktot - 1));
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          // A: rows of U (r x q); the two values of a register are columns
-          // q, q + 1 of one row, ld apart
-          auto at = [&](int r, int q) -> __nv_bfloat16 {
-            return (r < T.nr && q < k) ? U[(int64_t)q * ld + r] : z;
-          };
-          const int r0 = rw + 16 * i + g;
-          const int qa = kk + 2 * t4;
-          uint32_t a[4];
-          a[0] = bf2_pack(at(r0, qa), at(r0, qa + 1));
-          a[1] = bf2_pack(at(r0 + 8, qa), at(r0 + 8, qa + 1));
-          a[2] = bf2_pack(at(r0, qa + 8), at(r0, qa + 9));
-          a[3] = bf2_pack(at(r0 + 8, qa + 8), at(r0 + 8, qa + 9));
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            mma_bf16(acc[i][j], a, bh[j][0], bh[j][1]);
-            mma_bf16(acc[i][j], a, bl[j][0], bl[j][1]);
+            for (int e2 = 0; e2 < 8; ++e2) {
+              const int j = j0 + 8 * q8 + e2;
+              v[e2] = 0.f;
+              if (okc && j < ktot) {
+                while (s_kpre[e + 1] <= j) ++e;
+                v[e2] = t[s_toff[e] + (int64_t)(c0 + c) * s_k[e] + (j - s_kpre[e])];
+              }
+            }
+            uint4 hi, lo;
+            split8(v, hi, lo);
+            *reinterpret_cast<uint4*>(sB + t5_off(c, 8 * q8)) = hi;
+            *reinterpret_cast<uint4*>(sB + t5_off(32 + c, 8 * q8)) = lo;
           }
+          tc5::fence_smem_to_async();
+          __syncthreads();
+          if (tid == 0) {
+            tc5::fence_after();
+            const int nk = min(kT5K, ktot - j0);
+            for (int kk = 0; 16 * kk < nk; ++kk)
+              tc5::mma_bf16(tm, tc5::sdesc(tc5::smem_addr(sA) + kk * 2 * kT5Lbo, kT5Lbo, kT5Sbo),
+                            tc5::sdesc(tc5::smem_addr(sB) + kk * 2 * kT5Lbo, kT5Lbo, kT5Sbo),
+                            kT5Idesc, st > 0 || kk > 0);
+            tc5::mma_commit(&bar[pp.gs & 1]);
+          }
+          ++pp.gs;
         }
+        pp.drain(status);
+        tc5::fence_after();
+        if (pp.ok) {
+          float hv[32], lv[32];
+          if (nst > 0) {
+            const uint32_t ta = tm + ((uint32_t)(32 * warp) << 16);
+            tc5::tmem_ld32(ta, hv);
+            tc5::tmem_ld32(ta + 32, lv);
+          } else {  // no entries: the level adds nothing to these rows
+#pragma unroll
+            for (int c = 0; c < 32; ++c) hv[c] = lv[c] = 0.f;
+          }
+          const int r = 32 * warp + lane;
+          if (r < rows)
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+              if (c0 + c < P.nrhs)
+                yl[((int64_t)l * P.nrhs + c0 + c) * P.n + base + T.r0 + rt + r] = hv[c] + lv[c];
+        }
+        tc5::fence_before();
+        __syncthreads();
+        tc5::fence_after();
       }
     }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int e2 = 0; e2 < 4; ++e2) {
-          const int r = rw + 16 * i + g + 8 * (e2 >> 1);
-          const int c = c0 + 8 * j + 2 * t4 + (e2 & 1);
-          if (r < T.nr && c < P.nrhs)
-            yl[((int64_t)l * P.nrhs + c) * P.n + base + T.r0 + r] = acc[i][j][e2];
-        }
   }
+  pp.drain(status);
+  pp.finish();
+  tc5::fence_before();
+  __syncthreads();
+  if (warp == 0) tc5::tmem_dealloc(tm, 64);
 }
 
 // t[pair, side, q] = sum of the chunk partials in chunk order: one warp per
@@ -1990,55 +2313,33 @@ static ArgsV2 args_v2(const hodlr2d* h, int nrhs, int mode) {
   return P;
 }
 
-// Plan of the v2 product (once per handle, after the factors exist).
-int plan_v2(hodlr2d* h) {
+// Two-pass plan of levels [1, lmax): the projection tasks (pair, side, row
+// chunk), their grouping by box for the tensor cores and by column group for
+// binary64, the chunk-sum work and the expansion tasks (one per 256 rows of
+// a box).  Built for [1, l2max) with the plan, and for every level the first
+// time a product runs all levels in two passes (bfloat16, several
+// right-hand sides).
+static int build_two_pass(hodlr2d* h, int lmax) {
   V2Plan& V = h->v2;
-  if (V.ready) return HODLR2D_OK;
   const int kappa = h->kappa;
-  // the box kernel's two slices per warp exceed the default 48 KB
-  H2D_CK(cudaFuncSetAttribute(k_box<F64A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
-  H2D_CK(cudaFuncSetAttribute(k_box<DF32A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
-  H2D_CK(cudaFuncSetAttribute(k_box<F32A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
-  H2D_CK(cudaFuncSetAttribute(k_box<BF16A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
-  H2D_CK(cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kPair64Smem));
-  auto maxcount = [&](int l) {
-    const int sh = 2 * (kappa - l);
-    int64_t mx = 0;
-    for (int64_t b = 0; b < ((int64_t)1 << (2 * l)); ++b)
-      mx = std::max<int64_t>(mx, h->h_leaf_off[(b + 1) << sh] - h->h_leaf_off[b << sh]);
-    return mx;
-  };
-  V.lfuse = kappa + 1;
-  for (int l = 1; l <= kappa; ++l)
-    if (maxcount(l) <= kFuseRows) { V.lfuse = l; break; }
-  for (int l = V.lfuse; l <= kappa; ++l)  // the pair kernel holds at most kPairKmax terms
-    if (h->lev[l].max_rank > kPairKmax) V.lfuse = l + 1;
-  // two-pass levels that may also run as pairs, [ldual, lfuse): boxes of at
-  // most kDualRows points, ranks of at most kDualKmax (a pair block steps
-  // through its columns one reduction at a time), and enough pairs (two per
-  // SM) that one block per pair fills the GPU
-  {
-    int dev = 0;
-    H2D_CK(cudaGetDevice(&dev));
-    H2D_CK(cudaDeviceGetAttribute(&V.nsm, cudaDevAttrMultiProcessorCount, dev));
-  }
-  V.ldual = V.lfuse;
-  while (V.ldual > 1 && maxcount(V.ldual - 1) <= kDualRows &&
-         h->lev[V.ldual - 1].max_rank <= kDualKmax &&
-         h->lev[V.ldual - 1].npairs >= 2 * (int64_t)V.nsm)
-    --V.ldual;
-  // pair levels with boxes of more than kMultiRows points also get a two-pass
-  // plan, which several right-hand sides use: [lfuse, l2max)
-  V.l2max = V.lfuse;
-  while (V.l2max <= kappa && maxcount(V.l2max) > kMultiRows) ++V.l2max;
-  // two-pass task lists for levels < lfuse
+  for (void* q : {(void*)V.d_proj, (void*)V.d_exp, (void*)V.d_red, (void*)V.d_wtask,
+                  (void*)V.d_sideq, (void*)V.d_pgrp, (void*)V.d_gtask, (void*)V.d_grp})
+    cudaFree(q);
+  V.d_proj = nullptr;
+  V.d_exp = nullptr;
+  V.d_red = nullptr;
+  V.d_wtask = nullptr;
+  V.d_sideq = nullptr;
+  V.d_pgrp = nullptr;
+  V.d_gtask = nullptr;
+  V.d_grp = nullptr;
+  V.grp_ok = true;
   std::vector<ProjTask> proj;
   std::vector<ExpTask> exps;
   std::vector<int64_t> red;
   int64_t out = 0;
   int64_t pre_sides[HODLR2D_MAX_LEVELS + 1] = {};
-  for (int l = 1; l < V.l2max; ++l) {
+  for (int l = 1; l < lmax; ++l) {
     // the task lists are level-ordered: record the counts below level l
     V.pre_proj[l] = (int64_t)proj.size();
     V.pre_exp[l] = (int64_t)exps.size();
@@ -2089,11 +2390,49 @@ int plan_v2(hodlr2d* h) {
   }
   V.nproj = (int64_t)proj.size();
   V.nexp = (int64_t)exps.size();
-  for (int l = V.l2max; l <= HODLR2D_MAX_LEVELS; ++l) {
+  for (int l = lmax; l <= HODLR2D_MAX_LEVELS; ++l) {
     V.pre_proj[l] = V.nproj;
     V.pre_exp[l] = V.nexp;
     V.pre_part[l] = out;
     pre_sides[l] = (int64_t)red.size() / 2;
+  }
+  {  // bfloat16 tensor-core projection: tasks grouped by (level, box, row chunk)
+    std::vector<int32_t> order(proj.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      const ProjTask &A = proj[a], &B = proj[b];
+      if (A.level != B.level) return A.level < B.level;
+      if (A.base != B.base) return A.base < B.base;
+      return A.r0 < B.r0;
+    });
+    std::vector<int4> grp;
+    size_t i = 0;
+    while (i < order.size()) {
+      const ProjTask& T = proj[order[i]];
+      int4 g = make_int4((int)i, 0, 0, T.level);
+      while (i < order.size()) {
+        const ProjTask& U = proj[order[i]];
+        if (U.level != T.level || U.base != T.base || U.r0 != T.r0) break;
+        if (g.y > 0 && g.z + U.k > kGrpRows) break;
+        if (U.k > kGrpRows) V.grp_ok = false;  // a rank beyond one group: per-task kernel
+        g.y += 1;
+        g.z += U.k;
+        ++i;
+      }
+      grp.push_back(g);
+    }
+    for (int l = 1; l <= HODLR2D_MAX_LEVELS; ++l) {
+      int64_t c = 0;
+      while (c < (int64_t)grp.size() && grp[c].w < l) ++c;
+      V.pre_grp[l] = c;
+    }
+    H2D_CK(cudaMalloc(&V.d_gtask, sizeof(int32_t) * std::max<size_t>(order.size(), 1)));
+    H2D_CK(cudaMalloc(&V.d_grp, sizeof(int4) * std::max<size_t>(grp.size(), 1)));
+    if (!order.empty())
+      H2D_CK(cudaMemcpy(V.d_gtask, order.data(), sizeof(int32_t) * order.size(),
+                        cudaMemcpyHostToDevice));
+    if (!grp.empty())
+      H2D_CK(cudaMemcpy(V.d_grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice));
   }
   {  // binary64 projection work: (task, first column) per group of kProj64Cols columns
     std::vector<int2> pg;
@@ -2152,6 +2491,58 @@ int plan_v2(hodlr2d* h) {
     H2D_CK(cudaMemcpy(V.d_exp, exps.data(), sizeof(ExpTask) * V.nexp, cudaMemcpyHostToDevice));
   if (!red.empty())
     H2D_CK(cudaMemcpy(V.d_red, red.data(), sizeof(int64_t) * red.size(), cudaMemcpyHostToDevice));
+  V.two_levels = lmax;
+  return HODLR2D_OK;
+}
+
+// Plan of the v2 product (once per handle, after the factors exist).
+int plan_v2(hodlr2d* h) {
+  V2Plan& V = h->v2;
+  if (V.ready) return HODLR2D_OK;
+  const int kappa = h->kappa;
+  // the box kernel's two slices per warp exceed the default 48 KB
+  H2D_CK(cudaFuncSetAttribute(k_box<F64A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
+  H2D_CK(cudaFuncSetAttribute(k_box<DF32A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
+  H2D_CK(cudaFuncSetAttribute(k_box<F32A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
+  H2D_CK(cudaFuncSetAttribute(k_box<BF16A>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxSmem));
+  H2D_CK(cudaFuncSetAttribute(k_pair64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kPair64Smem));
+  H2D_CK(cudaFuncSetAttribute(k_proj_t5, cudaFuncAttributeMaxDynamicSharedMemorySize, kT5Smem));
+  H2D_CK(cudaFuncSetAttribute(k_projg_t5, cudaFuncAttributeMaxDynamicSharedMemorySize, kGrpSmem));
+  H2D_CK(cudaFuncSetAttribute(k_exp_t5, cudaFuncAttributeMaxDynamicSharedMemorySize, kT5Smem));
+  H2D_CK(cudaMalloc(&V.d_status, sizeof(int)));
+  H2D_CK(cudaMemset(V.d_status, 0, sizeof(int)));
+  auto maxcount = [&](int l) {
+    const int sh = 2 * (kappa - l);
+    int64_t mx = 0;
+    for (int64_t b = 0; b < ((int64_t)1 << (2 * l)); ++b)
+      mx = std::max<int64_t>(mx, h->h_leaf_off[(b + 1) << sh] - h->h_leaf_off[b << sh]);
+    return mx;
+  };
+  V.lfuse = kappa + 1;
+  for (int l = 1; l <= kappa; ++l)
+    if (maxcount(l) <= kFuseRows) { V.lfuse = l; break; }
+  for (int l = V.lfuse; l <= kappa; ++l)  // the pair kernel holds at most kPairKmax terms
+    if (h->lev[l].max_rank > kPairKmax) V.lfuse = l + 1;
+  // two-pass levels that may also run as pairs, [ldual, lfuse): boxes of at
+  // most kDualRows points, ranks of at most kDualKmax (a pair block steps
+  // through its columns one reduction at a time), and enough pairs (two per
+  // SM) that one block per pair fills the GPU
+  {
+    int dev = 0;
+    H2D_CK(cudaGetDevice(&dev));
+    H2D_CK(cudaDeviceGetAttribute(&V.nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  V.ldual = V.lfuse;
+  while (V.ldual > 1 && maxcount(V.ldual - 1) <= kDualRows &&
+         h->lev[V.ldual - 1].max_rank <= kDualKmax &&
+         h->lev[V.ldual - 1].npairs >= 2 * (int64_t)V.nsm)
+    --V.ldual;
+  // pair levels with boxes of more than kMultiRows points also get a two-pass
+  // plan, which several right-hand sides use: [lfuse, l2max)
+  V.l2max = V.lfuse;
+  while (V.l2max <= kappa && maxcount(V.l2max) > kMultiRows) ++V.l2max;
+  H2D_TRY(build_two_pass(h, V.l2max));
   // single-read levels: pair mode (one block per pair, partials for both
   // sides) or box mode (one warp per row box, partials for the column side)
   std::vector<BoxWork> bw;
@@ -2538,9 +2929,15 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
       ps.flops(2 * two_pass_vals * nrhs);
       const int64_t thr = npart * 32;  // one warp per (task, column)
       if (std::is_same<A, BF16A>::value && nrhs > 1)  // tensor cores
-        k_proj_tc<<<(unsigned)nproj, 128, 0, s>>>(P, V.d_proj,
-                                                  reinterpret_cast<const float*>(xt),
-                                                  reinterpret_cast<float*>(V.d_part));
+        if (V.grp_ok)  // tasks grouped by box: x loaded once per group
+          k_projg_t5<<<(unsigned)std::min<int64_t>(V.pre_grp[l2end], 3 * V.nsm), 256, kGrpSmem,
+                       s>>>(P, V.d_proj, V.d_gtask, V.d_grp, V.pre_grp[l2end],
+                            reinterpret_cast<const float*>(xt),
+                            reinterpret_cast<float*>(V.d_part), V.d_status);
+        else
+          k_proj_t5<<<(unsigned)std::min<int64_t>(nproj, 4 * V.nsm), 128, kT5Smem, s>>>(
+              P, V.d_proj, nproj, reinterpret_cast<const float*>(xt),
+              reinterpret_cast<float*>(V.d_part), V.d_status);
       else if (nrhs >= 24 && sizeof(Val) == 4)  // binary32 sums: tiled over many right-hand sides
         k_projm<A><<<(unsigned)nproj, 256, 0, s>>>(P, V.d_proj, xt,
                                                    reinterpret_cast<Val*>(V.d_part));
@@ -2574,14 +2971,18 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
     PhaseScope ps(h, 4, 1, fs * two_pass_vals + vb * (l2end - 1));
     ps.flops(2 * two_pass_vals * nrhs);
     if (std::is_same<A, BF16A>::value && nrhs > 1)  // tensor cores
-      k_exp_tc<<<(unsigned)nexp, 256, 0, s>>>(P, V.d_exp, reinterpret_cast<const float*>(V.d_t),
-                                              reinterpret_cast<float*>(yl));
+      k_exp_t5<<<(unsigned)std::min<int64_t>(nexp, 4 * V.nsm), 128, kT5Smem, s>>>(
+          P, V.d_exp, nexp, reinterpret_cast<const float*>(V.d_t), reinterpret_cast<float*>(yl),
+          V.d_status);
     else
       k_exp2<A><<<(unsigned)nexp, 256, 0, s>>>(P, V.d_exp, reinterpret_cast<const Val*>(V.d_t),
                                                yl);
   }
   H2D_CK(cudaEventRecord(V.ev_near, sn));
-  if (V.zero_partials) H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, sf));
+  bool any_pair = false;
+  for (int l = l2end; l <= h->kappa; ++l) any_pair = any_pair || P.lmode[l] == LMODE_PAIR;
+  if (V.zero_partials && any_pair)
+    H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs, sf));
   for (int l = l2end; l <= h->kappa; ++l) {
     if (P.lmode[l] != LMODE_PAIR || V.plev[l].nwork == 0) continue;
     const int phase = V.lmode[l] == LMODE_BOX ? 7 : l < V.lpair_small ? 6 : 8;
@@ -2614,9 +3015,26 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   return HODLR2D_OK;
 }
 
+// Reads and clears the device status word of the product kernels (a bounded
+// wait that gave up); synchronises the handle's stream.
+int product_status(hodlr2d* h) {
+  V2Plan& V = h->v2;
+  if (!V.ready || !V.d_status) return HODLR2D_OK;
+  int st = 0;
+  H2D_CK(cudaStreamSynchronize(h->stream));
+  H2D_CK(cudaMemcpy(&st, V.d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) H2D_CK(cudaMemset(V.d_status, 0, sizeof(int)));
+  return st ? HODLR2D_ERR_TIMEOUT : HODLR2D_OK;
+}
+
 // The product in a prepared mode (F64 or DF32) with device x and y.
 int product_device(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   H2D_TRY(plan_v2(h));
+  if (two_pass_end(h, nrhs, mode) > h->v2.two_levels) {  // first product of all levels in two passes
+    H2D_CK(cudaStreamSynchronize(h->stream));
+    H2D_TRY(build_two_pass(h, two_pass_end(h, nrhs, mode)));
+    h->v2.scratch_nrhs = 0;  // the partial sums grew
+  }
   H2D_TRY(scratch_v2(h, nrhs));
   if (mode == HODLR2D_MODE_F64) return run_v2<F64A>(h, x, y, nrhs, mode);
   if (mode == HODLR2D_MODE_DF32) return run_v2<DF32A>(h, x, y, nrhs, mode);
@@ -2715,6 +3133,9 @@ void free_v2(hodlr2d* h) {
   cudaFree(V.d_wtask);
   cudaFree(V.d_sideq);
   cudaFree(V.d_pgrp);
+  cudaFree(V.d_status);
+  cudaFree(V.d_gtask);
+  cudaFree(V.d_grp);
   cudaFree(V.d_bw);
   cudaFree(V.d_nearw);
   cudaFree(V.d_leaf_of);
