@@ -36,8 +36,6 @@ LEAF = 64
 EPS = 1e-8
 A_MQ = 1.0 / np.sqrt(N_FULL)
 ROOT_BOX = (-1.0, -1.0, 2.0)
-WORKLOAD = ("N=2^20 uniform [-1,1]^2 seed 0, MQ sqrt(r^2+a^2) a=2^-10, leaf 64 "
-            "(kappa 8), ACA eps 1e-8, 1 RHS N(0,1) seed 1")
 
 
 def parse():
@@ -240,9 +238,10 @@ class OracleLeg:
 def workload_config(n, kappa, mode, nrhs=1):
     """The bench line's config (the same for both arms)."""
     fb = {"f64": 8, "df32": 8, "f32": 4, "bf16": 2}[mode]
-    w = WORKLOAD if n == N_FULL else WORKLOAD.replace("2^20", str(n))
-    if nrhs > 1:
-        w = w.replace("1 RHS", "%d RHS" % nrhs)
+    lg = int(np.log2(n))
+    nn = "2^%d" % lg if n == 1 << lg else str(n)
+    w = ("N=%s uniform [-1,1]^2 seed 0, MQ sqrt(r^2+a^2) a=1/sqrt(N), leaf 64 (kappa %d), "
+         "ACA eps 1e-8, %d RHS N(0,1) seed 1" % (nn, kappa, nrhs))
     return {"workload": w,
             "n": n, "leaf": LEAF, "eps": EPS, "kernel": "mq", "a": 1.0 / np.sqrt(n), "nrhs": nrhs,
             "mode": mode, "kappa": kappa, "parallelism": "replicas",

@@ -1230,34 +1230,42 @@ __device__ __forceinline__ int f64_segments(int jobs, int rows, int& seglen) {
 
 // One column group of a two-pass projection task: NV >= c columns q0 ..
 // q0 + c - 1 of `mat` (leading dimension ld) against x over the task's rows
-// [r0, r0 + nr), 16 rows per lane (x kept in registers); the columns are
-// visited one after another, so the warp's loads stream one contiguous
-// column slice at a time; column q0 + j's total goes to out[j].
+// [r0, r0 + nr), 16 rows per lane in two halves of 8 (the half's x kept in
+// registers); within a half the columns are visited one after another, so
+// the warp's loads stream one contiguous column slice at a time; column
+// q0 + j's total goes to out[j].
 template <int NV>
 __device__ __forceinline__ void proj64_group(const double* __restrict__ mat, int64_t ld, int c,
                                              const double* __restrict__ xv, int r0, int nr,
                                              int lane, double* __restrict__ out) {
-  constexpr int R = kChunkP / 32;
-  double xr[R];
-#pragma unroll
-  for (int u = 0; u < R; ++u) {
-    const int r = lane + 32 * u;
-    xr[u] = r < nr ? xv[r0 + r] : 0.0;
-  }
+  constexpr int H = kChunkP / 64;  // rows per lane and half
   double acc[NV];
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    acc[j] = 0.0;
-    if (j < c) {
-      const double* col = mat + j * ld + r0;
-      if (nr == kChunkP) {  // a whole chunk: no row checks
+  for (int j = 0; j < NV; ++j) acc[j] = 0.0;
 #pragma unroll
-        for (int u = 0; u < R; ++u) acc[j] = fma(__ldg(col + lane + 32 * u), xr[u], acc[j]);
-      } else {
+  for (int hf = 0; hf < 2; ++hf) {
+    const int rb = 32 * H * hf;  // first row of the half, relative to r0
+    if (rb >= nr) break;         // uniform
+    double xr[H];
 #pragma unroll
-        for (int u = 0; u < R; ++u) {
-          const int r = lane + 32 * u;
-          if (32 * u < nr) acc[j] = fma(r < nr ? __ldg(col + r) : 0.0, xr[u], acc[j]);
+    for (int u = 0; u < H; ++u) {
+      const int r = rb + lane + 32 * u;
+      xr[u] = r < nr ? xv[r0 + r] : 0.0;
+    }
+    const bool full = rb + 32 * H <= nr;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      if (j < c) {
+        const double* col = mat + j * ld + r0 + rb + lane;
+        if (full) {
+#pragma unroll
+          for (int u = 0; u < H; ++u) acc[j] = fma(__ldg(col + 32 * u), xr[u], acc[j]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < H; ++u) {
+            const int r = rb + lane + 32 * u;
+            if (rb + 32 * u < nr) acc[j] = fma(r < nr ? __ldg(col + 32 * u) : 0.0, xr[u], acc[j]);
+          }
         }
       }
     }
@@ -1271,10 +1279,10 @@ __device__ __forceinline__ void proj64_group(const double* __restrict__ mat, int
 // Two-pass projection in binary64: one warp per (task, group of <= 8
 // columns) of the work list pg (task index, first column); the task's k
 // partial sums per right-hand side go where k_proj2 puts them.  Eight
-// columns per warp keep the registers low enough for 24 resident warps per
-// SM (the loads need them in flight) at 9 additions per 8 columns.
+// columns per warp, 9 additions per 8 columns; registers are kept to 64 so
+// that 32 warps per SM keep enough loads in flight.
 constexpr int kProj64Cols = 8;
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     k_proj64(ArgsV2 P, const ProjTask* __restrict__ tasks, const int2* __restrict__ pg,
              int64_t ngroups, const double* __restrict__ xt, double* __restrict__ part) {
   const int lane = threadIdx.x & 31;
