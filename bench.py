@@ -159,11 +159,14 @@ def peaks():
 
 
 # ncu DRAM traffic (read + write bytes) per algorithmic byte of a kernel,
-# keyed by (phase, mode): k_proj2 (DF32) measured at N = 2^17, 522.9 MB for
-# 514.6 MB of factor values.  Traffic grows with the values, so a launch's
-# traffic is this ratio times its algorithmic bytes.  Remove an entry when its
-# kernel changes.
-NCU_TRAFFIC_RATIO = {("proj", "df32"): 522.9 / 514.6}
+# keyed by (phase, mode), measured at N = 2^17: k_proj2 (DF32) 522.9 MB for
+# 514.6 MB of factor values.  Traffic grows with the units processed, so a
+# launch's traffic is this ratio times its algorithmic bytes.  Remove an entry
+# when its kernel changes.
+NCU_TRAFFIC_RATIO = {("proj", "df32"): 522.9 / 514.6,
+                     # k_near64 at N = 2^17: 3.276 MB of DRAM traffic for 5.243 MB of
+                     # algorithmic bytes (points and x, partly served by L2)
+                     ("near", "f64"): 3.276 / 5.243}
 
 
 def host_cpu():
