@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--nrhs", type=int, default=1, help="right-hand sides per product")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    p.add_argument("--extras", default="all",
+                   help="comma-separated secondary measurements to run (default: all)")
     p.add_argument("--n-learned", type=int, default=1 << 22,
                    help="points of the learned-rank build (log r kernel)")
     return p.parse_args()
@@ -327,7 +329,8 @@ def extra_gmres_nrhs(pkg, inputs, n, stream):
 def extra_batch(pkg, inputs, stream, count=256):
     """Independent point sets (sizes log-uniform in [2048, 65536], rectangles of
     aspect ratio up to 4), IMQ a = 1/sqrt(n_i), binary32 factors, 1-8
-    right-hand sides each, all products replayed as one CUDA graph.  The leaf
+    right-hand sides each, all products replayed as one CUDA graph, then as
+    one persistent cooperative kernel (shapes autotuned).  The leaf
     size is tuned per size class (four log-spaced classes) on one member."""
     import torch
     sets = inputs.point_sets(count, seed=0)
@@ -358,7 +361,7 @@ def extra_batch(pkg, inputs, stream, count=256):
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
     nprod = int(sum(x.shape[0] for x in xs))
-    b = pkg.Batch(mats, stream=stream)
+    b = pkg.Batch(mats, stream=stream, form="graph")
     b.matvec(xs, ys, mode="f32")  # records the graph
     torch.cuda.synchronize()
     e0, e1 = events(stream)
@@ -368,6 +371,24 @@ def extra_batch(pkg, inputs, stream, count=256):
     e1.record(stream)
     torch.cuda.synchronize()
     t_graph = e0.elapsed_time(e1) / 5
+    # one persistent cooperative kernel over all sets, shapes autotuned
+    yp = [torch.empty_like(y) for y in ys]
+    b.set_form("persistent")
+    t0 = time.perf_counter()
+    shapes, _ = b.autotune(xs, yp, mode="f32", reps=3)
+    t_ptune = time.perf_counter() - t0
+    b.matvec(xs, yp, mode="f32")
+    b.check()
+    e0.record(stream)
+    for _ in range(5):
+        b.matvec(xs, yp, mode="f32")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b.check()
+    t_pers = e0.elapsed_time(e1) / 5
+    phases = [round(v, 3) for v in b.phase_ms()]
+    pers_vs_graph = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c))
+                        for a, c in zip(yp, ys))
     for m in mats:
         m.set_stream(stream)
     ys2 = [torch.empty_like(y) for y in ys]
@@ -389,6 +410,13 @@ def extra_batch(pkg, inputs, stream, count=256):
             "leaf_per_class": {str(int(round(edges[c]))): v for c, v in leaf_of.items()},
             "graph_ms": round(t_graph, 3), "sequential_launches_ms": round(t_seq, 3),
             "products_per_s_graph": round(nprod / (t_graph * 1e-3), 1),
+            "persistent_ms": round(t_pers, 3),
+            "products_per_s_persistent": round(nprod / (t_pers * 1e-3), 1),
+            "persistent_shapes": {"pair_rows": shapes[0], "warp_rows": shapes[1]},
+            "persistent_tune_s": round(t_ptune, 2),
+            "persistent_phase_ms": dict(zip(["gather", "pairs_proj_near", "chunk_sums",
+                                             "expansions", "combine"], phases)),
+            "rel2_persistent_vs_graph_max": pers_vs_graph,
             "graph_equals_sequential": same, "rel2_f32_vs_f64_first8": err,
             "tune_s": round(t_tune, 2), "build_s": round(t_build, 2)}
 
@@ -586,16 +614,20 @@ def extra_paper_replay(pkg, inputs, stream):
     return out
 
 
-def extras(pkg, inputs, n, n_learned):
-    """Secondary measurements on one GPU (each section timed on its own)."""
+def extras(pkg, inputs, n, n_learned, names="all"):
+    """Secondary measurements on one GPU (each section timed on its own);
+    names: "all" or a comma-separated subset of the section names."""
     import torch
     stream = torch.cuda.current_stream()
     out = {}
+    pick = None if names == "all" else set(names.split(","))
     for name, fn in (("rbf_system", lambda: extra_gmres_nrhs(pkg, inputs, n, stream)),
                      ("paper_replay", lambda: extra_paper_replay(pkg, inputs, stream)),
                      ("panel_system_log", lambda: extra_panel_system(pkg, inputs, stream)),
                      ("batch_point_sets", lambda: extra_batch(pkg, inputs, stream)),
                      ("learned_rank_log", lambda: extra_learned(pkg, inputs, stream, n_learned))):
+        if pick is not None and name not in pick:
+            continue
         t0 = time.perf_counter()
         out[name] = fn()
         out[name]["section_s"] = round(time.perf_counter() - t0, 1)
@@ -791,7 +823,7 @@ def run_ours(args, ws, rank, local):
         del v["y"]
     g.close()
     if ws == 1 and not args.no_extras:
-        out["extras"] = extras(pkg, inputs, n, args.n_learned)
+        out["extras"] = extras(pkg, inputs, n, args.n_learned, args.extras)
     return out
 
 

@@ -286,19 +286,74 @@ void hodlr2d_rank_model_free(hodlr2d_rank_model_t m);
 int hodlr2d_pair_features(hodlr2d_t h, int64_t* npairs, float* feats, float* log2rank);
 
 /* ----- many independent matrices (point sets of uneven size) -----
- * Not in the paper (deployment batching).  A batch multiplies all its handles
- * with one CUDA graph launch: the first hodlr2d_batch_matvec (and any call
- * whose pointers, nrhs or mode differ from the recorded ones) runs the
- * products once, then records them into a graph (sets spread over eight
- * forked streams); later calls replay that graph on the batch's stream.
- * The handles must outlive the batch and must not be used concurrently with
- * it.  x[i], y[i]: device pointers, n_i x nrhs[i] column-major.  Profiling
- * (hodlr2d_profile) must be off on every handle.  Errors: ARG, STATE, CUDA. */
+ * Not in the paper (deployment batching).  Each set's product is the Alg. 2
+ * product of its own handle.  Two forms:
+ *   HODLR2D_BATCH_GRAPH: the first hodlr2d_batch_matvec (and any call whose
+ *     pointers, nrhs or mode differ from the recorded ones) runs the products
+ *     once, then records them into a CUDA graph (sets spread over eight
+ *     forked streams); later calls replay that graph on the batch's stream.
+ *     Every mode.  Bit for bit the handles' own products.
+ *   HODLR2D_BATCH_PERSISTENT: one cooperative kernel launch multiplies all
+ *     sets (recorded into a graph when the driver allows it), in five phases
+ *     separated by grid barriers: gather; pairs, projections and near field;
+ *     chunk sums; expansions; combine (see hodlr2d_batch_set_shapes).  Modes
+ *     F64 and F32 only (others: ARG).  Within rounding of the handles' own
+ *     products (its sums run in another order).  Each barrier wait is
+ *     bounded (hodlr2d_batch_set_wait_limit); a block whose wait gives up
+ *     records it and the launch ends without writing y:
+ *     hodlr2d_batch_check then returns HODLR2D_ERR_TIMEOUT.
+ *   HODLR2D_BATCH_AUTO (the default): PERSISTENT for F64 and F32 when the
+ *     device supports cooperative launches, else GRAPH.
+ * Either form is set up again when a handle's plans, working memory or
+ * factor copies have changed since the recording.  The handles must outlive
+ * the batch and must not be used concurrently with it.  x[i], y[i]: device
+ * pointers, n_i x nrhs[i] column-major.  Profiling (hodlr2d_profile) must be
+ * off on every handle.  Errors: ARG, STATE, CUDA. */
 typedef struct hodlr2d_batch* hodlr2d_batch_t;
+#define HODLR2D_BATCH_AUTO 0
+#define HODLR2D_BATCH_GRAPH 1
+#define HODLR2D_BATCH_PERSISTENT 2
 int hodlr2d_batch_create(const hodlr2d_t* handles, int count, hodlr2d_batch_t* out);
 int hodlr2d_batch_set_stream(hodlr2d_batch_t b, void* stream);
+/* form: one of HODLR2D_BATCH_*; ARG otherwise. */
+int hodlr2d_batch_set_form(hodlr2d_batch_t b, int form);
+/* Polls of a grid-barrier wait of the persistent form before it gives up
+ * (default 4194304, each poll followed by a sleep of about 64 ns, so at
+ * least a quarter of a second).  0 makes every wait give up at once: a
+ * self-test of the timeout path that leaves the context usable. */
+int hodlr2d_batch_set_wait_limit(hodlr2d_batch_t b, uint32_t polls);
 int hodlr2d_batch_matvec(hodlr2d_batch_t b, const double* const* x, double* const* y,
                          const int* nrhs, int mode);
+/* Synchronises the batch's stream; HODLR2D_ERR_TIMEOUT if a persistent
+ * product since the previous check gave up a barrier wait (its y is not
+ * written), else OK.  Clears the record. */
+int hodlr2d_batch_check(hodlr2d_batch_t b);
+/* The form the last hodlr2d_batch_matvec ran (HODLR2D_BATCH_GRAPH or
+ * HODLR2D_BATCH_PERSISTENT), or -1 before the first. */
+int hodlr2d_batch_last_form(hodlr2d_batch_t b);
+/* Work shapes of the persistent form by box size: the levels whose boxes
+ * hold at most pair_rows points (0 <= pair_rows <= 512) run as pairs, each
+ * stored pair read once (t1 = V^T x_Y, t2 = U^T x_X, then U t1 and V t2):
+ * pairs of at most warp_rows points (0 <= warp_rows <= 64) one per warp, the
+ * others one per 256-thread unit; coarser levels run in two passes
+ * (projections over 512-row chunks, chunk sums, expansions over 256-row
+ * chunks).  Defaults 384 and 64.  Takes effect at the next product. */
+int hodlr2d_batch_set_shapes(hodlr2d_batch_t b, int pair_rows, int warp_rows);
+int hodlr2d_batch_get_shapes(hodlr2d_batch_t b, int* pair_rows, int* warp_rows);
+/* Autotuner of those shapes: times reps persistent products (CUDA events on
+ * the batch's stream, after one untimed product) for each candidate
+ * pair_rows in {0, 64, 128, 256, 384, 512} and warp_rows in {0, 48, 64}
+ * (warp_rows <= pair_rows), keeps the fastest (hodlr2d_batch_set_shapes) and
+ * writes its time per product to *best_ms (may be NULL).  Arguments as in
+ * hodlr2d_batch_matvec (y is overwritten); modes F64 and F32 only.
+ * Synchronises the stream.  Errors: ARG, STATE, CUDA, TIMEOUT. */
+int hodlr2d_batch_autotune(hodlr2d_batch_t b, const double* const* x, double* const* y,
+                           const int* nrhs, int mode, int reps, double* best_ms);
+/* Milliseconds of the five phases of the last persistent product (gather;
+ * pairs, projections and near field; chunk sums; expansions; combine), read
+ * from the device clock at the grid barriers.  ms: host array of 5.
+ * Synchronises the stream.  STATE before the first persistent product. */
+int hodlr2d_batch_phase_ms(hodlr2d_batch_t b, double* ms);
 void hodlr2d_batch_free(hodlr2d_batch_t b);
 
 /* ----- product without any device allocation -----

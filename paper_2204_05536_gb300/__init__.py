@@ -324,11 +324,15 @@ class RankModel:
         return out
 
 
-class Batch:
-    """Independent HODLR2D matrices multiplied with one CUDA graph launch
-    (hodlr2d_batch_*).  Keeps the handles alive."""
+BATCH_FORMS = {"auto": 0, "graph": 1, "persistent": 2}
 
-    def __init__(self, matrices, stream=None):
+
+class Batch:
+    """Independent HODLR2D matrices multiplied as one unit (hodlr2d_batch_*):
+    one CUDA graph launch, or one persistent cooperative kernel over all sets
+    (form "auto", "graph" or "persistent").  Keeps the handles alive."""
+
+    def __init__(self, matrices, stream=None, form: str = "auto"):
         self._lib = load()
         self.mats = list(matrices)
         arr = (C.c_void_p * len(self.mats))(*[m.handle.value for m in self.mats])
@@ -340,16 +344,67 @@ class Batch:
             s = getattr(stream, "cuda_stream", stream)
             check(self._lib.hodlr2d_batch_set_stream(self._h, C.c_void_p(int(s))),
                   "hodlr2d_batch_set_stream")
+        self.set_form(form)
 
-    def matvec(self, xs, ys, mode: str = "f64"):
-        """xs[i], ys[i]: float64 CUDA tensors holding n_i x nrhs_i column-major
-        data (shape (nrhs_i, n_i) contiguous, or (n_i,))."""
+    def set_form(self, form: str):
+        check(self._lib.hodlr2d_batch_set_form(self._h, BATCH_FORMS[form]),
+              "hodlr2d_batch_set_form")
+
+    def set_wait_limit(self, polls: int):
+        """Polls of a grid-barrier wait (persistent form) before it gives up."""
+        check(self._lib.hodlr2d_batch_set_wait_limit(self._h, int(polls)),
+              "hodlr2d_batch_set_wait_limit")
+
+    def check(self):
+        """hodlr2d_batch_check: synchronise; raise if a barrier wait gave up."""
+        check(self._lib.hodlr2d_batch_check(self._h), "hodlr2d_batch_check")
+
+    @property
+    def last_form(self):
+        f = self._lib.hodlr2d_batch_last_form(self._h)
+        return {1: "graph", 2: "persistent"}.get(f)
+
+    def _args(self, xs, ys):
         n = len(self.mats)
         xa = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
         ya = (C.c_void_p * n)(*[y.data_ptr() for y in ys])
         nr = (C.c_int * n)(*[1 if x.dim() == 1 else x.shape[0] for x in xs])
+        return xa, ya, nr
+
+    def matvec(self, xs, ys, mode: str = "f64"):
+        """xs[i], ys[i]: float64 CUDA tensors holding n_i x nrhs_i column-major
+        data (shape (nrhs_i, n_i) contiguous, or (n_i,))."""
+        xa, ya, nr = self._args(xs, ys)
         check(self._lib.hodlr2d_batch_matvec(self._h, xa, ya, nr, MODES[mode]),
               "hodlr2d_batch_matvec")
+
+    def set_shapes(self, pair_rows: int, warp_rows: int):
+        """Persistent form: levels of boxes <= pair_rows points run as pairs
+        (one per warp up to warp_rows points), coarser ones in two passes."""
+        check(self._lib.hodlr2d_batch_set_shapes(self._h, int(pair_rows), int(warp_rows)),
+              "hodlr2d_batch_set_shapes")
+
+    def shapes(self):
+        a, b = C.c_int(), C.c_int()
+        check(self._lib.hodlr2d_batch_get_shapes(self._h, C.byref(a), C.byref(b)),
+              "hodlr2d_batch_get_shapes")
+        return a.value, b.value
+
+    def autotune(self, xs, ys, mode: str = "f32", reps: int = 3):
+        """hodlr2d_batch_autotune: time the persistent form's shape candidates
+        on these inputs, keep the fastest; returns ((pair_rows, warp_rows),
+        ms per product)."""
+        xa, ya, nr = self._args(xs, ys)
+        ms = C.c_double()
+        check(self._lib.hodlr2d_batch_autotune(self._h, xa, ya, nr, MODES[mode], int(reps),
+                                               C.byref(ms)), "hodlr2d_batch_autotune")
+        return self.shapes(), ms.value
+
+    def phase_ms(self):
+        """Milliseconds of the five phases of the last persistent product."""
+        out = (C.c_double * 5)()
+        check(self._lib.hodlr2d_batch_phase_ms(self._h, out), "hodlr2d_batch_phase_ms")
+        return list(out)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

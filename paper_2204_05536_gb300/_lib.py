@@ -87,6 +87,15 @@ SIGNATURES = {
     "hodlr2d_batch_create": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
     "hodlr2d_batch_set_stream": (C.c_int, [_P, _P]),
     "hodlr2d_batch_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+    "hodlr2d_batch_set_form": (C.c_int, [_P, C.c_int]),
+    "hodlr2d_batch_set_wait_limit": (C.c_int, [_P, C.c_uint32]),
+    "hodlr2d_batch_check": (C.c_int, [_P]),
+    "hodlr2d_batch_last_form": (C.c_int, [_P]),
+    "hodlr2d_batch_set_shapes": (C.c_int, [_P, C.c_int, C.c_int]),
+    "hodlr2d_batch_get_shapes": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "hodlr2d_batch_autotune": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int,
+                                         C.POINTER(C.c_double)]),
+    "hodlr2d_batch_phase_ms": (C.c_int, [_P, _P]),
     "hodlr2d_batch_free": (None, [_P]),
     "hodlr2d_free": (None, [_P]),
     "hodlr2d_strerror": (C.c_char_p, [C.c_int]),

@@ -290,6 +290,7 @@ int hodlr2d_release(hodlr2d_t h, int mode) {
   }
   h->prepared[mode] = false;
   if (mode == HODLR2D_MODE_F64) h->f64_released = true;
+  ++h->gen;
   return HODLR2D_OK;
 }
 

@@ -1,7 +1,9 @@
 // Many independent HODLR2D matrices (point sets of uneven size) multiplied
-// as one unit: the products of all sets are recorded once into a CUDA graph
-// (sets spread over kLanes forked streams, each set's own near/far streams
-// nested inside) and replayed with one graph launch per call.
+// as one unit, in one of two forms: the products of all sets recorded once
+// into a CUDA graph (sets spread over kLanes forked streams, each set's own
+// near/far streams nested inside) and replayed with one graph launch per
+// call; or one persistent cooperative kernel over all sets (product.cu),
+// itself recorded into a graph.
 #include <vector>
 
 #include "internal.h"
@@ -27,7 +29,34 @@ struct hodlr2d_batch {
   std::vector<int> gnrhs;
   int gmode = -1;
   cudaStream_t gstream = 0;
+  std::vector<uint64_t> ggen;  // the handles' buffer generations
+  // persistent form, what its descriptors were made for, and its launch
+  // recorded into a graph (when the driver takes a cooperative launch in a
+  // capture; else it is launched directly)
+  int form = HODLR2D_BATCH_AUTO;
+  int last_form = -1;
+  bool coop = false;  // the device supports cooperative launches
+  h2d::BatchPersist bp;
+  std::vector<const double*> px;
+  std::vector<double*> py;
+  std::vector<int> pnrhs;
+  std::vector<uint64_t> pgen;
+  cudaGraph_t pgraph = nullptr;
+  cudaGraphExec_t pexec = nullptr;
 };
+
+// True when every handle's buffers are those a recording was made for.
+static bool gens_match(const std::vector<hodlr2d*>& sets, const std::vector<uint64_t>& g) {
+  if (g.size() != sets.size()) return false;
+  for (size_t i = 0; i < sets.size(); ++i)
+    if (sets[i]->gen != g[i]) return false;
+  return true;
+}
+static std::vector<uint64_t> gens_of(const std::vector<hodlr2d*>& sets) {
+  std::vector<uint64_t> g(sets.size());
+  for (size_t i = 0; i < sets.size(); ++i) g[i] = sets[i]->gen;
+  return g;
+}
 
 using namespace h2d;
 
@@ -36,6 +65,14 @@ static void batch_drop_graph(hodlr2d_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
   b->graph = nullptr;
+}
+static void batch_drop_persistent(hodlr2d_batch* b) {
+  if (b->pexec) cudaGraphExecDestroy(b->pexec);
+  if (b->pgraph) cudaGraphDestroy(b->pgraph);
+  b->pexec = nullptr;
+  b->pgraph = nullptr;
+  batch_persist_free(&b->bp);
+  b->px.clear();
 }
 
 extern "C" {
@@ -60,6 +97,10 @@ int hodlr2d_batch_create(const hodlr2d_t* handles, int count, hodlr2d_batch_t* o
   }
   if (!rc && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
     rc = HODLR2D_ERR_CUDA;
+  int coop = 0;
+  if (!rc && cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device) != cudaSuccess)
+    rc = HODLR2D_ERR_CUDA;
+  b->coop = coop != 0;
   if (rc) {
     (void)cudaGetLastError();
     hodlr2d_batch_free(b);
@@ -75,6 +116,142 @@ int hodlr2d_batch_set_stream(hodlr2d_batch_t b, void* stream) {
   return HODLR2D_OK;
 }
 
+int hodlr2d_batch_set_form(hodlr2d_batch_t b, int form) {
+  if (!b || form < HODLR2D_BATCH_AUTO || form > HODLR2D_BATCH_PERSISTENT) return HODLR2D_ERR_ARG;
+  b->form = form;
+  return HODLR2D_OK;
+}
+
+int hodlr2d_batch_set_wait_limit(hodlr2d_batch_t b, uint32_t polls) {
+  if (!b) return HODLR2D_ERR_ARG;
+  if (b->bp.polls != polls) b->px.clear();  // the recorded launch holds the old limit
+  b->bp.polls = polls;
+  return HODLR2D_OK;
+}
+
+int hodlr2d_batch_last_form(hodlr2d_batch_t b) { return b ? b->last_form : -1; }
+
+int hodlr2d_batch_check(hodlr2d_batch_t b) {
+  if (!b) return HODLR2D_ERR_ARG;
+  H2D_CK(cudaStreamSynchronize(b->stream));
+  return batch_persist_status(b->bp, b->stream);
+}
+
+int hodlr2d_batch_phase_ms(hodlr2d_batch_t b, double* ms) {
+  if (!b || !ms) return HODLR2D_ERR_ARG;
+  return batch_persist_phase_ms(b->bp, b->stream, ms);
+}
+
+// Records the persistent launch into a graph on a private stream; false (and
+// no graph) when the capture or instantiation is refused.
+static bool batch_record_persistent(hodlr2d_batch* b) {
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const int rc = batch_persist_launch(b->bp, cs);
+    ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && rc == HODLR2D_OK && g;
+  }
+  if (ok) ok = cudaGraphInstantiate(&b->pexec, g, 0) == cudaSuccess;
+  if (!ok) {
+    (void)cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    b->pexec = nullptr;
+    g = nullptr;
+  }
+  b->pgraph = g;
+  cudaStreamDestroy(cs);
+  return ok;
+}
+
+// One persistent product of all sets; descriptors (and the recorded launch)
+// are rebuilt when the pointers, nrhs, mode or the handles' buffers change.
+static int batch_persistent(hodlr2d_batch* b, const double* const* x, double* const* y,
+                            const int* nrhs, int mode) {
+  const int count = (int)b->sets.size();
+  bool same = b->bp.d_sets && b->bp.mode == mode && !b->px.empty() &&
+              gens_match(b->sets, b->pgen);
+  for (int i = 0; same && i < count; ++i)
+    same = b->px[i] == x[i] && b->py[i] == y[i] && b->pnrhs[i] == nrhs[i];
+  if (!same) {
+    for (hodlr2d* h : b->sets) H2D_CK(cudaStreamSynchronize(h->stream));
+    H2D_CK(cudaStreamSynchronize(b->stream));
+    batch_drop_persistent(b);
+    H2D_TRY(batch_persist_setup(b->sets.data(), count, x, y, nrhs, mode, &b->bp));
+    b->px.assign(x, x + count);
+    b->py.assign(y, y + count);
+    b->pnrhs.assign(nrhs, nrhs + count);
+    b->pgen = gens_of(b->sets);
+    batch_record_persistent(b);
+  }
+  if (b->pexec) {
+    H2D_CK(cudaGraphLaunch(b->pexec, b->stream));
+    return HODLR2D_OK;
+  }
+  return batch_persist_launch(b->bp, b->stream);
+}
+
+int hodlr2d_batch_set_shapes(hodlr2d_batch_t b, int pair_rows, int warp_rows) {
+  if (!b || pair_rows < 0 || warp_rows < 0 || warp_rows > 64 || pair_rows > 512)
+    return HODLR2D_ERR_ARG;
+  if (b->bp.pair_rows != pair_rows || b->bp.warp_rows != warp_rows) b->px.clear();
+  b->bp.pair_rows = pair_rows;
+  b->bp.warp_rows = warp_rows;
+  return HODLR2D_OK;
+}
+
+int hodlr2d_batch_get_shapes(hodlr2d_batch_t b, int* pair_rows, int* warp_rows) {
+  if (!b || !pair_rows || !warp_rows) return HODLR2D_ERR_ARG;
+  *pair_rows = b->bp.pair_rows;
+  *warp_rows = b->bp.warp_rows;
+  return HODLR2D_OK;
+}
+
+int hodlr2d_batch_autotune(hodlr2d_batch_t b, const double* const* x, double* const* y,
+                           const int* nrhs, int mode, int reps, double* best_ms) {
+  if (!b || !x || !y || !nrhs || reps < 1) return HODLR2D_ERR_ARG;
+  if ((mode != HODLR2D_MODE_F64 && mode != HODLR2D_MODE_F32) || !b->coop) return HODLR2D_ERR_ARG;
+  static const int kPair[] = {0, 64, 128, 256, 384, 512};
+  static const int kWarp[] = {0, 48, 64};
+  const int form = b->form;
+  b->form = HODLR2D_BATCH_PERSISTENT;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = HODLR2D_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    rc = HODLR2D_ERR_CUDA;
+  float best = -1.f;
+  int bp_rows = b->bp.pair_rows, bw_rows = b->bp.warp_rows;
+  for (int pr : kPair)
+    for (int wr : kWarp) {
+      if (rc || wr > pr) continue;
+      rc = hodlr2d_batch_set_shapes(b, pr, wr);
+      if (!rc) rc = hodlr2d_batch_matvec(b, x, y, nrhs, mode);  // set-up and one warm launch
+      if (!rc) rc = hodlr2d_batch_check(b);
+      if (rc) break;
+      if (cudaEventRecord(e0, b->stream) != cudaSuccess) rc = HODLR2D_ERR_CUDA;
+      for (int r = 0; r < reps && !rc; ++r) rc = hodlr2d_batch_matvec(b, x, y, nrhs, mode);
+      if (!rc && cudaEventRecord(e1, b->stream) != cudaSuccess) rc = HODLR2D_ERR_CUDA;
+      if (!rc) rc = hodlr2d_batch_check(b);
+      float ms = 0.f;
+      if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = HODLR2D_ERR_CUDA;
+      if (!rc && (best < 0.f || ms < best)) {
+        best = ms;
+        bp_rows = pr;
+        bw_rows = wr;
+      }
+    }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  b->form = form;
+  if (rc) return rc;
+  if (best_ms) *best_ms = best / reps;
+  return hodlr2d_batch_set_shapes(b, bp_rows, bw_rows);
+}
+
 int hodlr2d_batch_matvec(hodlr2d_batch_t b, const double* const* x, double* const* y,
                          const int* nrhs, int mode) {
   if (!b || !x || !y || !nrhs || mode < 0 || mode > 3) return HODLR2D_ERR_ARG;
@@ -86,7 +263,16 @@ int hodlr2d_batch_matvec(hodlr2d_batch_t b, const double* const* x, double* cons
     if (!h->prepared[mode]) return HODLR2D_ERR_STATE;
     if (h->prof_on) return HODLR2D_ERR_STATE;  // event timing cannot be recorded
   }
-  bool same = b->exec && b->gmode == mode && b->gstream == b->stream;
+  const bool mode_ok = mode == HODLR2D_MODE_F64 || mode == HODLR2D_MODE_F32;
+  if (b->form == HODLR2D_BATCH_PERSISTENT && (!mode_ok || !b->coop)) return HODLR2D_ERR_ARG;
+  if (b->form == HODLR2D_BATCH_PERSISTENT || (b->form == HODLR2D_BATCH_AUTO && mode_ok && b->coop)) {
+    H2D_TRY(batch_persistent(b, x, y, nrhs, mode));
+    b->last_form = HODLR2D_BATCH_PERSISTENT;
+    return HODLR2D_OK;
+  }
+  b->last_form = HODLR2D_BATCH_GRAPH;
+  bool same = b->exec && b->gmode == mode && b->gstream == b->stream &&
+              gens_match(b->sets, b->ggen);
   for (int i = 0; same && i < count; ++i)
     same = b->gx[i] == x[i] && b->gy[i] == y[i] && b->gnrhs[i] == nrhs[i];
   if (!same) {
@@ -144,6 +330,7 @@ int hodlr2d_batch_matvec(hodlr2d_batch_t b, const double* const* x, double* cons
     b->gnrhs.assign(nrhs, nrhs + count);
     b->gmode = mode;
     b->gstream = b->stream;
+    b->ggen = gens_of(b->sets);
     if (cap) {  // replay on the legacy stream, then drop the private one
       H2D_CK(cudaStreamSynchronize(cap));
       cudaStreamDestroy(cap);
@@ -156,6 +343,7 @@ int hodlr2d_batch_matvec(hodlr2d_batch_t b, const double* const* x, double* cons
 void hodlr2d_batch_free(hodlr2d_batch_t b) {
   if (!b) return;
   batch_drop_graph(b);
+  batch_drop_persistent(b);
   for (int j = 0; j < hodlr2d_batch::kLanes; ++j) {
     if (b->lanes[j]) cudaStreamDestroy(b->lanes[j]);
     if (b->join[j]) cudaEventDestroy(b->join[j]);

@@ -150,6 +150,27 @@ struct V2Plan {
   cudaEvent_t ev_in = nullptr, ev_near = nullptr, ev_far = nullptr;
 };
 
+// A persistent batch product (product.cu): device descriptors of the sets,
+// prefix unit counts of the five phases, the pair items, the barrier words.
+struct BatchPersist {
+  void* d_sets = nullptr;
+  int64_t* d_pre = nullptr;
+  void* d_sync = nullptr;
+  void* d_work = nullptr;
+  int count = 0, mode = -1, grid = 0;
+  uint32_t polls = 1u << 22;  // polls of a barrier wait before it gives up
+  // shapes by size class: levels whose boxes hold at most pair_rows points
+  // run as pairs (one pair per 256-thread unit, or per warp for pairs of at
+  // most warp_rows points); coarser levels run in two passes
+  int pair_rows = 384, warp_rows = 64;
+};
+int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, double* const* y,
+                        const int* nrhs, int mode, BatchPersist* bp);
+int batch_persist_launch(const BatchPersist& bp, cudaStream_t s);
+int batch_persist_status(const BatchPersist& bp, cudaStream_t s);
+int batch_persist_phase_ms(const BatchPersist& bp, cudaStream_t s, double* ms);
+void batch_persist_free(BatchPersist* bp);
+
 }  // namespace h2d
 
 struct hodlr2d {
@@ -176,6 +197,9 @@ struct hodlr2d {
   bool has_factors = false;
   bool prepared[4] = {true, false, false, false};
   bool f64_released = false;  // hodlr2d_release dropped the binary64 factors
+  // bumped whenever device buffers a recorded batch product points to may
+  // have moved (plans, scratch, factor copies)
+  uint64_t gen = 0;
 
   // matvec plan
   int64_t nproj = 0, nexp = 0;

@@ -121,13 +121,23 @@ __device__ __forceinline__ float2 shfl_idx(float2 v, int src) {
 // ---------------------------------------------------------------------------
 // gather x into tree order
 // ---------------------------------------------------------------------------
+// The kernels of the two-pass product are written as device bodies with an
+// explicit work index (a point, a warp's item or a block's task) under thin
+// kernel wrappers, so that the persistent batch kernel (k_batch) runs the
+// same code.
 template <class A>
-__global__ void k_gather2(const double* __restrict__ x, const int64_t* __restrict__ perm,
-                          int64_t n, int nrhs, typename A::val* __restrict__ xt) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void gather2_body(const double* __restrict__ x,
+                                             const int64_t* __restrict__ perm, int64_t n,
+                                             int nrhs, typename A::val* __restrict__ xt,
+                                             int64_t i) {
   if (i >= n) return;
   const int64_t g = perm[i];
   for (int c = 0; c < nrhs; ++c) xt[i + c * n] = A::from_double(x[g + c * n]);
+}
+template <class A>
+__global__ void k_gather2(const double* __restrict__ x, const int64_t* __restrict__ perm,
+                          int64_t n, int nrhs, typename A::val* __restrict__ xt) {
+  gather2_body<A>(x, perm, n, nrhs, xt, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -177,16 +187,15 @@ struct NearF64 {  // binary64 points, entries and sums (bound by the binary64 pi
 // binary32 entry chains, which need the occupancy more than registers
 // (measured 0.85 -> 0.68 ms at N = 2^20).
 template <class NP, int NRH>
-__global__ void __launch_bounds__(32 * kNearWarps, NP::kMinBlocks)
-    k_near_warp(const typename NP::pt* __restrict__ xf, const typename NP::pt* __restrict__ yf,
-                const int32_t* __restrict__ leaf_off, int kappa, const int2* __restrict__ work,
-                int64_t nwork, typename NP::K kp, const typename NP::A::val* __restrict__ xt,
-                int64_t n, int nrhs, typename NP::A::val* __restrict__ yout) {
+__device__ __forceinline__ void near_warp_body(
+    const typename NP::pt* __restrict__ xf, const typename NP::pt* __restrict__ yf,
+    const int32_t* __restrict__ leaf_off, int kappa, const int2* __restrict__ work, int64_t nwork,
+    const typename NP::K& kp, const typename NP::A::val* __restrict__ xt, int64_t n, int nrhs,
+    typename NP::A::val* __restrict__ yout, int64_t wi) {
   using A = typename NP::A;
   using Val = typename A::val;
   using Pt = typename NP::pt;
   const int lane = threadIdx.x & 31;
-  const int64_t wi = (int64_t)blockIdx.x * kNearWarps + (threadIdx.x >> 5);
   if (wi >= nwork) return;
   // work item: (leaf, first target); a leaf of more than 32 points is split
   // into items of 32 targets, each against all of the leaf's sources
@@ -266,6 +275,15 @@ __global__ void __launch_bounds__(32 * kNearWarps, NP::kMinBlocks)
         for (int r = 0; r < nc; ++r) yout[(int64_t)(c0 + r) * n + it] = res[r];
     }
   }
+}
+template <class NP, int NRH>
+__global__ void __launch_bounds__(32 * kNearWarps, NP::kMinBlocks)
+    k_near_warp(const typename NP::pt* __restrict__ xf, const typename NP::pt* __restrict__ yf,
+                const int32_t* __restrict__ leaf_off, int kappa, const int2* __restrict__ work,
+                int64_t nwork, typename NP::K kp, const typename NP::A::val* __restrict__ xt,
+                int64_t n, int nrhs, typename NP::A::val* __restrict__ yout) {
+  near_warp_body<NP, NRH>(xf, yf, leaf_off, kappa, work, nwork, kp, xt, n, nrhs, yout,
+                          (int64_t)blockIdx.x * kNearWarps + (threadIdx.x >> 5));
 }
 
 // ---------------------------------------------------------------------------
@@ -752,10 +770,12 @@ __global__ void __launch_bounds__(T)
 // of X and of Y) for the pass's NR right-hand sides in registers; each column
 // of U and V is loaded once per pass and used for all of them.  The 2 NR
 // sums of a column reduce like k_pairg's.
+// (the T threads tid = 0 .. T - 1 that call it take pair wk together; with
+// T = 32 they are one warp and the body never synchronises the block)
 template <class A, int T, int RM, int NR>
-__global__ void __launch_bounds__(T)
-    k_pairm(ArgsV2 P, const int2* __restrict__ work, const typename A::val* __restrict__ xt,
-            typename A::val* __restrict__ ppart) {
+__device__ __forceinline__ void pairm_body(const ArgsV2& P, const int2 wk,
+                                           const typename A::val* __restrict__ xt,
+                                           typename A::val* __restrict__ ppart, const int tid) {
   using V = typename A::val;
   using F = typename A::fac;
   using Acc = typename A::acc;
@@ -764,8 +784,7 @@ __global__ void __launch_bounds__(T)
   constexpr int SH = 5 - ilog2c(NV);
   __shared__ V red[2][NW > 1 ? NW : 1][NV];
   __shared__ V tot[2][NV];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int2 wk = work[blockIdx.x];
+  const int lane = tid & 31, warp = tid >> 5;
   const LevelV2& L = P.lev[wk.x];
   const PairMeta PM = L.meta[wk.y];
   const int m = PM.m, n = PM.n, k = PM.k;
@@ -813,7 +832,7 @@ __global__ void __launch_bounds__(T)
       }
       const V mine = warp_reduce_scatter<A, NV>(s, lane);
       V t[NV];
-      if (NW == 1) {
+      if constexpr (NW == 1) {
 #pragma unroll
         for (int c = 0; c < NV; ++c) t[c] = shfl_idx(mine, c << SH);
       } else {
@@ -860,6 +879,12 @@ __global__ void __launch_bounds__(T)
       }
     }
   }
+}
+template <class A, int T, int RM, int NR>
+__global__ void __launch_bounds__(T)
+    k_pairm(ArgsV2 P, const int2* __restrict__ work, const typename A::val* __restrict__ xt,
+            typename A::val* __restrict__ ppart) {
+  pairm_body<A, T, RM, NR>(P, work[blockIdx.x], xt, ppart, threadIdx.x);
 }
 
 // Sub-warp form of k_pairg for the finest levels (boxes of <= kBoxRows
@@ -1447,14 +1472,13 @@ __global__ void __launch_bounds__(32 * kPair64Warps)
 // keep them in registers across the right-hand sides, and reduce by shuffles.
 // wtask[w] is the task of warp w; its column is w - out[task].
 template <class A>
-__global__ void __launch_bounds__(256)
-    k_proj2(ArgsV2 P, const ProjTask* __restrict__ tasks, const int32_t* __restrict__ wtask,
-            int64_t nwarps, const typename A::val* __restrict__ xt,
-            typename A::val* __restrict__ part) {
+__device__ __forceinline__ void proj2_body(const ArgsV2& P, const ProjTask* __restrict__ tasks,
+                                           const int32_t* __restrict__ wtask, int64_t nwarps,
+                                           const typename A::val* __restrict__ xt,
+                                           typename A::val* __restrict__ part, int64_t w) {
   using V = typename A::val;
   using Acc = typename A::acc;
   constexpr int R = kChunkP / 32;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= nwarps) return;
   const int64_t lo = wtask[w];
@@ -1482,6 +1506,14 @@ __global__ void __launch_bounds__(256)
     const V sum = A::warp_sum(a);
     if (lane == 0) part[T.out * P.nrhs + (int64_t)c * k + q] = sum;
   }
+}
+template <class A>
+__global__ void __launch_bounds__(256)
+    k_proj2(ArgsV2 P, const ProjTask* __restrict__ tasks, const int32_t* __restrict__ wtask,
+            int64_t nwarps, const typename A::val* __restrict__ xt,
+            typename A::val* __restrict__ part) {
+  proj2_body<A>(P, tasks, wtask, nwarps, xt, part,
+                (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
 }
 
 // Several right-hand sides (two-pass levels): one block of 256 threads per
@@ -2086,13 +2118,13 @@ __global__ void __launch_bounds__(128)
 // shuffle tree adds the 32 lane sums (one right-hand side), or lane c sums
 // all chunks of right-hand side c (several).  red[2 s] = {first task, count}.
 template <class A>
-__global__ void __launch_bounds__(256)
-    k_tsum2(ArgsV2 P, const ProjTask* __restrict__ tasks, const int64_t* __restrict__ red,
-            const int64_t* __restrict__ sideq, int64_t nwork,
-            const typename A::val* __restrict__ part, typename A::val* __restrict__ t,
-            int64_t min_count = 0) {
+__device__ __forceinline__ void tsum2_body(const ArgsV2& P, const ProjTask* __restrict__ tasks,
+                                           const int64_t* __restrict__ red,
+                                           const int64_t* __restrict__ sideq, int64_t nwork,
+                                           const typename A::val* __restrict__ part,
+                                           typename A::val* __restrict__ t, int64_t min_count,
+                                           int64_t w) {
   using V = typename A::val;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= nwork) return;
   const int64_t s = sideq[2 * w];
@@ -2121,23 +2153,34 @@ __global__ void __launch_bounds__(256)
     if (lane == 0) out[c * k + q] = acc;
   }
 }
+template <class A>
+__global__ void __launch_bounds__(256)
+    k_tsum2(ArgsV2 P, const ProjTask* __restrict__ tasks, const int64_t* __restrict__ red,
+            const int64_t* __restrict__ sideq, int64_t nwork,
+            const typename A::val* __restrict__ part, typename A::val* __restrict__ t,
+            int64_t min_count = 0) {
+  tsum2_body<A>(P, tasks, red, sideq, nwork, part, t, min_count,
+                (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+}
 
 // One block per expansion task (256 rows of one box): the box's list
 // (matrix offset, rank, t offset per entry) is staged in shared memory once,
 // then one thread per row sums U t1 / V t2 over the list in ascending partner
 // order, eight independent loads at a time.
 
+// (blocks of 256 threads; every thread of the block calls it with the same
+// task: it synchronises the block once)
 template <class A>
-__global__ void __launch_bounds__(256)
-    k_exp2(ArgsV2 P, const ExpTask* __restrict__ tasks, const typename A::val* __restrict__ t,
-           typename A::val* __restrict__ yl) {
+__device__ __forceinline__ void exp2_body(const ArgsV2& P, const ExpTask* __restrict__ tasks,
+                                          const typename A::val* __restrict__ t,
+                                          typename A::val* __restrict__ yl, int64_t bid) {
   using V = typename A::val;
   using Acc = typename A::acc;
   using F = typename A::fac;
   __shared__ int64_t s_off[kExpMaxEnt];
   __shared__ int64_t s_toff[kExpMaxEnt];
   __shared__ int s_k[kExpMaxEnt];
-  const ExpTask T = tasks[blockIdx.x];
+  const ExpTask T = tasks[bid];
   const int l = T.level;
   const LevelV2& L = P.lev[l];
   const uint32_t X = (uint32_t)T.box;
@@ -2209,18 +2252,25 @@ __global__ void __launch_bounds__(256)
     yl[((int64_t)l * P.nrhs + c) * P.n + base + r] = A::fin(a);
   }
 }
+template <class A>
+__global__ void __launch_bounds__(256)
+    k_exp2(ArgsV2 P, const ExpTask* __restrict__ tasks, const typename A::val* __restrict__ t,
+           typename A::val* __restrict__ yl) {
+  exp2_body<A>(P, tasks, t, yl, blockIdx.x);
+}
 
 // ---------------------------------------------------------------------------
 // combine: y[perm[i]] = near + sum over levels of (own / two-pass result)
 // + the partials of the pairs in which the point's box is the column side
 // ---------------------------------------------------------------------------
 template <class A>
-__global__ void k_combine2(ArgsV2 P, const typename A::val* __restrict__ yl,
-                           const typename A::val* __restrict__ ppart,
-                           const int32_t* __restrict__ leaf_of, const int64_t* __restrict__ perm,
-                           double* __restrict__ y) {
+__device__ __forceinline__ void combine2_body(const ArgsV2& P,
+                                              const typename A::val* __restrict__ yl,
+                                              const typename A::val* __restrict__ ppart,
+                                              const int32_t* __restrict__ leaf_of,
+                                              const int64_t* __restrict__ perm,
+                                              double* __restrict__ y, int64_t i) {
   using V = typename A::val;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= P.n) return;
   const uint32_t leaf = (uint32_t)leaf_of[i];
   const int64_t g = perm[i];
@@ -2244,6 +2294,13 @@ __global__ void k_combine2(ArgsV2 P, const typename A::val* __restrict__ yl,
     }
     y[g + (int64_t)c * P.n] = A::to_double(acc);
   }
+}
+template <class A>
+__global__ void k_combine2(ArgsV2 P, const typename A::val* __restrict__ yl,
+                           const typename A::val* __restrict__ ppart,
+                           const int32_t* __restrict__ leaf_of, const int64_t* __restrict__ perm,
+                           double* __restrict__ y) {
+  combine2_body<A>(P, yl, ppart, leaf_of, perm, y, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // entry e of a box list (pair * 2 + side) -> that side's partial offset << 1 | side
@@ -2500,6 +2557,7 @@ static int build_two_pass(hodlr2d* h, int lmax) {
   if (!red.empty())
     H2D_CK(cudaMemcpy(V.d_red, red.data(), sizeof(int64_t) * red.size(), cudaMemcpyHostToDevice));
   V.two_levels = lmax;
+  ++h->gen;
   return HODLR2D_OK;
 }
 
@@ -2736,6 +2794,7 @@ int scratch_v2(hodlr2d* h, int nrhs) {
   H2D_CK(cudaMalloc(&V.d_part, 8 * std::max<int64_t>(V.proj_partials, 1) * nrhs));
   H2D_CK(cudaMalloc(&V.d_t, 8 * std::max<int64_t>(h->t_total, 1) * nrhs));
   V.scratch_nrhs = nrhs;
+  ++h->gen;
   return HODLR2D_OK;
 }
 
@@ -3021,6 +3080,357 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   }
   H2D_CK(cudaGetLastError());
   return HODLR2D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batch product: the products of many independent handles (point
+// sets of uneven size) in one cooperative kernel launch.  Per set, the levels
+// whose boxes hold at most pair_rows points run as pairs (each stored pair
+// read once: t1 = V^T x_Y and t2 = U^T x_X, then U t1 and V t2 into the
+// pair's partial results); the coarser levels run in two passes
+// (projections over row chunks, chunk sums, expansions).  The work falls
+// into five phases, each a flat list of units over all sets (a unit is the
+// work of one 256-thread block):
+//   0 gather x into tree order;
+//   1 pairs of more than warp_rows points (one pair per unit), the two-pass
+//     projections, the near field, pairs of at most warp_rows points (one
+//     pair per warp) -- independent work, longest units first;
+//   2 chunk sums; 3 expansions; 4 combine.
+// Blocks walk a phase's units (grid-stride; a unit finds its set by binary
+// search over the phase's prefix counts), then meet at a grid barrier.  All
+// blocks are resident (cooperative launch), and every barrier wait is
+// bounded: a block that polls `polls` times in vain records it in the status
+// word and leaves, so the launch always ends.  The last block out resets the
+// barrier counters for the next launch, so one launch is the whole product.
+// ---------------------------------------------------------------------------
+constexpr int kBatchMinBlocks = 3;  // 24 warps per SM (80 registers a thread)
+constexpr int kBatchBlockRows = 512;  // largest box of a one-pair-per-unit item (2 rows a thread)
+
+struct BatchSet {
+  ArgsV2 P;                   // LMODE_TWO below the first pair level, LMODE_PAIR from it on
+  const double* x;            // caller's x and y (n x nrhs, column-major)
+  double* y;
+  const int64_t* perm;
+  const int32_t* leaf_of;
+  void* xt;                   // the handle's scratch
+  void* yl;
+  void* ppart;
+  void* part;
+  void* t;
+  const void* xf;             // near-field points of the mode
+  const void* yf;
+  KernelParams kp;            // binary64 entries
+  KernelF32 kf32;             // binary32 entries
+  const int2* nearw;
+  int64_t nnearw;
+  const ProjTask* proj;
+  const int32_t* wtask;
+  int64_t npart;              // projection warps
+  const int64_t* red;
+  const int64_t* sideq;
+  int64_t ntsum;              // chunk-sum warps
+  const ExpTask* exps;
+  int64_t nexp;
+  const int2* pwork;          // pair items (level, pair): npb unit items, then npw warp items
+  int64_t npb, npw;
+  int64_t u_proj, u_near;     // phase-1 units of the projections and of the near field
+};
+
+// Device words of a persistent launch.
+struct BatchSync {
+  unsigned bar;     // barrier arrivals of the running launch
+  unsigned exit;    // blocks that have left
+  int status;       // nonzero: a barrier wait gave up
+  int pad;
+  unsigned long long ts[6];  // %globaltimer: start, after each barrier, end
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool batch_barrier(BatchSync* sy, unsigned target, uint32_t polls) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's writes before its arrival
+    atomicAdd(&sy->bar, 1u);
+    int ok = 0;
+    for (uint32_t it = 0; it < polls; ++it) {
+      if (*reinterpret_cast<volatile unsigned*>(&sy->bar) >= target) {
+        ok = 1;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (!ok) atomicOr(&sy->status, 1);
+    __threadfence();  // the other blocks' writes before this block's reads
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <class A, class NP>
+__device__ __forceinline__ void batch_unit(const BatchSet& S, int ph, int64_t lv) {
+  using V = typename A::val;
+  constexpr int NRM = sizeof(typename A::acc) == 4 ? 4 : 2;  // right-hand sides per pair pass
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  V* xt = reinterpret_cast<V*>(S.xt);
+  V* yl = reinterpret_cast<V*>(S.yl);
+  V* part = reinterpret_cast<V*>(S.part);
+  V* tt = reinterpret_cast<V*>(S.t);
+  V* ppart = reinterpret_cast<V*>(S.ppart);
+  const bool one = S.P.nrhs == 1;
+  switch (ph) {
+    case 0:
+      gather2_body<A>(S.x, S.perm, S.P.n, S.P.nrhs, xt, lv * 256 + tid);
+      return;
+    case 1: {
+      if (lv < S.npb) {  // one pair of more than warp_rows points
+        if (one) pairm_body<A, 256, 2, 1>(S.P, S.pwork[lv], xt, ppart, tid);
+        else pairm_body<A, 256, 2, NRM>(S.P, S.pwork[lv], xt, ppart, tid);
+        return;
+      }
+      lv -= S.npb;
+      if (lv < S.u_proj) {
+        proj2_body<A>(S.P, S.proj, S.wtask, S.npart, xt, part, lv * 8 + warp);
+        return;
+      }
+      lv -= S.u_proj;
+      if (lv < S.u_near) {
+        const typename NP::K* kpp;
+        if constexpr (std::is_same<typename NP::K, KernelParams>::value) kpp = &S.kp;
+        else kpp = &S.kf32;
+        const typename NP::pt* xf = reinterpret_cast<const typename NP::pt*>(S.xf);
+        const typename NP::pt* yf = reinterpret_cast<const typename NP::pt*>(S.yf);
+        if (one)
+          near_warp_body<NP, 1>(xf, yf, S.P.leaf_off, S.P.kappa, S.nearw, S.nnearw, *kpp, xt,
+                                S.P.n, S.P.nrhs, yl, lv * 8 + warp);
+        else
+          near_warp_body<NP, 4>(xf, yf, S.P.leaf_off, S.P.kappa, S.nearw, S.nnearw, *kpp, xt,
+                                S.P.n, S.P.nrhs, yl, lv * 8 + warp);
+        return;
+      }
+      lv -= S.u_near;
+      const int64_t j = lv * 8 + warp;  // one pair of at most warp_rows points per warp
+      if (j >= S.npw) return;
+      if (one) pairm_body<A, 32, 2, 1>(S.P, S.pwork[S.npb + j], xt, ppart, lane);
+      else pairm_body<A, 32, 2, NRM>(S.P, S.pwork[S.npb + j], xt, ppart, lane);
+      return;
+    }
+    case 2:
+      tsum2_body<A>(S.P, S.proj, S.red, S.sideq, S.ntsum, part, tt, 0, lv * 8 + warp);
+      return;
+    case 3:
+      exp2_body<A>(S.P, S.exps, tt, yl, lv);
+      __syncthreads();  // its shared list is refilled by the next unit
+      return;
+    default:
+      combine2_body<A>(S.P, yl, ppart, S.leaf_of, S.perm, S.y, lv * 256 + tid);
+  }
+}
+
+template <class A, class NP>
+__global__ void __launch_bounds__(256, kBatchMinBlocks)
+    k_batch(const BatchSet* __restrict__ sets, const int64_t* __restrict__ pre, int nsets,
+            BatchSync* sy, uint32_t polls) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) sy->ts[0] = global_ns();
+  for (int ph = 0; ph < 5; ++ph) {
+    const int64_t* pp = pre + (int64_t)ph * (nsets + 1);
+    const int64_t total = pp[nsets];
+    for (int64_t vb = blockIdx.x; vb < total; vb += gridDim.x) {
+      int lo = 0, hi = nsets - 1;  // the last set whose units start at or before vb
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pp[mid] <= vb) lo = mid;
+        else hi = mid - 1;
+      }
+      batch_unit<A, NP>(sets[lo], ph, vb - pp[lo]);
+    }
+    if (ph == 4) break;
+    if (!batch_barrier(sy, (unsigned)(ph + 1) * gridDim.x, polls)) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) sy->ts[ph + 1] = global_ns();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMax(&sy->ts[5], global_ns());
+    __threadfence();
+    if (atomicAdd(&sy->exit, 1u) == gridDim.x - 1) {  // every block has left: reset
+      sy->bar = 0;
+      sy->exit = 0;
+      __threadfence();
+    }
+  }
+}
+
+// First level of set h that runs as pairs in the persistent form: every
+// level from it on has a pair plan and boxes of at most pair_rows points.
+static int batch_first_pair_level(const hodlr2d* h, int pair_rows) {
+  const V2Plan& V = h->v2;
+  int lp = h->kappa + 1;
+  for (int l = h->kappa; l >= std::max(1, V.ldual); --l) {
+    if (V.plev[l].max_rows > pair_rows) break;
+    lp = l;
+  }
+  return lp;
+}
+
+int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, double* const* y,
+                        const int* nrhs, int mode, BatchPersist* bp) {
+  if (mode != HODLR2D_MODE_F64 && mode != HODLR2D_MODE_F32) return HODLR2D_ERR_ARG;
+  const int pair_rows = std::min(bp->pair_rows, kBatchBlockRows);
+  const int warp_rows = std::min(bp->warp_rows, 64);  // two rows a lane
+  std::vector<BatchSet> sets(count);
+  std::vector<int64_t> pre(5 * (size_t)(count + 1), 0);
+  std::vector<int> lpair(count);
+  int64_t nitems = 0;
+  for (int i = 0; i < count; ++i) {
+    hodlr2d* h = hs[i];
+    V2Plan& V = h->v2;
+    H2D_TRY(plan_v2(h));
+    lpair[i] = batch_first_pair_level(h, pair_rows);
+    if (V.two_levels < lpair[i]) {
+      H2D_CK(cudaStreamSynchronize(h->stream));
+      H2D_TRY(build_two_pass(h, lpair[i]));
+      V.scratch_nrhs = 0;  // the partial sums grew
+    }
+    H2D_TRY(scratch_v2(h, nrhs[i]));
+    for (int l = lpair[i]; l <= h->kappa; ++l) nitems += V.plev[l].nwork;
+  }
+  batch_persist_free(bp);
+  H2D_CK(cudaMalloc(&bp->d_work, sizeof(int2) * std::max<int64_t>(nitems, 1)));
+  int2* wp = reinterpret_cast<int2*>(bp->d_work);
+  cudaStream_t s0 = hs[0]->stream;
+  for (int i = 0; i < count; ++i) {
+    hodlr2d* h = hs[i];
+    V2Plan& V = h->v2;
+    const int lp = lpair[i];
+    BatchSet& S = sets[i];
+    S.P = args_v2(h, nrhs[i], mode);
+    for (int l = 0; l < HODLR2D_MAX_LEVELS; ++l) S.P.lmode[l] = l < lp ? LMODE_TWO : LMODE_PAIR;
+    S.x = x[i];
+    S.y = y[i];
+    S.perm = h->d_perm;
+    S.leaf_of = V.d_leaf_of;
+    S.xt = V.d_xt;
+    S.yl = V.d_yl;
+    S.ppart = V.d_ppart;
+    S.part = V.d_part;
+    S.t = V.d_t;
+    if (mode == HODLR2D_MODE_F64) {
+      S.xf = h->d_x;
+      S.yf = h->d_y;
+    } else {
+      S.xf = V.d_x32;
+      S.yf = V.d_y32;
+    }
+    S.kp = h->kp;
+    S.kf32 = V.kf32;
+    S.nearw = V.d_nearw;
+    S.nnearw = V.nnearw;
+    S.proj = V.d_proj;
+    S.wtask = V.d_wtask;
+    S.npart = V.pre_part[lp];
+    S.red = V.d_red;
+    S.sideq = V.d_sideq;
+    S.ntsum = V.pre_tsum[lp];
+    S.exps = V.d_exp;
+    S.nexp = V.pre_exp[lp];
+    // pair items: the size classes of more than warp_rows points of every
+    // pair level, then those of at most warp_rows points (classes ascend)
+    S.pwork = wp;
+    S.npb = S.npw = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int l = lp; l <= h->kappa; ++l) {
+        const PairLevel& G = V.plev[l];
+        int cw = 0;  // classes [0, cw) go one pair per warp (empty classes pass)
+        while (cw < kPairClasses && (G.off[cw + 1] == G.off[cw] || G.cls_rows[cw] <= warp_rows))
+          ++cw;
+        const int64_t a = pass == 0 ? G.off[cw] : 0;
+        const int64_t b = pass == 0 ? G.nwork : G.off[cw];
+        if (b > a)
+          H2D_CK(cudaMemcpyAsync(wp, G.d_work + a, sizeof(int2) * (b - a),
+                                 cudaMemcpyDeviceToDevice, s0));
+        wp += b - a;
+        (pass == 0 ? S.npb : S.npw) += b - a;
+      }
+    // slots of rank-0 pairs are read by the combine and written by no item
+    H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs[i], s0));
+    S.u_proj = (S.npart + 7) / 8;
+    S.u_near = (V.nnearw + 7) / 8;
+    const int64_t units[5] = {(h->n + 255) / 256, S.npb + S.u_proj + S.u_near + (S.npw + 7) / 8,
+                              (S.ntsum + 7) / 8, S.nexp, (h->n + 255) / 256};
+    for (int ph = 0; ph < 5; ++ph)
+      pre[(size_t)ph * (count + 1) + i + 1] = pre[(size_t)ph * (count + 1) + i] + units[ph];
+  }
+  H2D_CK(cudaMalloc(&bp->d_sets, sizeof(BatchSet) * count));
+  H2D_CK(cudaMalloc(&bp->d_pre, sizeof(int64_t) * pre.size()));
+  H2D_CK(cudaMalloc(&bp->d_sync, sizeof(BatchSync)));
+  H2D_CK(cudaMemcpyAsync(bp->d_sets, sets.data(), sizeof(BatchSet) * count,
+                         cudaMemcpyHostToDevice, s0));
+  H2D_CK(cudaMemcpyAsync(bp->d_pre, pre.data(), sizeof(int64_t) * pre.size(),
+                         cudaMemcpyHostToDevice, s0));
+  H2D_CK(cudaMemsetAsync(bp->d_sync, 0, sizeof(BatchSync), s0));
+  H2D_CK(cudaStreamSynchronize(s0));
+  bp->count = count;
+  bp->mode = mode;
+  int dev = 0, nsm = 1, per = 0;
+  H2D_CK(cudaGetDevice(&dev));
+  H2D_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (mode == HODLR2D_MODE_F64)
+    H2D_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<F64A, NearF64>, 256, 0));
+  else
+    H2D_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<F32A, NearF32>, 256, 0));
+  bp->grid = std::max(1, per) * nsm;
+  return HODLR2D_OK;
+}
+
+// One persistent launch on stream s: the whole product of every set.
+int batch_persist_launch(const BatchPersist& bp, cudaStream_t s) {
+  BatchSync* sy = reinterpret_cast<BatchSync*>(bp.d_sync);
+  void* args[] = {(void*)&bp.d_sets, (void*)&bp.d_pre, (void*)&bp.count, (void*)&sy,
+                  (void*)&bp.polls};
+  const void* fn = bp.mode == HODLR2D_MODE_F64 ? (const void*)k_batch<F64A, NearF64>
+                                               : (const void*)k_batch<F32A, NearF32>;
+  H2D_CK(cudaLaunchCooperativeKernel(fn, dim3((unsigned)bp.grid), dim3(256), args, 0, s));
+  return HODLR2D_OK;
+}
+
+// Reads and clears the status word (synchronises stream s): TIMEOUT if a
+// barrier wait gave up since the previous call.
+int batch_persist_status(const BatchPersist& bp, cudaStream_t s) {
+  if (!bp.d_sync) return HODLR2D_OK;
+  H2D_CK(cudaStreamSynchronize(s));
+  BatchSync* sy = reinterpret_cast<BatchSync*>(bp.d_sync);
+  int st = 0;
+  H2D_CK(cudaMemcpy(&st, &sy->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) H2D_CK(cudaMemset(&sy->status, 0, sizeof(int)));
+  return st ? HODLR2D_ERR_TIMEOUT : HODLR2D_OK;
+}
+
+// Milliseconds of the five phases of the last launch (block 0's view of the
+// barriers; the last phase ends with the last block).
+int batch_persist_phase_ms(const BatchPersist& bp, cudaStream_t s, double* ms) {
+  if (!bp.d_sync) return HODLR2D_ERR_STATE;
+  H2D_CK(cudaStreamSynchronize(s));
+  BatchSync h{};
+  H2D_CK(cudaMemcpy(&h, bp.d_sync, sizeof(BatchSync), cudaMemcpyDeviceToHost));
+  for (int p = 0; p < 5; ++p) ms[p] = (double)(int64_t)(h.ts[p + 1] - h.ts[p]) * 1e-6;
+  return HODLR2D_OK;
+}
+
+void batch_persist_free(BatchPersist* bp) {
+  cudaFree(bp->d_sets);
+  cudaFree(bp->d_pre);
+  cudaFree(bp->d_sync);
+  cudaFree(bp->d_work);
+  bp->d_sets = nullptr;
+  bp->d_pre = nullptr;
+  bp->d_sync = nullptr;
+  bp->d_work = nullptr;
 }
 
 // Reads and clears the device status word of the product kernels (a bounded

@@ -1,7 +1,10 @@
-"""Independent point sets of uneven size multiplied with one CUDA graph
-launch (hodlr2d_batch_*): equal bit for bit to the per-set products, with 1
-to 8 right-hand sides per set, across replays and when x changes in place.
-The leaf-size autotuner returns one of its candidates with its timings."""
+"""Independent point sets of uneven size multiplied as one unit
+(hodlr2d_batch_*): the graph form equal bit for bit to the per-set products,
+the persistent form within rounding of them (its sums run in another
+order), with 1 to 8 right-hand sides per set, across replays, when x changes
+in place and when a handle's working memory moves between calls.  The
+shape autotuner keeps one of its candidates; the leaf-size autotuner returns
+one of its candidates with its timings."""
 import numpy as np
 import pytest
 
@@ -20,8 +23,12 @@ def pkg():
     return p
 
 
+TOL = {"f64": 1e-13, "f32": 1e-5}
+
+
+@pytest.mark.parametrize("form", ["graph", "persistent"])
 @pytest.mark.parametrize("mode", ["f64", "f32"])
-def test_batch_equals_individual_products(pkg, mode):
+def test_batch_equals_individual_products(pkg, mode, form):
     sets = inputs.point_sets(12, seed=4, nmin=300, nmax=6000)
     rng = np.random.default_rng(1)
     mats, xs, ys = [], [], []
@@ -33,16 +40,45 @@ def test_batch_equals_individual_products(pkg, mode):
         nr = int(rng.integers(1, 9))
         xs.append(torch.from_numpy(rng.standard_normal((nr, len(p)))).cuda())
         ys.append(torch.zeros_like(xs[-1]))
-    b = pkg.Batch(mats)
-    for rep in range(3):
-        if rep == 2:  # new data in the same buffers: the recorded graph sees it
+    b = pkg.Batch(mats, form=form)
+    for rep in range(4):
+        if rep == 2:  # new data in the same buffers: the recorded launch sees it
             for x in xs:
                 x.mul_(-0.5)
+        if rep == 3:  # a handle's working memory moves: the batch is set up again
+            big = torch.zeros((9, mats[0].n), dtype=torch.float64, device="cuda")
+            mats[0].matvec(big.t(), mode=mode)
         b.matvec(xs, ys, mode=mode)
-        torch.cuda.synchronize()
+        b.check()
+        assert b.last_form == form
         for g, x, y in zip(mats, xs, ys):
             ref = g.matvec(x.t().contiguous(), mode=mode).t()
-            assert torch.equal(y, ref)
+            if form == "graph":
+                assert torch.equal(y, ref)
+            else:
+                err = float(torch.linalg.norm(y - ref) / torch.linalg.norm(ref))
+                assert err <= TOL[mode], err
+    b.close()
+
+
+def test_batch_shape_autotuner(pkg):
+    sets = inputs.point_sets(6, seed=6, nmin=2000, nmax=20000)
+    mats = [pkg.HODLR2D(p, pkg.kernel("imq", 1.0 / np.sqrt(len(p))), 32, 1e-8) for p in sets]
+    for g in mats:
+        g.prepare("f32")
+    rng = np.random.default_rng(2)
+    xs = [torch.from_numpy(rng.standard_normal((2, g.n))).cuda() for g in mats]
+    ys = [torch.empty_like(x) for x in xs]
+    b = pkg.Batch(mats, form="persistent")
+    (pr, wr), ms = b.autotune(xs, ys, mode="f32", reps=2)
+    assert pr in (0, 64, 128, 256, 384, 512) and wr in (0, 48, 64) and wr <= pr and ms > 0
+    b.matvec(xs, ys, mode="f32")
+    b.check()
+    assert len(b.phase_ms()) == 5 and all(t >= 0 for t in b.phase_ms())
+    for g, x, y in zip(mats, xs, ys):
+        ref = g.matvec(x.t().contiguous(), mode="f32").t()
+        assert float(torch.linalg.norm(y - ref) / torch.linalg.norm(ref)) <= TOL["f32"]
+    b.close()
 
 
 def test_autotune_leaf(pkg):

@@ -16,8 +16,9 @@ with identical U and V (Alg. 2) and differ only by rounding order:
     kernel) against the oracle's 32-column product;
   - N = 2^20 (marked slow): the benchmark's own workload, binary64 and
     float-float, one right-hand side;
-  - a batch of independent point sets multiplied with one graph launch,
-    each set against its own oracle.
+  - a batch of independent point sets multiplied with one graph launch or
+    one persistent kernel, each set against its own oracle, and the
+    persistent kernel's bounded barrier wait giving up on request.
 Bounds: 1e-12 (relative 2-norm) for binary64 and float-float, 5e-6 for
 binary32 factors and sums, 2e-2 for bfloat16 factors (the factors' own
 rounding, 2^-9 relative per value, sets it).
@@ -123,10 +124,11 @@ def test_p1_bench_workload_2e20(h2d, oracle):
         assert rel(y, y_o) <= BOUND[mode], mode
 
 
-def test_batch_against_oracle(h2d, oracle):
-    """hodlr2d_batch_matvec (one graph launch over independent handles of
-    uneven size, 1-4 right-hand sides each) against each set's own oracle
-    product on the same factors, in binary64 and binary32."""
+@pytest.fixture(scope="module")
+def batch_sets(h2d, oracle):
+    """Five independent point sets of 1500-6000 points (leaves 32-64), IMQ,
+    GPU handles on the oracle's factors, 1-4 right-hand sides each, and each
+    set's oracle product."""
     sets = inputs.point_sets(5, seed=3, nmin=1500, nmax=6000)
     rng = np.random.default_rng(4)
     mats, orcs, xs = [], [], []
@@ -142,15 +144,59 @@ def test_batch_against_oracle(h2d, oracle):
         mats.append(g)
         orcs.append(o)
     want = [o.matvec(np.ascontiguousarray(x.T)) for o, x in zip(orcs, xs)]
-    b = h2d.Batch(mats, stream=torch.cuda.current_stream())
+    return mats, xs, want
+
+
+@pytest.mark.parametrize("form,shapes", [("graph", None), ("persistent", None),
+                                         ("persistent", (0, 0)), ("persistent", (128, 0)),
+                                         ("persistent", (512, 48))])
+def test_batch_against_oracle(h2d, batch_sets, form, shapes):
+    """hodlr2d_batch_matvec over independent handles of uneven size against
+    each set's own oracle product on the same factors, in binary64 and
+    binary32: one graph launch (recorded on the first call, replayed on the
+    second), or one persistent cooperative kernel (five phases behind
+    bounded grid barriers) with its default shapes, with every level in two
+    passes (0, 0), with pairs up to 128 points one per 256-thread unit
+    (128, 0), and with pairs up to 512 points, those of <= 48 one per warp."""
+    mats, xs, want = batch_sets
+    b = h2d.Batch(mats, stream=torch.cuda.current_stream(), form=form)
+    if shapes is not None:
+        b.set_shapes(*shapes)
     xd = [torch.from_numpy(x).cuda() for x in xs]
     for mode in ("f64", "f32"):
         ys = [torch.empty_like(x) for x in xd]
-        for _ in range(2):  # the first call records the graph, the second replays it
+        for _ in range(2):
             b.matvec(xd, ys, mode=mode)
-            torch.cuda.synchronize()
+            b.check()
+            assert b.last_form == form
             for y, w in zip(ys, want):
                 assert rel(y.cpu().numpy().T, w) <= BOUND[mode], mode
+    b.close()
+
+
+def test_batch_persistent_wait_gives_up(h2d, batch_sets):
+    """The persistent form's grid-barrier waits are bounded: with a wait
+    limit of 0 polls every block gives up at the first barrier, the launch
+    ends without writing y, hodlr2d_batch_check reports HODLR2D_ERR_TIMEOUT,
+    and the context stays usable (the next product with the default limit is
+    right)."""
+    from paper_2204_05536_gb300 import _lib
+    mats, xs, want = batch_sets
+    b = h2d.Batch(mats, stream=torch.cuda.current_stream(), form="persistent")
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    ys = [torch.full_like(x, 123.0) for x in xd]
+    b.set_wait_limit(0)
+    b.matvec(xd, ys, mode="f64")
+    with pytest.raises(_lib.HodlrError) as ei:
+        b.check()
+    assert ei.value.code == _lib.ERR_TIMEOUT
+    assert all(bool((y == 123.0).all()) for y in ys)  # the combine never ran
+    b.check()  # the record was cleared
+    b.set_wait_limit(1 << 22)
+    b.matvec(xd, ys, mode="f64")
+    b.check()
+    for y, w in zip(ys, want):
+        assert rel(y.cpu().numpy().T, w) <= BOUND["f64"]
     b.close()
 
 
