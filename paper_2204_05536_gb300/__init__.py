@@ -400,6 +400,23 @@ class Batch:
                                                C.byref(ms)), "hodlr2d_batch_autotune")
         return self.shapes(), ms.value
 
+    def set_blocks_per_sm(self, blocks: int):
+        """Resident blocks per SM of the persistent kernel (2, 3 or 4)."""
+        check(self._lib.hodlr2d_batch_set_blocks_per_sm(self._h, int(blocks)),
+              "hodlr2d_batch_set_blocks_per_sm")
+
+    def tune_table(self):
+        """[(pair_rows, warp_rows, blocks per SM, ms per product)] of the last
+        autotune."""
+        cnt = C.c_int(0)
+        check(self._lib.hodlr2d_batch_tune_table(self._h, C.byref(cnt), None, None, None, None),
+              "hodlr2d_batch_tune_table")
+        n = cnt.value
+        pr, wr, mb, ms = (C.c_int * n)(), (C.c_int * n)(), (C.c_int * n)(), (C.c_double * n)()
+        check(self._lib.hodlr2d_batch_tune_table(self._h, C.byref(cnt), pr, wr, mb, ms),
+              "hodlr2d_batch_tune_table")
+        return [(pr[i], wr[i], mb[i], ms[i]) for i in range(n)]
+
     def phase_ms(self):
         """Milliseconds of the five phases of the last persistent product."""
         out = (C.c_double * 5)()

@@ -4,6 +4,7 @@
 // near/far streams nested inside) and replayed with one graph launch per
 // call; or one persistent cooperative kernel over all sets (product.cu),
 // itself recorded into a graph.
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -43,6 +44,10 @@ struct hodlr2d_batch {
   std::vector<uint64_t> pgen;
   cudaGraph_t pgraph = nullptr;
   cudaGraphExec_t pexec = nullptr;
+  // the last autotuning: (pair_rows, warp_rows, blocks per SM, ms per
+  // product) per candidate
+  std::vector<int> tune_pair, tune_warp, tune_minb;
+  std::vector<double> tune_ms;
 };
 
 // True when every handle's buffers are those a recording was made for.
@@ -204,10 +209,37 @@ int hodlr2d_batch_set_shapes(hodlr2d_batch_t b, int pair_rows, int warp_rows) {
   return HODLR2D_OK;
 }
 
+int hodlr2d_batch_set_blocks_per_sm(hodlr2d_batch_t b, int blocks) {
+  if (!b || blocks < 2 || blocks > 4) return HODLR2D_ERR_ARG;
+  if (b->bp.minb != blocks) b->px.clear();
+  b->bp.minb = blocks;
+  return HODLR2D_OK;
+}
+
 int hodlr2d_batch_get_shapes(hodlr2d_batch_t b, int* pair_rows, int* warp_rows) {
   if (!b || !pair_rows || !warp_rows) return HODLR2D_ERR_ARG;
   *pair_rows = b->bp.pair_rows;
   *warp_rows = b->bp.warp_rows;
+  return HODLR2D_OK;
+}
+
+// Times reps products with the current settings (after one untimed product
+// that also sets up); ms per product.
+static int batch_time(hodlr2d_batch* b, const double* const* x, double* const* y,
+                      const int* nrhs, int mode, int reps, cudaEvent_t e0, cudaEvent_t e1,
+                      float* ms) {
+  H2D_TRY(hodlr2d_batch_matvec(b, x, y, nrhs, mode));
+  H2D_TRY(hodlr2d_batch_check(b));
+  H2D_CK(cudaEventRecord(e0, b->stream));
+  for (int r = 0; r < reps; ++r) H2D_TRY(hodlr2d_batch_matvec(b, x, y, nrhs, mode));
+  H2D_CK(cudaEventRecord(e1, b->stream));
+  H2D_TRY(hodlr2d_batch_check(b));
+  H2D_CK(cudaEventElapsedTime(ms, e0, e1));
+  *ms /= reps;
+  b->tune_pair.push_back(b->bp.pair_rows);
+  b->tune_warp.push_back(b->bp.warp_rows);
+  b->tune_minb.push_back(b->bp.minb);
+  b->tune_ms.push_back(*ms);
   return HODLR2D_OK;
 }
 
@@ -223,33 +255,56 @@ int hodlr2d_batch_autotune(hodlr2d_batch_t b, const double* const* x, double* co
   int rc = HODLR2D_OK;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     rc = HODLR2D_ERR_CUDA;
-  float best = -1.f;
-  int bp_rows = b->bp.pair_rows, bw_rows = b->bp.warp_rows;
+  b->tune_pair.clear();
+  b->tune_warp.clear();
+  b->tune_minb.clear();
+  b->tune_ms.clear();
+  float best = -1.f, ms = 0.f;
+  int bpr = b->bp.pair_rows, bwr = b->bp.warp_rows, bmb = b->bp.minb;
+  // shapes at the current occupancy, then the occupancy at the best shapes
   for (int pr : kPair)
     for (int wr : kWarp) {
       if (rc || wr > pr) continue;
       rc = hodlr2d_batch_set_shapes(b, pr, wr);
-      if (!rc) rc = hodlr2d_batch_matvec(b, x, y, nrhs, mode);  // set-up and one warm launch
-      if (!rc) rc = hodlr2d_batch_check(b);
-      if (rc) break;
-      if (cudaEventRecord(e0, b->stream) != cudaSuccess) rc = HODLR2D_ERR_CUDA;
-      for (int r = 0; r < reps && !rc; ++r) rc = hodlr2d_batch_matvec(b, x, y, nrhs, mode);
-      if (!rc && cudaEventRecord(e1, b->stream) != cudaSuccess) rc = HODLR2D_ERR_CUDA;
-      if (!rc) rc = hodlr2d_batch_check(b);
-      float ms = 0.f;
-      if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = HODLR2D_ERR_CUDA;
+      if (!rc) rc = batch_time(b, x, y, nrhs, mode, reps, e0, e1, &ms);
       if (!rc && (best < 0.f || ms < best)) {
         best = ms;
-        bp_rows = pr;
-        bw_rows = wr;
+        bpr = pr;
+        bwr = wr;
       }
     }
+  if (!rc) rc = hodlr2d_batch_set_shapes(b, bpr, bwr);
+  const int mb0 = bmb;
+  for (int mb = 2; mb <= 4 && !rc; ++mb) {
+    if (mb == mb0) continue;
+    rc = hodlr2d_batch_set_blocks_per_sm(b, mb);
+    if (!rc) rc = batch_time(b, x, y, nrhs, mode, reps, e0, e1, &ms);
+    if (!rc && ms < best) {
+      best = ms;
+      bmb = mb;
+    }
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   b->form = form;
   if (rc) return rc;
-  if (best_ms) *best_ms = best / reps;
-  return hodlr2d_batch_set_shapes(b, bp_rows, bw_rows);
+  if (best_ms) *best_ms = best;
+  return hodlr2d_batch_set_blocks_per_sm(b, bmb);
+}
+
+int hodlr2d_batch_tune_table(hodlr2d_batch_t b, int* count, int* pair_rows, int* warp_rows,
+                             int* blocks, double* ms) {
+  if (!b || !count) return HODLR2D_ERR_ARG;
+  const int n = (int)b->tune_ms.size();
+  if (pair_rows && warp_rows && blocks && ms)
+    for (int i = 0; i < std::min(n, *count); ++i) {
+      pair_rows[i] = b->tune_pair[i];
+      warp_rows[i] = b->tune_warp[i];
+      blocks[i] = b->tune_minb[i];
+      ms[i] = b->tune_ms[i];
+    }
+  *count = n;
+  return HODLR2D_OK;
 }
 
 int hodlr2d_batch_matvec(hodlr2d_batch_t b, const double* const* x, double* const* y,

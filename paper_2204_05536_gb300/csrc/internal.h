@@ -93,6 +93,7 @@ struct PairLevel {
   int max_rows = 0;                    // largest box of the level
   int64_t off[kPairClasses + 1] = {};  // class c: work [off[c], off[c + 1])
   int cls_rows[kPairClasses] = {};     // largest box of class c
+  std::vector<int2> h_work;            // host copy of the work list
 };
 
 struct V2Plan {
@@ -163,6 +164,7 @@ struct BatchPersist {
   // run as pairs (one pair per 256-thread unit, or per warp for pairs of at
   // most warp_rows points); coarser levels run in two passes
   int pair_rows = 384, warp_rows = 64;
+  int minb = 3;  // resident blocks per SM (2, 3 or 4: 128, 80 or 64 registers a thread)
 };
 int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, double* const* y,
                         const int* nrhs, int mode, BatchPersist* bp);

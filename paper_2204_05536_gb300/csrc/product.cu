@@ -770,20 +770,30 @@ __global__ void __launch_bounds__(T)
 // of X and of Y) for the pass's NR right-hand sides in registers; each column
 // of U and V is loaded once per pass and used for all of them.  The 2 NR
 // sums of a column reduce like k_pairg's.
-// (the T threads tid = 0 .. T - 1 that call it take pair wk together; with
-// T = 32 they are one warp and the body never synchronises the block)
-template <class A, int T, int RM, int NR>
+// (the T threads tid = 0 .. T - 1 of group gid, whole warps, take pair wk
+// together.  With T = 32 they are one warp and never synchronise; with NG = 1
+// they are the whole block and synchronise it; with NG > 1 groups of one
+// block they synchronise on the named barrier 1 + gid, T threads.)
+template <int T, int NG>
+__device__ __forceinline__ void group_sync(int gid) {
+  if constexpr (NG == 1) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(1 + gid), "r"(T) : "memory");
+}
+template <class A, int T, int RM, int NR, int NG = 1>
 __device__ __forceinline__ void pairm_body(const ArgsV2& P, const int2 wk,
                                            const typename A::val* __restrict__ xt,
-                                           typename A::val* __restrict__ ppart, const int tid) {
+                                           typename A::val* __restrict__ ppart, const int tid,
+                                           const int gid = 0) {
   using V = typename A::val;
   using F = typename A::fac;
   using Acc = typename A::acc;
   constexpr int NW = T / 32;
   constexpr int NV = 2 * NR;
   constexpr int SH = 5 - ilog2c(NV);
-  __shared__ V red[2][NW > 1 ? NW : 1][NV];
-  __shared__ V tot[2][NV];
+  __shared__ V red_all[NG][2][NW > 1 ? NW : 1][NV];
+  __shared__ V tot_all[NG][2][NV];
+  auto& red = red_all[gid];
+  auto& tot = tot_all[gid];
   const int lane = tid & 31, warp = tid >> 5;
   const LevelV2& L = P.lev[wk.x];
   const PairMeta PM = L.meta[wk.y];
@@ -837,14 +847,14 @@ __device__ __forceinline__ void pairm_body(const ArgsV2& P, const int2 wk,
         for (int c = 0; c < NV; ++c) t[c] = shfl_idx(mine, c << SH);
       } else {
         if ((lane & ((1 << SH) - 1)) == 0) red[par][warp][lane >> SH] = mine;
-        __syncthreads();
+        group_sync<T, NG>(gid);
         if (tid < NV) {
           V acc = red[par][0][tid];
 #pragma unroll
           for (int w = 1; w < NW; ++w) acc = A::add(acc, red[par][w][tid]);
           tot[par][tid] = acc;
         }
-        __syncthreads();
+        group_sync<T, NG>(gid);
 #pragma unroll
         for (int c = 0; c < NV; ++c) t[c] = tot[par][c];
         par ^= 1;
@@ -2723,6 +2733,7 @@ int plan_v2(hodlr2d* h) {
     }
     G.off[kPairClasses] = (int64_t)wl.size();
     G.nwork = (int64_t)wl.size();
+    G.h_work = wl;
     H2D_CK(cudaMalloc(&G.d_work, sizeof(int2) * std::max<int64_t>(G.nwork, 1)));
     if (G.nwork)
       H2D_CK(cudaMemcpy(G.d_work, wl.data(), sizeof(int2) * G.nwork, cudaMemcpyHostToDevice));
@@ -3092,9 +3103,10 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
 // into five phases, each a flat list of units over all sets (a unit is the
 // work of one 256-thread block):
 //   0 gather x into tree order;
-//   1 pairs of more than warp_rows points (one pair per unit), the two-pass
-//     projections, the near field, pairs of at most warp_rows points (one
-//     pair per warp) -- independent work, longest units first;
+//   1 pairs (by their larger box: up to 512 points one pair per unit, up to
+//     256 two per unit of 128 threads each, up to 128 four per unit of 64
+//     threads each, up to warp_rows one per warp), the two-pass projections
+//     and the near field -- independent work, longest units first;
 //   2 chunk sums; 3 expansions; 4 combine.
 // Blocks walk a phase's units (grid-stride; a unit finds its set by binary
 // search over the phase's prefix counts), then meet at a grid barrier.  All
@@ -3103,7 +3115,6 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
 // word and leaves, so the launch always ends.  The last block out resets the
 // barrier counters for the next launch, so one launch is the whole product.
 // ---------------------------------------------------------------------------
-constexpr int kBatchMinBlocks = 3;  // 24 warps per SM (80 registers a thread)
 constexpr int kBatchBlockRows = 512;  // largest box of a one-pair-per-unit item (2 rows a thread)
 
 struct BatchSet {
@@ -3131,8 +3142,10 @@ struct BatchSet {
   int64_t ntsum;              // chunk-sum warps
   const ExpTask* exps;
   int64_t nexp;
-  const int2* pwork;          // pair items (level, pair): npb unit items, then npw warp items
-  int64_t npb, npw;
+  // pair items (level, pair) by group size: one per unit (256 threads), per
+  // 128, per 64 and per 32 threads, in that order in pwork
+  const int2* pwork;
+  int64_t np[4];
   int64_t u_proj, u_near;     // phase-1 units of the projections and of the near field
 };
 
@@ -3189,12 +3202,34 @@ __device__ __forceinline__ void batch_unit(const BatchSet& S, int ph, int64_t lv
       gather2_body<A>(S.x, S.perm, S.P.n, S.P.nrhs, xt, lv * 256 + tid);
       return;
     case 1: {
-      if (lv < S.npb) {  // one pair of more than warp_rows points
-        if (one) pairm_body<A, 256, 2, 1>(S.P, S.pwork[lv], xt, ppart, tid);
-        else pairm_body<A, 256, 2, NRM>(S.P, S.pwork[lv], xt, ppart, tid);
+      const int2* pw = S.pwork;
+      if (lv < S.np[0]) {  // one pair of at most 512 points
+        if (one) pairm_body<A, 256, 2, 1>(S.P, pw[lv], xt, ppart, tid);
+        else pairm_body<A, 256, 2, NRM>(S.P, pw[lv], xt, ppart, tid);
         return;
       }
-      lv -= S.npb;
+      lv -= S.np[0];
+      pw += S.np[0];
+      if (lv < (S.np[1] + 1) / 2) {  // two pairs of at most 256 points
+        const int g = tid >> 7;
+        const int64_t j = lv * 2 + g;
+        if (j >= S.np[1]) return;
+        if (one) pairm_body<A, 128, 2, 1, 2>(S.P, pw[j], xt, ppart, tid & 127, g);
+        else pairm_body<A, 128, 2, NRM, 2>(S.P, pw[j], xt, ppart, tid & 127, g);
+        return;
+      }
+      lv -= (S.np[1] + 1) / 2;
+      pw += S.np[1];
+      if (lv < (S.np[2] + 3) / 4) {  // four pairs of at most 128 points
+        const int g = tid >> 6;
+        const int64_t j = lv * 4 + g;
+        if (j >= S.np[2]) return;
+        if (one) pairm_body<A, 64, 2, 1, 4>(S.P, pw[j], xt, ppart, tid & 63, g);
+        else pairm_body<A, 64, 2, NRM, 4>(S.P, pw[j], xt, ppart, tid & 63, g);
+        return;
+      }
+      lv -= (S.np[2] + 3) / 4;
+      pw += S.np[2];
       if (lv < S.u_proj) {
         proj2_body<A>(S.P, S.proj, S.wtask, S.npart, xt, part, lv * 8 + warp);
         return;
@@ -3216,9 +3251,9 @@ __device__ __forceinline__ void batch_unit(const BatchSet& S, int ph, int64_t lv
       }
       lv -= S.u_near;
       const int64_t j = lv * 8 + warp;  // one pair of at most warp_rows points per warp
-      if (j >= S.npw) return;
-      if (one) pairm_body<A, 32, 2, 1>(S.P, S.pwork[S.npb + j], xt, ppart, lane);
-      else pairm_body<A, 32, 2, NRM>(S.P, S.pwork[S.npb + j], xt, ppart, lane);
+      if (j >= S.np[3]) return;
+      if (one) pairm_body<A, 32, 2, 1>(S.P, pw[j], xt, ppart, lane);
+      else pairm_body<A, 32, 2, NRM>(S.P, pw[j], xt, ppart, lane);
       return;
     }
     case 2:
@@ -3233,8 +3268,10 @@ __device__ __forceinline__ void batch_unit(const BatchSet& S, int ph, int64_t lv
   }
 }
 
-template <class A, class NP>
-__global__ void __launch_bounds__(256, kBatchMinBlocks)
+// MINB: resident blocks per SM the compiler is asked for (registers a thread
+// 65536 / (256 MINB)); the batch picks one of 2, 3, 4
+template <class A, class NP, int MINB>
+__global__ void __launch_bounds__(256, MINB)
     k_batch(const BatchSet* __restrict__ sets, const int64_t* __restrict__ pre, int nsets,
             BatchSync* sy, uint32_t polls) {
   if (blockIdx.x == 0 && threadIdx.x == 0) sy->ts[0] = global_ns();
@@ -3266,6 +3303,16 @@ __global__ void __launch_bounds__(256, kBatchMinBlocks)
   }
 }
 
+// The instantiation of the batch's mode and registers a thread.
+static const void* batch_kernel(const BatchPersist& bp) {
+  const bool f64 = bp.mode == HODLR2D_MODE_F64;
+  switch (bp.minb) {
+    case 2: return f64 ? (const void*)k_batch<F64A, NearF64, 2> : (const void*)k_batch<F32A, NearF32, 2>;
+    case 4: return f64 ? (const void*)k_batch<F64A, NearF64, 4> : (const void*)k_batch<F32A, NearF32, 4>;
+    default: return f64 ? (const void*)k_batch<F64A, NearF64, 3> : (const void*)k_batch<F32A, NearF32, 3>;
+  }
+}
+
 // First level of set h that runs as pairs in the persistent form: every
 // level from it on has a pair plan and boxes of at most pair_rows points.
 static int batch_first_pair_level(const hodlr2d* h, int pair_rows) {
@@ -3286,7 +3333,6 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
   std::vector<BatchSet> sets(count);
   std::vector<int64_t> pre(5 * (size_t)(count + 1), 0);
   std::vector<int> lpair(count);
-  int64_t nitems = 0;
   for (int i = 0; i < count; ++i) {
     hodlr2d* h = hs[i];
     V2Plan& V = h->v2;
@@ -3298,11 +3344,12 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
       V.scratch_nrhs = 0;  // the partial sums grew
     }
     H2D_TRY(scratch_v2(h, nrhs[i]));
-    for (int l = lpair[i]; l <= h->kappa; ++l) nitems += V.plev[l].nwork;
   }
   batch_persist_free(bp);
-  H2D_CK(cudaMalloc(&bp->d_work, sizeof(int2) * std::max<int64_t>(nitems, 1)));
-  int2* wp = reinterpret_cast<int2*>(bp->d_work);
+  // pair items of every set, grouped by the threads that take one pair:
+  // 256 (boxes of at most 512 points), 128 (256), 64 (128), 32 (warp_rows)
+  std::vector<int2> items;
+  std::vector<int64_t> item0(count);
   cudaStream_t s0 = hs[0]->stream;
   for (int i = 0; i < count; ++i) {
     hodlr2d* h = hs[i];
@@ -3339,33 +3386,36 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
     S.ntsum = V.pre_tsum[lp];
     S.exps = V.d_exp;
     S.nexp = V.pre_exp[lp];
-    // pair items: the size classes of more than warp_rows points of every
-    // pair level, then those of at most warp_rows points (classes ascend)
-    S.pwork = wp;
-    S.npb = S.npw = 0;
-    for (int pass = 0; pass < 2; ++pass)
+    item0[i] = (int64_t)items.size();
+    for (int kind = 0; kind < 4; ++kind) {
+      S.np[kind] = 0;
       for (int l = lp; l <= h->kappa; ++l) {
         const PairLevel& G = V.plev[l];
-        int cw = 0;  // classes [0, cw) go one pair per warp (empty classes pass)
-        while (cw < kPairClasses && (G.off[cw + 1] == G.off[cw] || G.cls_rows[cw] <= warp_rows))
-          ++cw;
-        const int64_t a = pass == 0 ? G.off[cw] : 0;
-        const int64_t b = pass == 0 ? G.nwork : G.off[cw];
-        if (b > a)
-          H2D_CK(cudaMemcpyAsync(wp, G.d_work + a, sizeof(int2) * (b - a),
-                                 cudaMemcpyDeviceToDevice, s0));
-        wp += b - a;
-        (pass == 0 ? S.npb : S.npw) += b - a;
+        for (int c = 0; c < kPairClasses; ++c) {
+          const int r = G.cls_rows[c];
+          const int k = r <= warp_rows ? 3 : r <= 128 ? 2 : r <= 256 ? 1 : 0;
+          if (k != kind) continue;
+          items.insert(items.end(), G.h_work.begin() + G.off[c], G.h_work.begin() + G.off[c + 1]);
+          S.np[kind] += G.off[c + 1] - G.off[c];
+        }
       }
+    }
     // slots of rank-0 pairs are read by the combine and written by no item
     H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs[i], s0));
     S.u_proj = (S.npart + 7) / 8;
     S.u_near = (V.nnearw + 7) / 8;
-    const int64_t units[5] = {(h->n + 255) / 256, S.npb + S.u_proj + S.u_near + (S.npw + 7) / 8,
+    const int64_t units[5] = {(h->n + 255) / 256,
+                              S.np[0] + (S.np[1] + 1) / 2 + (S.np[2] + 3) / 4 + S.u_proj +
+                                  S.u_near + (S.np[3] + 7) / 8,
                               (S.ntsum + 7) / 8, S.nexp, (h->n + 255) / 256};
     for (int ph = 0; ph < 5; ++ph)
       pre[(size_t)ph * (count + 1) + i + 1] = pre[(size_t)ph * (count + 1) + i] + units[ph];
   }
+  H2D_CK(cudaMalloc(&bp->d_work, sizeof(int2) * std::max<size_t>(items.size(), 1)));
+  for (int i = 0; i < count; ++i) sets[i].pwork = reinterpret_cast<int2*>(bp->d_work) + item0[i];
+  if (!items.empty())
+    H2D_CK(cudaMemcpyAsync(bp->d_work, items.data(), sizeof(int2) * items.size(),
+                           cudaMemcpyHostToDevice, s0));
   H2D_CK(cudaMalloc(&bp->d_sets, sizeof(BatchSet) * count));
   H2D_CK(cudaMalloc(&bp->d_pre, sizeof(int64_t) * pre.size()));
   H2D_CK(cudaMalloc(&bp->d_sync, sizeof(BatchSync)));
@@ -3380,10 +3430,7 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
   int dev = 0, nsm = 1, per = 0;
   H2D_CK(cudaGetDevice(&dev));
   H2D_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  if (mode == HODLR2D_MODE_F64)
-    H2D_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<F64A, NearF64>, 256, 0));
-  else
-    H2D_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<F32A, NearF32>, 256, 0));
+  H2D_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel(*bp), 256, 0));
   bp->grid = std::max(1, per) * nsm;
   return HODLR2D_OK;
 }
@@ -3393,9 +3440,8 @@ int batch_persist_launch(const BatchPersist& bp, cudaStream_t s) {
   BatchSync* sy = reinterpret_cast<BatchSync*>(bp.d_sync);
   void* args[] = {(void*)&bp.d_sets, (void*)&bp.d_pre, (void*)&bp.count, (void*)&sy,
                   (void*)&bp.polls};
-  const void* fn = bp.mode == HODLR2D_MODE_F64 ? (const void*)k_batch<F64A, NearF64>
-                                               : (const void*)k_batch<F32A, NearF32>;
-  H2D_CK(cudaLaunchCooperativeKernel(fn, dim3((unsigned)bp.grid), dim3(256), args, 0, s));
+  H2D_CK(cudaLaunchCooperativeKernel(batch_kernel(bp), dim3((unsigned)bp.grid), dim3(256), args,
+                                     0, s));
   return HODLR2D_OK;
 }
 
