@@ -773,13 +773,16 @@ __global__ void __launch_bounds__(T)
 // (the T threads tid = 0 .. T - 1 of group gid, whole warps, take pair wk
 // together.  With T = 32 they are one warp and never synchronise; with NG = 1
 // they are the whole block and synchronise it; with NG > 1 groups of one
-// block they synchronise on the named barrier 1 + gid, T threads.)
-template <int T, int NG>
+// block they synchronise on the named barrier B0 + gid, T threads.  A block
+// whose groups may drift into the next unit before the others finish must
+// give each group size its own barrier ids, so that one id is always used by
+// the same warps with the same count.)
+template <int T, int NG, int B0>
 __device__ __forceinline__ void group_sync(int gid) {
   if constexpr (NG == 1) __syncthreads();
-  else asm volatile("bar.sync %0, %1;" ::"r"(1 + gid), "r"(T) : "memory");
+  else asm volatile("bar.sync %0, %1;" ::"r"(B0 + gid), "r"(T) : "memory");
 }
-template <class A, int T, int RM, int NR, int NG = 1>
+template <class A, int T, int RM, int NR, int NG = 1, int B0 = 1>
 __device__ __forceinline__ void pairm_body(const ArgsV2& P, const int2 wk,
                                            const typename A::val* __restrict__ xt,
                                            typename A::val* __restrict__ ppart, const int tid,
@@ -847,14 +850,14 @@ __device__ __forceinline__ void pairm_body(const ArgsV2& P, const int2 wk,
         for (int c = 0; c < NV; ++c) t[c] = shfl_idx(mine, c << SH);
       } else {
         if ((lane & ((1 << SH) - 1)) == 0) red[par][warp][lane >> SH] = mine;
-        group_sync<T, NG>(gid);
+        group_sync<T, NG, B0>(gid);
         if (tid < NV) {
           V acc = red[par][0][tid];
 #pragma unroll
           for (int w = 1; w < NW; ++w) acc = A::add(acc, red[par][w][tid]);
           tot[par][tid] = acc;
         }
-        group_sync<T, NG>(gid);
+        group_sync<T, NG, B0>(gid);
 #pragma unroll
         for (int c = 0; c < NV; ++c) t[c] = tot[par][c];
         par ^= 1;
@@ -3106,7 +3109,10 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
 //   1 pairs (by their larger box: up to 512 points one pair per unit, up to
 //     256 two per unit of 128 threads each, up to 128 four per unit of 64
 //     threads each, up to warp_rows one per warp), the two-pass projections
-//     and the near field -- independent work, longest units first;
+//     and the near field -- independent work, longest units first.  The
+//     groups of one unit do not wait for each other at its end: the groups
+//     of 128 threads synchronise on named barriers 1-2, those of 64 on 3-6,
+//     each id always used by the same warps;
 //   2 chunk sums; 3 expansions; 4 combine.
 // Blocks walk a phase's units (grid-stride; a unit finds its set by binary
 // search over the phase's prefix counts), then meet at a grid barrier.  All
@@ -3214,8 +3220,8 @@ __device__ __forceinline__ void batch_unit(const BatchSet& S, int ph, int64_t lv
         const int g = tid >> 7;
         const int64_t j = lv * 2 + g;
         if (j >= S.np[1]) return;
-        if (one) pairm_body<A, 128, 2, 1, 2>(S.P, pw[j], xt, ppart, tid & 127, g);
-        else pairm_body<A, 128, 2, NRM, 2>(S.P, pw[j], xt, ppart, tid & 127, g);
+        if (one) pairm_body<A, 128, 2, 1, 2, 1>(S.P, pw[j], xt, ppart, tid & 127, g);
+        else pairm_body<A, 128, 2, NRM, 2, 1>(S.P, pw[j], xt, ppart, tid & 127, g);
         return;
       }
       lv -= (S.np[1] + 1) / 2;
@@ -3224,8 +3230,8 @@ __device__ __forceinline__ void batch_unit(const BatchSet& S, int ph, int64_t lv
         const int g = tid >> 6;
         const int64_t j = lv * 4 + g;
         if (j >= S.np[2]) return;
-        if (one) pairm_body<A, 64, 2, 1, 4>(S.P, pw[j], xt, ppart, tid & 63, g);
-        else pairm_body<A, 64, 2, NRM, 4>(S.P, pw[j], xt, ppart, tid & 63, g);
+        if (one) pairm_body<A, 64, 2, 1, 4, 3>(S.P, pw[j], xt, ppart, tid & 63, g);
+        else pairm_body<A, 64, 2, NRM, 4, 3>(S.P, pw[j], xt, ppart, tid & 63, g);
         return;
       }
       lv -= (S.np[2] + 3) / 4;
