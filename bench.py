@@ -377,6 +377,7 @@ def extra_batch(pkg, inputs, stream, count=256):
     t0 = time.perf_counter()
     shapes, _ = b.autotune(xs, yp, mode="f32", reps=3)
     t_ptune = time.perf_counter() - t0
+    table = {"%d/%d/%d" % (a, c, m): round(t, 3) for a, c, m, t in b.tune_table()}
     b.matvec(xs, yp, mode="f32")
     b.check()
     e0.record(stream)
@@ -414,8 +415,7 @@ def extra_batch(pkg, inputs, stream, count=256):
             "products_per_s_persistent": round(nprod / (t_pers * 1e-3), 1),
             "persistent_shapes": {"pair_rows": shapes[0], "warp_rows": shapes[1]},
             "persistent_tune_s": round(t_ptune, 2),
-            "persistent_tune_table_ms": {"%d/%d/%d" % (a, c, m): round(t, 3)
-                                         for a, c, m, t in b.tune_table()},
+            "persistent_tune_table_ms": table,
             "persistent_phase_ms": dict(zip(["gather", "pairs_proj_near", "chunk_sums",
                                              "expansions", "combine"], phases)),
             "rel2_persistent_vs_graph_max": pers_vs_graph,
