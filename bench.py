@@ -377,7 +377,7 @@ def extra_batch(pkg, inputs, stream, count=256):
     t0 = time.perf_counter()
     shapes, _ = b.autotune(xs, yp, mode="f32", reps=3)
     t_ptune = time.perf_counter() - t0
-    table = {"%d/%d/%d" % (a, c, m): round(t, 3) for a, c, m, t in b.tune_table()}
+    table = {"%d/%d/%d/%d" % (a, c, m, pl): round(t, 3) for a, c, m, pl, t in b.tune_table()}
     b.matvec(xs, yp, mode="f32")
     b.check()
     e0.record(stream)

@@ -343,21 +343,27 @@ int hodlr2d_batch_get_shapes(hodlr2d_batch_t b, int* pair_rows, int* warp_rows);
 /* Resident 256-thread blocks per SM of the persistent kernel: 2, 3 (the
  * default) or 4, i.e. at most 128, 80 or 64 registers a thread. */
 int hodlr2d_batch_set_blocks_per_sm(hodlr2d_batch_t b, int blocks);
+/* Phase of the work that depends only on the gathered x (0-3): bit 0 runs
+ * the near field beside the expansions (phase 3) instead of beside the
+ * projections (phase 1); bit 1 runs the one-warp pairs beside the chunk sums
+ * (phase 2).  Default 0. */
+int hodlr2d_batch_set_placement(hodlr2d_batch_t b, int place);
 /* Autotuner of those settings: times reps persistent products (CUDA events
  * on the batch's stream, after one untimed product) for each candidate
  * pair_rows in {0, 64, 128, 256, 384, 512} and warp_rows in {0, 48, 64}
- * (warp_rows <= pair_rows) at the current blocks per SM, then the other
- * blocks-per-SM values at the fastest shapes; keeps the fastest and writes
- * its time per product to *best_ms (may be NULL).  Arguments as in
+ * (warp_rows <= pair_rows) at the current blocks per SM and placement,
+ * then the other blocks-per-SM values at the fastest shapes, then the other
+ * placements; keeps the fastest and writes its time per product to *best_ms
+ * (may be NULL).  Arguments as in
  * hodlr2d_batch_matvec (y is overwritten); modes F64 and F32 only.
  * Synchronises the stream.  Errors: ARG, STATE, CUDA, TIMEOUT. */
 int hodlr2d_batch_autotune(hodlr2d_batch_t b, const double* const* x, double* const* y,
                            const int* nrhs, int mode, int reps, double* best_ms);
 /* The candidates of the last hodlr2d_batch_autotune with their times per
- * product.  *count: in, the room of the four host arrays; out, the number
+ * product.  *count: in, the room of the five host arrays; out, the number
  * of candidates timed (arrays may be NULL to query it). */
 int hodlr2d_batch_tune_table(hodlr2d_batch_t b, int* count, int* pair_rows, int* warp_rows,
-                             int* blocks, double* ms);
+                             int* blocks, int* place, double* ms);
 /* Milliseconds of the five phases of the last persistent product (gather;
  * pairs, projections and near field; chunk sums; expansions; combine), read
  * from the device clock at the grid barriers.  ms: host array of 5.

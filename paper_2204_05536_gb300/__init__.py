@@ -405,17 +405,24 @@ class Batch:
         check(self._lib.hodlr2d_batch_set_blocks_per_sm(self._h, int(blocks)),
               "hodlr2d_batch_set_blocks_per_sm")
 
+    def set_placement(self, place: int):
+        """Persistent form: bit 0 runs the near field beside the expansions,
+        bit 1 the one-warp pairs beside the chunk sums."""
+        check(self._lib.hodlr2d_batch_set_placement(self._h, int(place)),
+              "hodlr2d_batch_set_placement")
+
     def tune_table(self):
-        """[(pair_rows, warp_rows, blocks per SM, ms per product)] of the last
-        autotune."""
+        """[(pair_rows, warp_rows, blocks per SM, placement, ms per product)]
+        of the last autotune."""
         cnt = C.c_int(0)
-        check(self._lib.hodlr2d_batch_tune_table(self._h, C.byref(cnt), None, None, None, None),
-              "hodlr2d_batch_tune_table")
+        check(self._lib.hodlr2d_batch_tune_table(self._h, C.byref(cnt), None, None, None, None,
+                                                 None), "hodlr2d_batch_tune_table")
         n = cnt.value
-        pr, wr, mb, ms = (C.c_int * n)(), (C.c_int * n)(), (C.c_int * n)(), (C.c_double * n)()
-        check(self._lib.hodlr2d_batch_tune_table(self._h, C.byref(cnt), pr, wr, mb, ms),
+        arr = [(C.c_int * n)() for _ in range(4)]
+        ms = (C.c_double * n)()
+        check(self._lib.hodlr2d_batch_tune_table(self._h, C.byref(cnt), *arr, ms),
               "hodlr2d_batch_tune_table")
-        return [(pr[i], wr[i], mb[i], ms[i]) for i in range(n)]
+        return [(arr[0][i], arr[1][i], arr[2][i], arr[3][i], ms[i]) for i in range(n)]
 
     def phase_ms(self):
         """Milliseconds of the five phases of the last persistent product."""

@@ -96,7 +96,8 @@ SIGNATURES = {
     "hodlr2d_batch_autotune": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int,
                                          C.POINTER(C.c_double)]),
     "hodlr2d_batch_phase_ms": (C.c_int, [_P, _P]),
-    "hodlr2d_batch_tune_table": (C.c_int, [_P, C.POINTER(C.c_int), _P, _P, _P, _P]),
+    "hodlr2d_batch_tune_table": (C.c_int, [_P, C.POINTER(C.c_int), _P, _P, _P, _P, _P]),
+    "hodlr2d_batch_set_placement": (C.c_int, [_P, C.c_int]),
     "hodlr2d_batch_set_blocks_per_sm": (C.c_int, [_P, C.c_int]),
     "hodlr2d_batch_free": (None, [_P]),
     "hodlr2d_free": (None, [_P]),

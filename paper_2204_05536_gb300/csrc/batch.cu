@@ -46,7 +46,7 @@ struct hodlr2d_batch {
   cudaGraphExec_t pexec = nullptr;
   // the last autotuning: (pair_rows, warp_rows, blocks per SM, ms per
   // product) per candidate
-  std::vector<int> tune_pair, tune_warp, tune_minb;
+  std::vector<int> tune_pair, tune_warp, tune_minb, tune_place;
   std::vector<double> tune_ms;
 };
 
@@ -216,6 +216,13 @@ int hodlr2d_batch_set_blocks_per_sm(hodlr2d_batch_t b, int blocks) {
   return HODLR2D_OK;
 }
 
+int hodlr2d_batch_set_placement(hodlr2d_batch_t b, int place) {
+  if (!b || place < 0 || place > 3) return HODLR2D_ERR_ARG;
+  if (b->bp.place != place) b->px.clear();
+  b->bp.place = place;
+  return HODLR2D_OK;
+}
+
 int hodlr2d_batch_get_shapes(hodlr2d_batch_t b, int* pair_rows, int* warp_rows) {
   if (!b || !pair_rows || !warp_rows) return HODLR2D_ERR_ARG;
   *pair_rows = b->bp.pair_rows;
@@ -239,6 +246,7 @@ static int batch_time(hodlr2d_batch* b, const double* const* x, double* const* y
   b->tune_pair.push_back(b->bp.pair_rows);
   b->tune_warp.push_back(b->bp.warp_rows);
   b->tune_minb.push_back(b->bp.minb);
+  b->tune_place.push_back(b->bp.place);
   b->tune_ms.push_back(*ms);
   return HODLR2D_OK;
 }
@@ -258,10 +266,12 @@ int hodlr2d_batch_autotune(hodlr2d_batch_t b, const double* const* x, double* co
   b->tune_pair.clear();
   b->tune_warp.clear();
   b->tune_minb.clear();
+  b->tune_place.clear();
   b->tune_ms.clear();
   float best = -1.f, ms = 0.f;
-  int bpr = b->bp.pair_rows, bwr = b->bp.warp_rows, bmb = b->bp.minb;
-  // shapes at the current occupancy, then the occupancy at the best shapes
+  int bpr = b->bp.pair_rows, bwr = b->bp.warp_rows, bmb = b->bp.minb, bpl = b->bp.place;
+  // shapes at the current occupancy and placement, then the occupancy at the
+  // best shapes, then the placement
   for (int pr : kPair)
     for (int wr : kWarp) {
       if (rc || wr > pr) continue;
@@ -284,23 +294,35 @@ int hodlr2d_batch_autotune(hodlr2d_batch_t b, const double* const* x, double* co
       bmb = mb;
     }
   }
+  if (!rc) rc = hodlr2d_batch_set_blocks_per_sm(b, bmb);
+  const int pl0 = bpl;
+  for (int pl = 0; pl <= 3 && !rc; ++pl) {
+    if (pl == pl0) continue;
+    rc = hodlr2d_batch_set_placement(b, pl);
+    if (!rc) rc = batch_time(b, x, y, nrhs, mode, reps, e0, e1, &ms);
+    if (!rc && ms < best) {
+      best = ms;
+      bpl = pl;
+    }
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   b->form = form;
   if (rc) return rc;
   if (best_ms) *best_ms = best;
-  return hodlr2d_batch_set_blocks_per_sm(b, bmb);
+  return hodlr2d_batch_set_placement(b, bpl);
 }
 
 int hodlr2d_batch_tune_table(hodlr2d_batch_t b, int* count, int* pair_rows, int* warp_rows,
-                             int* blocks, double* ms) {
+                             int* blocks, int* place, double* ms) {
   if (!b || !count) return HODLR2D_ERR_ARG;
   const int n = (int)b->tune_ms.size();
-  if (pair_rows && warp_rows && blocks && ms)
+  if (pair_rows && warp_rows && blocks && place && ms)
     for (int i = 0; i < std::min(n, *count); ++i) {
       pair_rows[i] = b->tune_pair[i];
       warp_rows[i] = b->tune_warp[i];
       blocks[i] = b->tune_minb[i];
+      place[i] = b->tune_place[i];
       ms[i] = b->tune_ms[i];
     }
   *count = n;

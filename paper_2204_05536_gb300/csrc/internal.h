@@ -152,10 +152,11 @@ struct V2Plan {
 };
 
 // A persistent batch product (product.cu): device descriptors of the sets,
-// prefix unit counts of the five phases, the pair items, the barrier words.
+// the unit descriptors of the five phases, the pair items, the barrier words.
 struct BatchPersist {
   void* d_sets = nullptr;
-  int64_t* d_pre = nullptr;
+  int64_t* d_pre = nullptr;   // the six phase offsets into d_tab
+  uint64_t* d_tab = nullptr;  // unit descriptors
   void* d_sync = nullptr;
   void* d_work = nullptr;
   int count = 0, mode = -1, grid = 0;
@@ -165,6 +166,7 @@ struct BatchPersist {
   // most warp_rows points); coarser levels run in two passes
   int pair_rows = 384, warp_rows = 64;
   int minb = 3;  // resident blocks per SM (2, 3 or 4: 128, 80 or 64 registers a thread)
+  int place = 0;  // bit 0: near field beside the expansions; bit 1: warp pairs beside chunk sums
 };
 int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, double* const* y,
                         const int* nrhs, int mode, BatchPersist* bp);

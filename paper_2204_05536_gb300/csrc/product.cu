@@ -33,6 +33,7 @@
 // product is bitwise reproducible.
 #include <algorithm>
 #include <type_traits>
+#include <array>
 #include <vector>
 
 #include "arith.cuh"
@@ -822,13 +823,21 @@ __device__ __forceinline__ void pairm_body(const ArgsV2& P, const int2 wk,
         yY[a][c] = A::zero();
       }
     }
+    // column q + 1 of U and V is loaded while column q is reduced
+    F u[RM], v[RM];
+#pragma unroll
+    for (int a = 0; a < RM; ++a) {
+      const int i = tid + a * T;
+      u[a] = i < m && k > 0 ? Ug[i] : fac_zero<F>();
+      v[a] = i < n && k > 0 ? Vg[i] : fac_zero<F>();
+    }
     for (int q = 0; q < k; ++q) {
-      F u[RM], v[RM];
+      F un[RM], vn[RM];
 #pragma unroll
       for (int a = 0; a < RM; ++a) {
         const int i = tid + a * T;
-        u[a] = i < m ? Ug[(int64_t)q * lm + i] : fac_zero<F>();
-        v[a] = i < n ? Vg[(int64_t)q * ln + i] : fac_zero<F>();
+        un[a] = i < m && q + 1 < k ? Ug[(int64_t)(q + 1) * lm + i] : fac_zero<F>();
+        vn[a] = i < n && q + 1 < k ? Vg[(int64_t)(q + 1) * ln + i] : fac_zero<F>();
       }
       V s[NV];  // s[c] = partial t1 of RHS c (V), s[NR + c] = partial t2 (U)
 #pragma unroll
@@ -878,6 +887,11 @@ __device__ __forceinline__ void pairm_body(const ArgsV2& P, const int2 wk,
             A::renorm(yX[a][c]);
             A::renorm(yY[a][c]);
           }
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        u[a] = un[a];
+        v[a] = vn[a];
+      }
     }
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
@@ -3104,7 +3118,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
 // pair's partial results); the coarser levels run in two passes
 // (projections over row chunks, chunk sums, expansions).  The work falls
 // into five phases, each a flat list of units over all sets (a unit is the
-// work of one 256-thread block):
+// work of one 256-thread block, named by a descriptor: set, kind, index):
 //   0 gather x into tree order;
 //   1 pairs (by their larger box: up to 512 points one pair per unit, up to
 //     256 two per unit of 128 threads each, up to 128 four per unit of 64
@@ -3114,8 +3128,9 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
 //     of 128 threads synchronise on named barriers 1-2, those of 64 on 3-6,
 //     each id always used by the same warps;
 //   2 chunk sums; 3 expansions; 4 combine.
-// Blocks walk a phase's units (grid-stride; a unit finds its set by binary
-// search over the phase's prefix counts), then meet at a grid barrier.  All
+// The near field and the one-warp pairs depend only on the gathered x, so
+// they may instead run beside the expansions and the chunk sums (place).
+// Blocks walk a phase's units grid-stride, then meet at a grid barrier.  All
 // blocks are resident (cooperative launch), and every barrier wait is
 // bounded: a block that polls `polls` times in vain records it in the status
 // word and leaves, so the launch always ends.  The last block out resets the
@@ -3192,8 +3207,27 @@ __device__ __forceinline__ bool batch_barrier(BatchSync* sy, unsigned target, ui
   return ok_s != 0;
 }
 
+// Unit kinds of the persistent product, and the unit descriptors: set
+// << 44 | kind << 40 | index of the unit among the set's units of its kind.
+enum BatchKind {
+  BK_GATHER = 0,  // 256 points
+  BK_BLK,         // one pair of at most 512 points
+  BK_G128,        // two pairs of at most 256 points (128 threads each)
+  BK_G64,         // four pairs of at most 128 points (64 threads each)
+  BK_PROJ,        // eight projection warps
+  BK_NEAR,        // eight near-field warps
+  BK_WARP,        // eight pairs of at most warp_rows points (a warp each)
+  BK_TSUM,        // eight chunk-sum warps
+  BK_EXP,         // one expansion task
+  BK_COMBINE,     // 256 points
+  BK_COUNT
+};
+__host__ __device__ constexpr uint64_t batch_desc(int set, int kind, int64_t i) {
+  return (uint64_t)set << 44 | (uint64_t)kind << 40 | (uint64_t)i;
+}
+
 template <class A, class NP>
-__device__ __forceinline__ void batch_unit(const BatchSet& S, int ph, int64_t lv) {
+__device__ __forceinline__ void batch_unit(const BatchSet& S, int kind, int64_t lv) {
   using V = typename A::val;
   constexpr int NRM = sizeof(typename A::acc) == 4 ? 4 : 2;  // right-hand sides per pair pass
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -3203,69 +3237,61 @@ __device__ __forceinline__ void batch_unit(const BatchSet& S, int ph, int64_t lv
   V* tt = reinterpret_cast<V*>(S.t);
   V* ppart = reinterpret_cast<V*>(S.ppart);
   const bool one = S.P.nrhs == 1;
-  switch (ph) {
-    case 0:
+  switch (kind) {
+    case BK_GATHER:
       gather2_body<A>(S.x, S.perm, S.P.n, S.P.nrhs, xt, lv * 256 + tid);
       return;
-    case 1: {
-      const int2* pw = S.pwork;
-      if (lv < S.np[0]) {  // one pair of at most 512 points
-        if (one) pairm_body<A, 256, 2, 1>(S.P, pw[lv], xt, ppart, tid);
-        else pairm_body<A, 256, 2, NRM>(S.P, pw[lv], xt, ppart, tid);
-        return;
-      }
-      lv -= S.np[0];
-      pw += S.np[0];
-      if (lv < (S.np[1] + 1) / 2) {  // two pairs of at most 256 points
-        const int g = tid >> 7;
-        const int64_t j = lv * 2 + g;
-        if (j >= S.np[1]) return;
-        if (one) pairm_body<A, 128, 2, 1, 2, 1>(S.P, pw[j], xt, ppart, tid & 127, g);
-        else pairm_body<A, 128, 2, NRM, 2, 1>(S.P, pw[j], xt, ppart, tid & 127, g);
-        return;
-      }
-      lv -= (S.np[1] + 1) / 2;
-      pw += S.np[1];
-      if (lv < (S.np[2] + 3) / 4) {  // four pairs of at most 128 points
-        const int g = tid >> 6;
-        const int64_t j = lv * 4 + g;
-        if (j >= S.np[2]) return;
-        if (one) pairm_body<A, 64, 2, 1, 4, 3>(S.P, pw[j], xt, ppart, tid & 63, g);
-        else pairm_body<A, 64, 2, NRM, 4, 3>(S.P, pw[j], xt, ppart, tid & 63, g);
-        return;
-      }
-      lv -= (S.np[2] + 3) / 4;
-      pw += S.np[2];
-      if (lv < S.u_proj) {
-        proj2_body<A>(S.P, S.proj, S.wtask, S.npart, xt, part, lv * 8 + warp);
-        return;
-      }
-      lv -= S.u_proj;
-      if (lv < S.u_near) {
-        const typename NP::K* kpp;
-        if constexpr (std::is_same<typename NP::K, KernelParams>::value) kpp = &S.kp;
-        else kpp = &S.kf32;
-        const typename NP::pt* xf = reinterpret_cast<const typename NP::pt*>(S.xf);
-        const typename NP::pt* yf = reinterpret_cast<const typename NP::pt*>(S.yf);
-        if (one)
-          near_warp_body<NP, 1>(xf, yf, S.P.leaf_off, S.P.kappa, S.nearw, S.nnearw, *kpp, xt,
-                                S.P.n, S.P.nrhs, yl, lv * 8 + warp);
-        else
-          near_warp_body<NP, 4>(xf, yf, S.P.leaf_off, S.P.kappa, S.nearw, S.nnearw, *kpp, xt,
-                                S.P.n, S.P.nrhs, yl, lv * 8 + warp);
-        return;
-      }
-      lv -= S.u_near;
-      const int64_t j = lv * 8 + warp;  // one pair of at most warp_rows points per warp
-      if (j >= S.np[3]) return;
-      if (one) pairm_body<A, 32, 2, 1>(S.P, pw[j], xt, ppart, lane);
-      else pairm_body<A, 32, 2, NRM>(S.P, pw[j], xt, ppart, lane);
+    case BK_BLK:
+      if (one) pairm_body<A, 256, 2, 1>(S.P, S.pwork[lv], xt, ppart, tid);
+      else pairm_body<A, 256, 2, NRM>(S.P, S.pwork[lv], xt, ppart, tid);
+      return;
+    case BK_G128: {
+      const int g = tid >> 7;
+      const int64_t j = lv * 2 + g;
+      if (j >= S.np[1]) return;
+      const int2 wk = S.pwork[S.np[0] + j];
+      if (one) pairm_body<A, 128, 2, 1, 2, 1>(S.P, wk, xt, ppart, tid & 127, g);
+      else pairm_body<A, 128, 2, NRM, 2, 1>(S.P, wk, xt, ppart, tid & 127, g);
       return;
     }
-    case 2:
+    case BK_G64: {
+      const int g = tid >> 6;
+      const int64_t j = lv * 4 + g;
+      if (j >= S.np[2]) return;
+      const int2 wk = S.pwork[S.np[0] + S.np[1] + j];
+      if (one) pairm_body<A, 64, 2, 1, 4, 3>(S.P, wk, xt, ppart, tid & 63, g);
+      else pairm_body<A, 64, 2, NRM, 4, 3>(S.P, wk, xt, ppart, tid & 63, g);
+      return;
+    }
+    case BK_PROJ:
+      proj2_body<A>(S.P, S.proj, S.wtask, S.npart, xt, part, lv * 8 + warp);
+      return;
+    case BK_NEAR: {
+      const typename NP::K* kpp;
+      if constexpr (std::is_same<typename NP::K, KernelParams>::value) kpp = &S.kp;
+      else kpp = &S.kf32;
+      const typename NP::pt* xf = reinterpret_cast<const typename NP::pt*>(S.xf);
+      const typename NP::pt* yf = reinterpret_cast<const typename NP::pt*>(S.yf);
+      if (one)
+        near_warp_body<NP, 1>(xf, yf, S.P.leaf_off, S.P.kappa, S.nearw, S.nnearw, *kpp, xt,
+                              S.P.n, S.P.nrhs, yl, lv * 8 + warp);
+      else
+        near_warp_body<NP, 4>(xf, yf, S.P.leaf_off, S.P.kappa, S.nearw, S.nnearw, *kpp, xt,
+                              S.P.n, S.P.nrhs, yl, lv * 8 + warp);
+      return;
+    }
+    case BK_WARP: {
+      const int64_t j = lv * 8 + warp;
+      if (j >= S.np[3]) return;
+      const int2 wk = S.pwork[S.np[0] + S.np[1] + S.np[2] + j];
+      if (one) pairm_body<A, 32, 2, 1>(S.P, wk, xt, ppart, lane);
+      else pairm_body<A, 32, 2, NRM>(S.P, wk, xt, ppart, lane);
+      return;
+    }
+    case BK_TSUM:
       tsum2_body<A>(S.P, S.proj, S.red, S.sideq, S.ntsum, part, tt, 0, lv * 8 + warp);
       return;
-    case 3:
+    case BK_EXP:
       exp2_body<A>(S.P, S.exps, tt, yl, lv);
       __syncthreads();  // its shared list is refilled by the next unit
       return;
@@ -3275,23 +3301,24 @@ __device__ __forceinline__ void batch_unit(const BatchSet& S, int ph, int64_t lv
 }
 
 // MINB: resident blocks per SM the compiler is asked for (registers a thread
-// 65536 / (256 MINB)); the batch picks one of 2, 3, 4
+// 65536 / (256 MINB)); the batch picks one of 2, 3, 4.  tab holds the unit
+// descriptors of the five phases, phase p at [off[p], off[p + 1]); a block
+// walks its units grid-stride, loading the next descriptor before it runs
+// the current unit.
 template <class A, class NP, int MINB>
 __global__ void __launch_bounds__(256, MINB)
-    k_batch(const BatchSet* __restrict__ sets, const int64_t* __restrict__ pre, int nsets,
-            BatchSync* sy, uint32_t polls) {
+    k_batch(const BatchSet* __restrict__ sets, const uint64_t* __restrict__ tab,
+            const int64_t* __restrict__ off, BatchSync* sy, uint32_t polls) {
   if (blockIdx.x == 0 && threadIdx.x == 0) sy->ts[0] = global_ns();
   for (int ph = 0; ph < 5; ++ph) {
-    const int64_t* pp = pre + (int64_t)ph * (nsets + 1);
-    const int64_t total = pp[nsets];
-    for (int64_t vb = blockIdx.x; vb < total; vb += gridDim.x) {
-      int lo = 0, hi = nsets - 1;  // the last set whose units start at or before vb
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pp[mid] <= vb) lo = mid;
-        else hi = mid - 1;
-      }
-      batch_unit<A, NP>(sets[lo], ph, vb - pp[lo]);
+    const int64_t end = off[ph + 1];
+    int64_t vb = off[ph] + blockIdx.x;
+    uint64_t d = vb < end ? tab[vb] : 0;
+    for (; vb < end; vb += gridDim.x) {
+      const uint64_t cur = d;
+      if (vb + gridDim.x < end) d = tab[vb + gridDim.x];
+      batch_unit<A, NP>(sets[cur >> 44], (int)((cur >> 40) & 15),
+                        (int64_t)(cur & ((uint64_t(1) << 40) - 1)));
     }
     if (ph == 4) break;
     if (!batch_barrier(sy, (unsigned)(ph + 1) * gridDim.x, polls)) break;
@@ -3336,8 +3363,9 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
   if (mode != HODLR2D_MODE_F64 && mode != HODLR2D_MODE_F32) return HODLR2D_ERR_ARG;
   const int pair_rows = std::min(bp->pair_rows, kBatchBlockRows);
   const int warp_rows = std::min(bp->warp_rows, 64);  // two rows a lane
+  if (count > (1 << 19)) return HODLR2D_ERR_ARG;  // set index of a unit descriptor
   std::vector<BatchSet> sets(count);
-  std::vector<int64_t> pre(5 * (size_t)(count + 1), 0);
+  std::vector<std::array<int64_t, BK_COUNT>> units(count);
   std::vector<int> lpair(count);
   for (int i = 0; i < count; ++i) {
     hodlr2d* h = hs[i];
@@ -3410,12 +3438,38 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
     H2D_CK(cudaMemsetAsync(V.d_ppart, 0, 8 * V.pstride * nrhs[i], s0));
     S.u_proj = (S.npart + 7) / 8;
     S.u_near = (V.nnearw + 7) / 8;
-    const int64_t units[5] = {(h->n + 255) / 256,
-                              S.np[0] + (S.np[1] + 1) / 2 + (S.np[2] + 3) / 4 + S.u_proj +
-                                  S.u_near + (S.np[3] + 7) / 8,
-                              (S.ntsum + 7) / 8, S.nexp, (h->n + 255) / 256};
-    for (int ph = 0; ph < 5; ++ph)
-      pre[(size_t)ph * (count + 1) + i + 1] = pre[(size_t)ph * (count + 1) + i] + units[ph];
+    auto& u = units[i];
+    u[BK_GATHER] = u[BK_COMBINE] = (h->n + 255) / 256;
+    u[BK_BLK] = S.np[0];
+    u[BK_G128] = (S.np[1] + 1) / 2;
+    u[BK_G64] = (S.np[2] + 3) / 4;
+    u[BK_PROJ] = S.u_proj;
+    u[BK_NEAR] = S.u_near;
+    u[BK_WARP] = (S.np[3] + 7) / 8;
+    u[BK_TSUM] = (S.ntsum + 7) / 8;
+    u[BK_EXP] = S.nexp;
+  }
+  // unit descriptors, phase by phase; within a phase kind by kind (longest
+  // units first), set by set.  place bit 0 moves the near field from phase 1
+  // to phase 3 (beside the expansions), bit 1 the one-warp pairs to phase 2
+  // (beside the chunk sums).
+  std::vector<int> kinds[5];
+  kinds[0] = {BK_GATHER};
+  kinds[1] = {BK_BLK, BK_G128, BK_G64, BK_PROJ};
+  if (!(bp->place & 1)) kinds[1].push_back(BK_NEAR);
+  if (!(bp->place & 2)) kinds[1].push_back(BK_WARP);
+  if (bp->place & 2) kinds[2].push_back(BK_WARP);
+  kinds[2].push_back(BK_TSUM);
+  kinds[3] = {BK_EXP};
+  if (bp->place & 1) kinds[3].push_back(BK_NEAR);
+  kinds[4] = {BK_COMBINE};
+  std::vector<uint64_t> tab;
+  int64_t off[6] = {0, 0, 0, 0, 0, 0};
+  for (int ph = 0; ph < 5; ++ph) {
+    for (int kind : kinds[ph])
+      for (int i = 0; i < count; ++i)
+        for (int64_t j = 0; j < units[i][kind]; ++j) tab.push_back(batch_desc(i, kind, j));
+    off[ph + 1] = (int64_t)tab.size();
   }
   H2D_CK(cudaMalloc(&bp->d_work, sizeof(int2) * std::max<size_t>(items.size(), 1)));
   for (int i = 0; i < count; ++i) sets[i].pwork = reinterpret_cast<int2*>(bp->d_work) + item0[i];
@@ -3423,12 +3477,15 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
     H2D_CK(cudaMemcpyAsync(bp->d_work, items.data(), sizeof(int2) * items.size(),
                            cudaMemcpyHostToDevice, s0));
   H2D_CK(cudaMalloc(&bp->d_sets, sizeof(BatchSet) * count));
-  H2D_CK(cudaMalloc(&bp->d_pre, sizeof(int64_t) * pre.size()));
+  H2D_CK(cudaMalloc(&bp->d_pre, sizeof(off)));
+  H2D_CK(cudaMalloc(&bp->d_tab, sizeof(uint64_t) * std::max<size_t>(tab.size(), 1)));
   H2D_CK(cudaMalloc(&bp->d_sync, sizeof(BatchSync)));
   H2D_CK(cudaMemcpyAsync(bp->d_sets, sets.data(), sizeof(BatchSet) * count,
                          cudaMemcpyHostToDevice, s0));
-  H2D_CK(cudaMemcpyAsync(bp->d_pre, pre.data(), sizeof(int64_t) * pre.size(),
-                         cudaMemcpyHostToDevice, s0));
+  H2D_CK(cudaMemcpyAsync(bp->d_pre, off, sizeof(off), cudaMemcpyHostToDevice, s0));
+  if (!tab.empty())
+    H2D_CK(cudaMemcpyAsync(bp->d_tab, tab.data(), sizeof(uint64_t) * tab.size(),
+                           cudaMemcpyHostToDevice, s0));
   H2D_CK(cudaMemsetAsync(bp->d_sync, 0, sizeof(BatchSync), s0));
   H2D_CK(cudaStreamSynchronize(s0));
   bp->count = count;
@@ -3444,7 +3501,7 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
 // One persistent launch on stream s: the whole product of every set.
 int batch_persist_launch(const BatchPersist& bp, cudaStream_t s) {
   BatchSync* sy = reinterpret_cast<BatchSync*>(bp.d_sync);
-  void* args[] = {(void*)&bp.d_sets, (void*)&bp.d_pre, (void*)&bp.count, (void*)&sy,
+  void* args[] = {(void*)&bp.d_sets, (void*)&bp.d_tab, (void*)&bp.d_pre, (void*)&sy,
                   (void*)&bp.polls};
   H2D_CK(cudaLaunchCooperativeKernel(batch_kernel(bp), dim3((unsigned)bp.grid), dim3(256), args,
                                      0, s));
@@ -3477,10 +3534,12 @@ int batch_persist_phase_ms(const BatchPersist& bp, cudaStream_t s, double* ms) {
 void batch_persist_free(BatchPersist* bp) {
   cudaFree(bp->d_sets);
   cudaFree(bp->d_pre);
+  cudaFree(bp->d_tab);
   cudaFree(bp->d_sync);
   cudaFree(bp->d_work);
   bp->d_sets = nullptr;
   bp->d_pre = nullptr;
+  bp->d_tab = nullptr;
   bp->d_sync = nullptr;
   bp->d_work = nullptr;
 }

@@ -147,12 +147,12 @@ def batch_sets(h2d, oracle):
     return mats, xs, want
 
 
-@pytest.mark.parametrize("form,shapes,blocks", [("graph", None, None),
-                                                ("persistent", None, None),
-                                                ("persistent", (0, 0), 2),
-                                                ("persistent", (128, 0), 4),
-                                                ("persistent", (512, 48), 3)])
-def test_batch_against_oracle(h2d, batch_sets, form, shapes, blocks):
+@pytest.mark.parametrize("form,shapes,blocks,place", [("graph", None, None, None),
+                                                      ("persistent", None, None, None),
+                                                      ("persistent", (0, 0), 2, 0),
+                                                      ("persistent", (128, 0), 4, 1),
+                                                      ("persistent", (512, 48), 3, 3)])
+def test_batch_against_oracle(h2d, batch_sets, form, shapes, blocks, place):
     """hodlr2d_batch_matvec over independent handles of uneven size against
     each set's own oracle product on the same factors, in binary64 and
     binary32: one graph launch (recorded on the first call, replayed on the
@@ -160,12 +160,15 @@ def test_batch_against_oracle(h2d, batch_sets, form, shapes, blocks):
     bounded grid barriers) with its default shapes, with every level in two
     passes (0, 0), with pairs up to 128 points four per 256-thread unit
     (128, 0), and with pairs up to 512 points, those of <= 48 one per warp
-    (512, 48); at 2, 4 and 3 resident blocks per SM."""
+    (512, 48); at 2, 4 and 3 resident blocks per SM; with the near field in
+    the first phase or beside the expansions, the one-warp pairs beside the
+    chunk sums."""
     mats, xs, want = batch_sets
     b = h2d.Batch(mats, stream=torch.cuda.current_stream(), form=form)
     if shapes is not None:
         b.set_shapes(*shapes)
         b.set_blocks_per_sm(blocks)
+        b.set_placement(place)
     xd = [torch.from_numpy(x).cuda() for x in xs]
     for mode in ("f64", "f32"):
         ys = [torch.empty_like(x) for x in xd]
