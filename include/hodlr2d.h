@@ -332,12 +332,14 @@ int hodlr2d_batch_check(hodlr2d_batch_t b);
  * HODLR2D_BATCH_PERSISTENT), or -1 before the first. */
 int hodlr2d_batch_last_form(hodlr2d_batch_t b);
 /* Work shapes of the persistent form by box size: the levels whose boxes
- * hold at most pair_rows points (0 <= pair_rows <= 512) run as pairs, each
- * stored pair read once (t1 = V^T x_Y, t2 = U^T x_X, then U t1 and V t2):
- * pairs of at most warp_rows points (0 <= warp_rows <= 64) one per warp, the
- * others one per 256-thread unit; coarser levels run in two passes
- * (projections over 512-row chunks, chunk sums, expansions over 256-row
- * chunks).  Defaults 384 and 64.  Takes effect at the next product. */
+ * hold at most pair_rows points (0 <= pair_rows <= 2048; binary64 uses at
+ * most 1024) run as pairs, each stored pair read once (t1 = V^T x_Y,
+ * t2 = U^T x_X, then U t1 and V t2): pairs of at most warp_rows points
+ * (0 <= warp_rows <= 64) one per warp, of at most 128 points four per
+ * 256-thread unit, of at most 256 two per unit, larger ones one per unit;
+ * coarser levels run in two passes (projections over 512-row chunks, chunk
+ * sums, expansions over 256-row chunks).  Defaults 384 and 64.  Takes effect
+ * at the next product. */
 int hodlr2d_batch_set_shapes(hodlr2d_batch_t b, int pair_rows, int warp_rows);
 int hodlr2d_batch_get_shapes(hodlr2d_batch_t b, int* pair_rows, int* warp_rows);
 /* Resident 256-thread blocks per SM of the persistent kernel: 2, 3 (the
@@ -350,7 +352,7 @@ int hodlr2d_batch_set_blocks_per_sm(hodlr2d_batch_t b, int blocks);
 int hodlr2d_batch_set_placement(hodlr2d_batch_t b, int place);
 /* Autotuner of those settings: times reps persistent products (CUDA events
  * on the batch's stream, after one untimed product) for each candidate
- * pair_rows in {0, 64, 128, 256, 384, 512} and warp_rows in {0, 48, 64}
+ * pair_rows in {0, 128, 256, 512, 1024, 2048} and warp_rows in {0, 48, 64}
  * (warp_rows <= pair_rows) at the current blocks per SM and placement,
  * then the other blocks-per-SM values at the fastest shapes, then the other
  * placements; keeps the fastest and writes its time per product to *best_ms

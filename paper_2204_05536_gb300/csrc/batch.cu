@@ -201,7 +201,7 @@ static int batch_persistent(hodlr2d_batch* b, const double* const* x, double* co
 }
 
 int hodlr2d_batch_set_shapes(hodlr2d_batch_t b, int pair_rows, int warp_rows) {
-  if (!b || pair_rows < 0 || warp_rows < 0 || warp_rows > 64 || pair_rows > 512)
+  if (!b || pair_rows < 0 || warp_rows < 0 || warp_rows > 64 || pair_rows > 2048)
     return HODLR2D_ERR_ARG;
   if (b->bp.pair_rows != pair_rows || b->bp.warp_rows != warp_rows) b->px.clear();
   b->bp.pair_rows = pair_rows;
@@ -255,7 +255,7 @@ int hodlr2d_batch_autotune(hodlr2d_batch_t b, const double* const* x, double* co
                            const int* nrhs, int mode, int reps, double* best_ms) {
   if (!b || !x || !y || !nrhs || reps < 1) return HODLR2D_ERR_ARG;
   if ((mode != HODLR2D_MODE_F64 && mode != HODLR2D_MODE_F32) || !b->coop) return HODLR2D_ERR_ARG;
-  static const int kPair[] = {0, 64, 128, 256, 384, 512};
+  static const int kPair[] = {0, 128, 256, 512, 1024, 2048};
   static const int kWarp[] = {0, 48, 64};
   const int form = b->form;
   b->form = HODLR2D_BATCH_PERSISTENT;

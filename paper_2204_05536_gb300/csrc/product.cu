@@ -3120,8 +3120,8 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
 // into five phases, each a flat list of units over all sets (a unit is the
 // work of one 256-thread block, named by a descriptor: set, kind, index):
 //   0 gather x into tree order;
-//   1 pairs (by their larger box: up to 512 points one pair per unit, up to
-//     256 two per unit of 128 threads each, up to 128 four per unit of 64
+//   1 pairs (by their larger box: up to 2048 points one pair per unit, up
+//     to 256 two per unit of 128 threads each, up to 128 four per unit of 64
 //     threads each, up to warp_rows one per warp), the two-pass projections
 //     and the near field -- independent work, longest units first.  The
 //     groups of one unit do not wait for each other at its end: the groups
@@ -3136,7 +3136,14 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
 // word and leaves, so the launch always ends.  The last block out resets the
 // barrier counters for the next launch, so one launch is the whole product.
 // ---------------------------------------------------------------------------
-constexpr int kBatchBlockRows = 512;  // largest box of a one-pair-per-unit item (2 rows a thread)
+// largest box of a one-pair-per-unit item: 2048 points (8 rows a thread,
+// one right-hand side per pass) for 4-byte sums, 1024 for binary64
+constexpr int kBatchBlockRows = 2048;
+// pair items by the box size they take, largest first: one per unit with
+// 8, 4 or 2 rows a thread, two per unit (128 threads each), four per unit
+// (64 threads each), one per warp
+constexpr int kBatchPairKinds = 6;
+constexpr int kBatchKindRows[kBatchPairKinds - 1] = {2048, 1024, 512, 256, 128};
 
 struct BatchSet {
   ArgsV2 P;                   // LMODE_TWO below the first pair level, LMODE_PAIR from it on
@@ -3163,10 +3170,10 @@ struct BatchSet {
   int64_t ntsum;              // chunk-sum warps
   const ExpTask* exps;
   int64_t nexp;
-  // pair items (level, pair) by group size: one per unit (256 threads), per
-  // 128, per 64 and per 32 threads, in that order in pwork
+  // pair items (level, pair) by kind (kBatchKindRows): kind q at
+  // pwork[p0[q] .. p0[q + 1])
   const int2* pwork;
-  int64_t np[4];
+  int64_t p0[kBatchPairKinds + 1];
   int64_t u_proj, u_near;     // phase-1 units of the projections and of the near field
 };
 
@@ -3211,6 +3218,8 @@ __device__ __forceinline__ bool batch_barrier(BatchSync* sy, unsigned target, ui
 // << 44 | kind << 40 | index of the unit among the set's units of its kind.
 enum BatchKind {
   BK_GATHER = 0,  // 256 points
+  BK_BLK8,        // one pair of at most 2048 points (4-byte sums only)
+  BK_BLK4,        // one pair of at most 1024 points
   BK_BLK,         // one pair of at most 512 points
   BK_G128,        // two pairs of at most 256 points (128 threads each)
   BK_G64,         // four pairs of at most 128 points (64 threads each)
@@ -3237,28 +3246,36 @@ __device__ __forceinline__ void batch_unit(const BatchSet& S, int kind, int64_t 
   V* tt = reinterpret_cast<V*>(S.t);
   V* ppart = reinterpret_cast<V*>(S.ppart);
   const bool one = S.P.nrhs == 1;
+  constexpr bool b32 = sizeof(typename A::acc) == 4;
   switch (kind) {
     case BK_GATHER:
       gather2_body<A>(S.x, S.perm, S.P.n, S.P.nrhs, xt, lv * 256 + tid);
       return;
+    case BK_BLK8:
+      if constexpr (b32) pairm_body<A, 256, 8, 1>(S.P, S.pwork[S.p0[0] + lv], xt, ppart, tid);
+      return;
+    case BK_BLK4:
+      if (one || !b32) pairm_body<A, 256, 4, 1>(S.P, S.pwork[S.p0[1] + lv], xt, ppart, tid);
+      else pairm_body<A, 256, 4, 2>(S.P, S.pwork[S.p0[1] + lv], xt, ppart, tid);
+      return;
     case BK_BLK:
-      if (one) pairm_body<A, 256, 2, 1>(S.P, S.pwork[lv], xt, ppart, tid);
-      else pairm_body<A, 256, 2, NRM>(S.P, S.pwork[lv], xt, ppart, tid);
+      if (one) pairm_body<A, 256, 2, 1>(S.P, S.pwork[S.p0[2] + lv], xt, ppart, tid);
+      else pairm_body<A, 256, 2, NRM>(S.P, S.pwork[S.p0[2] + lv], xt, ppart, tid);
       return;
     case BK_G128: {
       const int g = tid >> 7;
-      const int64_t j = lv * 2 + g;
-      if (j >= S.np[1]) return;
-      const int2 wk = S.pwork[S.np[0] + j];
+      const int64_t j = S.p0[3] + lv * 2 + g;
+      if (j >= S.p0[4]) return;
+      const int2 wk = S.pwork[j];
       if (one) pairm_body<A, 128, 2, 1, 2, 1>(S.P, wk, xt, ppart, tid & 127, g);
       else pairm_body<A, 128, 2, NRM, 2, 1>(S.P, wk, xt, ppart, tid & 127, g);
       return;
     }
     case BK_G64: {
       const int g = tid >> 6;
-      const int64_t j = lv * 4 + g;
-      if (j >= S.np[2]) return;
-      const int2 wk = S.pwork[S.np[0] + S.np[1] + j];
+      const int64_t j = S.p0[4] + lv * 4 + g;
+      if (j >= S.p0[5]) return;
+      const int2 wk = S.pwork[j];
       if (one) pairm_body<A, 64, 2, 1, 4, 3>(S.P, wk, xt, ppart, tid & 63, g);
       else pairm_body<A, 64, 2, NRM, 4, 3>(S.P, wk, xt, ppart, tid & 63, g);
       return;
@@ -3281,9 +3298,9 @@ __device__ __forceinline__ void batch_unit(const BatchSet& S, int kind, int64_t 
       return;
     }
     case BK_WARP: {
-      const int64_t j = lv * 8 + warp;
-      if (j >= S.np[3]) return;
-      const int2 wk = S.pwork[S.np[0] + S.np[1] + S.np[2] + j];
+      const int64_t j = S.p0[5] + lv * 8 + warp;
+      if (j >= S.p0[6]) return;
+      const int2 wk = S.pwork[j];
       if (one) pairm_body<A, 32, 2, 1>(S.P, wk, xt, ppart, lane);
       else pairm_body<A, 32, 2, NRM>(S.P, wk, xt, ppart, lane);
       return;
@@ -3361,7 +3378,8 @@ static int batch_first_pair_level(const hodlr2d* h, int pair_rows) {
 int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, double* const* y,
                         const int* nrhs, int mode, BatchPersist* bp) {
   if (mode != HODLR2D_MODE_F64 && mode != HODLR2D_MODE_F32) return HODLR2D_ERR_ARG;
-  const int pair_rows = std::min(bp->pair_rows, kBatchBlockRows);
+  const int pair_rows =
+      std::min(bp->pair_rows, mode == HODLR2D_MODE_F64 ? kBatchBlockRows / 2 : kBatchBlockRows);
   const int warp_rows = std::min(bp->warp_rows, 64);  // two rows a lane
   if (count > (1 << 19)) return HODLR2D_ERR_ARG;  // set index of a unit descriptor
   std::vector<BatchSet> sets(count);
@@ -3421,16 +3439,20 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
     S.exps = V.d_exp;
     S.nexp = V.pre_exp[lp];
     item0[i] = (int64_t)items.size();
-    for (int kind = 0; kind < 4; ++kind) {
-      S.np[kind] = 0;
+    S.p0[0] = 0;
+    for (int kind = 0; kind < kBatchPairKinds; ++kind) {
+      S.p0[kind + 1] = S.p0[kind];
       for (int l = lp; l <= h->kappa; ++l) {
         const PairLevel& G = V.plev[l];
         for (int c = 0; c < kPairClasses; ++c) {
           const int r = G.cls_rows[c];
-          const int k = r <= warp_rows ? 3 : r <= 128 ? 2 : r <= 256 ? 1 : 0;
+          int k = kBatchPairKinds - 1;  // the smallest kind whose boxes hold r points
+          if (r > warp_rows)
+            for (k = kBatchPairKinds - 2; k > 0 && r > kBatchKindRows[k]; --k) {
+            }
           if (k != kind) continue;
           items.insert(items.end(), G.h_work.begin() + G.off[c], G.h_work.begin() + G.off[c + 1]);
-          S.np[kind] += G.off[c + 1] - G.off[c];
+          S.p0[kind + 1] += G.off[c + 1] - G.off[c];
         }
       }
     }
@@ -3440,12 +3462,14 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
     S.u_near = (V.nnearw + 7) / 8;
     auto& u = units[i];
     u[BK_GATHER] = u[BK_COMBINE] = (h->n + 255) / 256;
-    u[BK_BLK] = S.np[0];
-    u[BK_G128] = (S.np[1] + 1) / 2;
-    u[BK_G64] = (S.np[2] + 3) / 4;
+    u[BK_BLK8] = S.p0[1] - S.p0[0];
+    u[BK_BLK4] = S.p0[2] - S.p0[1];
+    u[BK_BLK] = S.p0[3] - S.p0[2];
+    u[BK_G128] = (S.p0[4] - S.p0[3] + 1) / 2;
+    u[BK_G64] = (S.p0[5] - S.p0[4] + 3) / 4;
     u[BK_PROJ] = S.u_proj;
     u[BK_NEAR] = S.u_near;
-    u[BK_WARP] = (S.np[3] + 7) / 8;
+    u[BK_WARP] = (S.p0[6] - S.p0[5] + 7) / 8;
     u[BK_TSUM] = (S.ntsum + 7) / 8;
     u[BK_EXP] = S.nexp;
   }
@@ -3455,7 +3479,7 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
   // (beside the chunk sums).
   std::vector<int> kinds[5];
   kinds[0] = {BK_GATHER};
-  kinds[1] = {BK_BLK, BK_G128, BK_G64, BK_PROJ};
+  kinds[1] = {BK_BLK8, BK_BLK4, BK_BLK, BK_G128, BK_G64, BK_PROJ};
   if (!(bp->place & 1)) kinds[1].push_back(BK_NEAR);
   if (!(bp->place & 2)) kinds[1].push_back(BK_WARP);
   if (bp->place & 2) kinds[2].push_back(BK_WARP);

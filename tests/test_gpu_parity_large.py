@@ -151,7 +151,8 @@ def batch_sets(h2d, oracle):
                                                       ("persistent", None, None, None),
                                                       ("persistent", (0, 0), 2, 0),
                                                       ("persistent", (128, 0), 4, 1),
-                                                      ("persistent", (512, 48), 3, 3)])
+                                                      ("persistent", (512, 48), 3, 3),
+                                                      ("persistent", (2048, 64), 3, 2)])
 def test_batch_against_oracle(h2d, batch_sets, form, shapes, blocks, place):
     """hodlr2d_batch_matvec over independent handles of uneven size against
     each set's own oracle product on the same factors, in binary64 and
@@ -160,7 +161,9 @@ def test_batch_against_oracle(h2d, batch_sets, form, shapes, blocks, place):
     bounded grid barriers) with its default shapes, with every level in two
     passes (0, 0), with pairs up to 128 points four per 256-thread unit
     (128, 0), and with pairs up to 512 points, those of <= 48 one per warp
-    (512, 48); at 2, 4 and 3 resident blocks per SM; with the near field in
+    (512, 48), and with pairs up to 2048 points (binary64: 1024), at most
+    8 rows a thread (2048, 64); at 2, 4 and 3 resident blocks per SM; with
+    the near field in
     the first phase or beside the expansions, the one-warp pairs beside the
     chunk sums."""
     mats, xs, want = batch_sets
