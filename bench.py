@@ -377,7 +377,12 @@ def extra_batch(pkg, inputs, stream, count=256):
     t0 = time.perf_counter()
     shapes, _ = b.autotune(xs, yp, mode="f32", reps=3)
     t_ptune = time.perf_counter() - t0
-    table = {"%d/%d/%d/%d" % (a, c, m, pl): round(t, 3) for a, c, m, pl, t in b.tune_table()}
+    table = {("graph" if a < 0 else "%d/%d/%d/%d" % (a, c, m, pl)): round(t, 3)
+             for a, c, m, pl, t in b.tune_table()}
+    b.set_form("auto")
+    b.matvec(xs, yp, mode="f32")
+    auto_form = b.last_form
+    b.set_form("persistent")
     b.matvec(xs, yp, mode="f32")
     b.check()
     e0.record(stream)
@@ -416,6 +421,7 @@ def extra_batch(pkg, inputs, stream, count=256):
             "persistent_shapes": {"pair_rows": shapes[0], "warp_rows": shapes[1]},
             "persistent_tune_s": round(t_ptune, 2),
             "persistent_tune_table_ms": table,
+            "auto_form_after_tune": auto_form,
             "persistent_phase_ms": dict(zip(["gather", "pairs_proj_near", "chunk_sums",
                                              "expansions", "combine"], phases)),
             "rel2_persistent_vs_graph_max": pers_vs_graph,

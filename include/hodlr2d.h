@@ -302,8 +302,9 @@ int hodlr2d_pair_features(hodlr2d_t h, int64_t* npairs, float* feats, float* log
  *     bounded (hodlr2d_batch_set_wait_limit); a block whose wait gives up
  *     records it and the launch ends without writing y:
  *     hodlr2d_batch_check then returns HODLR2D_ERR_TIMEOUT.
- *   HODLR2D_BATCH_AUTO (the default): PERSISTENT for F64 and F32 when the
- *     device supports cooperative launches, else GRAPH.
+ *   HODLR2D_BATCH_AUTO (the default): GRAPH, which measured faster on the
+ *     benchmark's 256 sets, until hodlr2d_batch_autotune has timed both
+ *     forms on the caller's inputs; then the faster of the two.
  * Either form is set up again when a handle's plans, working memory or
  * factor copies have changed since the recording.  The handles must outlive
  * the batch and must not be used concurrently with it.  x[i], y[i]: device
@@ -356,7 +357,9 @@ int hodlr2d_batch_set_placement(hodlr2d_batch_t b, int place);
  * (warp_rows <= pair_rows) at the current blocks per SM and placement,
  * then the other blocks-per-SM values at the fastest shapes, then the other
  * placements; keeps the fastest and writes its time per product to *best_ms
- * (may be NULL).  Arguments as in
+ * (may be NULL).  Then times the graph form once (its table row has -1 for
+ * the four settings), and HODLR2D_BATCH_AUTO runs the faster form from then
+ * on.  Arguments as in
  * hodlr2d_batch_matvec (y is overwritten); modes F64 and F32 only.
  * Synchronises the stream.  Errors: ARG, STATE, CUDA, TIMEOUT. */
 int hodlr2d_batch_autotune(hodlr2d_batch_t b, const double* const* x, double* const* y,

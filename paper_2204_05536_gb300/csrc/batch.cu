@@ -35,6 +35,7 @@ struct hodlr2d_batch {
   // recorded into a graph (when the driver takes a cooperative launch in a
   // capture; else it is launched directly)
   int form = HODLR2D_BATCH_AUTO;
+  int auto_form = HODLR2D_BATCH_GRAPH;  // what AUTO runs (hodlr2d_batch_autotune may change it)
   int last_form = -1;
   bool coop = false;  // the device supports cooperative launches
   h2d::BatchPersist bp;
@@ -305,12 +306,23 @@ int hodlr2d_batch_autotune(hodlr2d_batch_t b, const double* const* x, double* co
       bpl = pl;
     }
   }
+  if (!rc) rc = hodlr2d_batch_set_placement(b, bpl);
+  // the graph form on the same inputs decides what AUTO runs
+  float gms = 0.f;
+  if (!rc) {
+    b->form = HODLR2D_BATCH_GRAPH;
+    rc = batch_time(b, x, y, nrhs, mode, reps, e0, e1, &gms);
+    if (!rc) {
+      b->tune_pair.back() = b->tune_warp.back() = b->tune_minb.back() = b->tune_place.back() = -1;
+      b->auto_form = gms < best ? HODLR2D_BATCH_GRAPH : HODLR2D_BATCH_PERSISTENT;
+    }
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   b->form = form;
   if (rc) return rc;
   if (best_ms) *best_ms = best;
-  return hodlr2d_batch_set_placement(b, bpl);
+  return HODLR2D_OK;
 }
 
 int hodlr2d_batch_tune_table(hodlr2d_batch_t b, int* count, int* pair_rows, int* warp_rows,
@@ -342,7 +354,10 @@ int hodlr2d_batch_matvec(hodlr2d_batch_t b, const double* const* x, double* cons
   }
   const bool mode_ok = mode == HODLR2D_MODE_F64 || mode == HODLR2D_MODE_F32;
   if (b->form == HODLR2D_BATCH_PERSISTENT && (!mode_ok || !b->coop)) return HODLR2D_ERR_ARG;
-  if (b->form == HODLR2D_BATCH_PERSISTENT || (b->form == HODLR2D_BATCH_AUTO && mode_ok && b->coop)) {
+  const bool pers = b->form == HODLR2D_BATCH_PERSISTENT ||
+                    (b->form == HODLR2D_BATCH_AUTO && b->auto_form == HODLR2D_BATCH_PERSISTENT &&
+                     mode_ok && b->coop);
+  if (pers) {
     H2D_TRY(batch_persistent(b, x, y, nrhs, mode));
     b->last_form = HODLR2D_BATCH_PERSISTENT;
     return HODLR2D_OK;

@@ -72,6 +72,13 @@ def test_batch_shape_autotuner(pkg):
     b = pkg.Batch(mats, form="persistent")
     (pr, wr), ms = b.autotune(xs, ys, mode="f32", reps=2)
     assert pr in (0, 128, 256, 512, 1024, 2048) and wr in (0, 48, 64) and wr <= pr and ms > 0
+    table = b.tune_table()
+    assert table[-1][:4] == (-1, -1, -1, -1)  # the graph form, timed last
+    b.set_form("auto")
+    b.matvec(xs, ys, mode="f32")
+    want = "graph" if table[-1][4] < ms else "persistent"
+    assert b.last_form == want
+    b.set_form("persistent")
     b.matvec(xs, ys, mode="f32")
     b.check()
     assert len(b.phase_ms()) == 5 and all(t >= 0 for t in b.phase_ms())
