@@ -361,6 +361,8 @@ def extra_batch(pkg, inputs, stream, count=256):
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
     nprod = int(sum(x.shape[0] for x in xs))
+    far_values = int(sum(m.stats()["far_values"] for m in mats))
+    hbm_gbs = peaks()[0]
     b = pkg.Batch(mats, stream=stream, form="graph")
     b.matvec(xs, ys, mode="f32")  # records the graph
     torch.cuda.synchronize()
@@ -416,6 +418,8 @@ def extra_batch(pkg, inputs, stream, count=256):
             "leaf_per_class": {str(int(round(edges[c]))): v for c, v in leaf_of.items()},
             "graph_ms": round(t_graph, 3), "sequential_launches_ms": round(t_seq, 3),
             "products_per_s_graph": round(nprod / (t_graph * 1e-3), 1),
+            "factor_bytes_f32": 4 * far_values,
+            "factor_read_once_ms_at_hbm_peak": round(4 * far_values / (hbm_gbs * 1e6), 3),
             "persistent_ms": round(t_pers, 3),
             "products_per_s_persistent": round(nprod / (t_pers * 1e-3), 1),
             "persistent_shapes": {"pair_rows": shapes[0], "warp_rows": shapes[1]},
