@@ -41,7 +41,9 @@ ROOT_BOX = (-1.0, -1.0, 2.0)
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default: 200, a timed region of about 2 s for the "
+                        "binary64 product; 20 for the CPU reference arm)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--modes", default="f64,df32,f32,bf16",
@@ -54,7 +56,10 @@ def parse():
                    help="comma-separated secondary measurements to run (default: all)")
     p.add_argument("--n-learned", type=int, default=1 << 22,
                    help="points of the learned-rank build (log r kernel)")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.steps is None:
+        args.steps = 200 if args.impl == "ours" else 20
+    return args
 
 
 def dist_setup():
