@@ -101,6 +101,7 @@ struct V2Plan {
   int lfuse = 1;   // first single-read level
   int ldual = 1;   // first two-pass level that also has a pair plan (<= lfuse)
   int l2max = 1;   // two-pass plans exist for levels [1, l2max) (>= lfuse)
+  int l2few = 1;   // first level of boxes <= 1024 points (>= lfuse): few-RHS pair levels
   // two-pass task counts of the levels below l (level-ordered list prefixes)
   int64_t pre_proj[HODLR2D_MAX_LEVELS + 1] = {}, pre_exp[HODLR2D_MAX_LEVELS + 1] = {};
   int64_t pre_part[HODLR2D_MAX_LEVELS + 1] = {}, pre_tsum[HODLR2D_MAX_LEVELS + 1] = {};

@@ -63,6 +63,10 @@ constexpr int kDualKmax = 64;
 // two passes (each factor value read twice for all of them); smaller ones run
 // with the multi-RHS register pair kernel.
 constexpr int kMultiRows = 256;
+// with at most kFewRhs right-hand sides, pairs of boxes up to kMultiRowsFew
+// points run as pairs too (one 256-thread block each)
+constexpr int kFewRhs = 8;
+constexpr int kMultiRowsFew = 1024;
 
 struct LevelV2 {
   const int32_t* px;
@@ -2367,14 +2371,15 @@ static bool box_as_pairs(const hodlr2d* h, int l, int nrhs, int mode) {
 
 // First level that is not run in two passes by a product:
 //   binary64                    lfuse (pairs from there on)
-//   several right-hand sides    l2max (boxes of <= kMultiRows points as pairs)
+//   several right-hand sides    l2max (boxes of <= kMultiRows points as pairs;
+//                               with <= kFewRhs, l2few: <= kMultiRowsFew)
 //   one right-hand side         ldual (the 512 x 9 register forms hold the
 //                               boxes of [ldual, lfuse): two columns per
 //                               step in binary32, one in float-float)
 static int two_pass_end(const hodlr2d* h, int nrhs, int mode) {
   const V2Plan& V = h->v2;
   if (mode == HODLR2D_MODE_F64) return V.lfuse;
-  if (nrhs > 1) return V.l2max;
+  if (nrhs > 1) return nrhs <= kFewRhs ? V.l2few : V.l2max;
   return V.ldual;
 }
 
@@ -2635,6 +2640,8 @@ int plan_v2(hodlr2d* h) {
   // plan, which several right-hand sides use: [lfuse, l2max)
   V.l2max = V.lfuse;
   while (V.l2max <= kappa && maxcount(V.l2max) > kMultiRows) ++V.l2max;
+  V.l2few = V.lfuse;
+  while (V.l2few <= kappa && maxcount(V.l2few) > kMultiRowsFew) ++V.l2few;
   H2D_TRY(build_two_pass(h, V.l2max));
   // single-read levels: pair mode (one block per pair, partials for both
   // sides) or box mode (one warp per row box, partials for the column side)
@@ -2891,6 +2898,10 @@ static int launch_pair_multi(const int2* work, int64_t nw, int rows, const ArgsV
     k_pairm<A, 64, 2, NR><<<nb, 64, 0, st>>>(P, work, xt, ppart);
   else if (rows <= kMultiRows)
     k_pairm<A, 128, 2, NR><<<nb, 128, 0, st>>>(P, work, xt, ppart);
+  else if (rows <= 512 && P.nrhs <= kFewRhs)
+    k_pairm<A, 256, 2, NR><<<nb, 256, 0, st>>>(P, work, xt, ppart);
+  else if (rows <= kMultiRowsFew && P.nrhs <= kFewRhs)  // four rows a thread: half the RHS a pass
+    k_pairm<A, 256, 4, NR / 2><<<nb, 256, 0, st>>>(P, work, xt, ppart);
   else
     return launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st);
   H2D_CK(cudaGetLastError());
