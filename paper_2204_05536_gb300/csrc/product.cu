@@ -3034,7 +3034,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
       PhaseScope ps(h, 2, 1, fs * two_pass_vals + vs * npart * nrhs);
       ps.flops(2 * two_pass_vals * nrhs);
       const int64_t thr = npart * 32;  // one warp per (task, column)
-      if (std::is_same<A, BF16A>::value && nrhs > 1)  // tensor cores
+      if (std::is_same<A, BF16A>::value && nrhs > kFewRhs)  // tensor cores
         if (V.grp_ok)  // tasks grouped by box: x loaded once per group
           k_projg_t5<<<(unsigned)std::min<int64_t>(V.pre_grp[l2end], 3 * V.nsm), 256, kGrpSmem,
                        s>>>(P, V.d_proj, V.d_gtask, V.d_grp, V.pre_grp[l2end],
@@ -3076,7 +3076,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   if (nexp) {
     PhaseScope ps(h, 4, 1, fs * two_pass_vals + vb * (l2end - 1));
     ps.flops(2 * two_pass_vals * nrhs);
-    if (std::is_same<A, BF16A>::value && nrhs > 1)  // tensor cores
+    if (std::is_same<A, BF16A>::value && nrhs > kFewRhs)  // tensor cores
       k_exp_t5<<<(unsigned)std::min<int64_t>(nexp, 4 * V.nsm), 128, kT5Smem, s>>>(
           P, V.d_exp, nexp, reinterpret_cast<const float*>(V.d_t), reinterpret_cast<float*>(yl),
           V.d_status);
