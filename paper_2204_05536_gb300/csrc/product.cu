@@ -63,10 +63,18 @@ constexpr int kDualKmax = 64;
 // two passes (each factor value read twice for all of them); smaller ones run
 // with the multi-RHS register pair kernel.
 constexpr int kMultiRows = 256;
-// with at most kFewRhs right-hand sides, pairs of boxes up to kMultiRowsFew
-// points run as pairs too (one 256-thread block each)
+// With few right-hand sides (binary32 sums: 2-8, bfloat16 factors: 2-4),
+// pairs of boxes up to kMultiRowsFew points run as pairs too (one 256-thread
+// block each), and bfloat16 stays off the tensor cores.  Measured at N = 2^20
+// against two passes above 256 points: binary32 2/4/8 RHS 7.62/8.85/11.83 ->
+// 7.56/8.56/11.03 ms, bfloat16 2/4 RHS 11.35/11.57 -> 9.65/10.62 ms;
+// float-float and bfloat16 with 8 RHS were slower this way.
 constexpr int kFewRhs = 8;
 constexpr int kMultiRowsFew = 1024;
+__host__ __device__ constexpr bool few_rhs(int nrhs, int mode) {
+  return nrhs > 1 && ((mode == HODLR2D_MODE_F32 && nrhs <= kFewRhs) ||
+                      (mode == HODLR2D_MODE_BF16 && nrhs <= 4));
+}
 
 struct LevelV2 {
   const int32_t* px;
@@ -2372,14 +2380,14 @@ static bool box_as_pairs(const hodlr2d* h, int l, int nrhs, int mode) {
 // First level that is not run in two passes by a product:
 //   binary64                    lfuse (pairs from there on)
 //   several right-hand sides    l2max (boxes of <= kMultiRows points as pairs;
-//                               with <= kFewRhs, l2few: <= kMultiRowsFew)
+//                               few_rhs: l2few, boxes of <= kMultiRowsFew)
 //   one right-hand side         ldual (the 512 x 9 register forms hold the
 //                               boxes of [ldual, lfuse): two columns per
 //                               step in binary32, one in float-float)
 static int two_pass_end(const hodlr2d* h, int nrhs, int mode) {
   const V2Plan& V = h->v2;
   if (mode == HODLR2D_MODE_F64) return V.lfuse;
-  if (nrhs > 1) return nrhs <= kFewRhs ? V.l2few : V.l2max;
+  if (nrhs > 1) return few_rhs(nrhs, mode) ? V.l2few : V.l2max;
   return V.ldual;
 }
 
@@ -3034,7 +3042,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
       PhaseScope ps(h, 2, 1, fs * two_pass_vals + vs * npart * nrhs);
       ps.flops(2 * two_pass_vals * nrhs);
       const int64_t thr = npart * 32;  // one warp per (task, column)
-      if (std::is_same<A, BF16A>::value && nrhs > kFewRhs)  // tensor cores
+      if (std::is_same<A, BF16A>::value && nrhs > 1 && !few_rhs(nrhs, mode))  // tensor cores
         if (V.grp_ok)  // tasks grouped by box: x loaded once per group
           k_projg_t5<<<(unsigned)std::min<int64_t>(V.pre_grp[l2end], 3 * V.nsm), 256, kGrpSmem,
                        s>>>(P, V.d_proj, V.d_gtask, V.d_grp, V.pre_grp[l2end],
@@ -3076,7 +3084,7 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   if (nexp) {
     PhaseScope ps(h, 4, 1, fs * two_pass_vals + vb * (l2end - 1));
     ps.flops(2 * two_pass_vals * nrhs);
-    if (std::is_same<A, BF16A>::value && nrhs > kFewRhs)  // tensor cores
+    if (std::is_same<A, BF16A>::value && nrhs > 1 && !few_rhs(nrhs, mode))  // tensor cores
       k_exp_t5<<<(unsigned)std::min<int64_t>(nexp, 4 * V.nsm), 128, kT5Smem, s>>>(
           P, V.d_exp, nexp, reinterpret_cast<const float*>(V.d_t), reinterpret_cast<float*>(yl),
           V.d_status);

@@ -301,7 +301,7 @@ def test_register_pair_kernel_block_sizes(h2d, oracle, n):
     x2 = torch.stack([xd, xd], dim=1)
     # bound2: the two forms sum in different orders; float-float rounds each
     # operation to about 2^-44, binary32 to 2^-24; the bound of bfloat16
-    # also covers its tensor-core form (more than eight right-hand sides),
+    # also covers its tensor-core form (more than four right-hand sides),
     # which rounds x and t to two bfloat16 terms (about 2^-17)
     for mode, bound, bound2 in (("df32", 1e-12, 1e-12), ("f32", 5e-6, 1e-6), ("bf16", 2e-2, 1e-4)):
         g.prepare(mode)
