@@ -400,6 +400,7 @@ def extra_batch(pkg, inputs, stream, count=256):
     b.check()
     t_pers = e0.elapsed_time(e1) / 5
     phases = [round(v, 3) for v in b.phase_ms()]
+    recorded = b.persistent_recorded
     pers_vs_graph = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c))
                         for a, c in zip(yp, ys))
     for m in mats:
@@ -426,6 +427,7 @@ def extra_batch(pkg, inputs, stream, count=256):
             "factor_bytes_f32": 4 * far_values,
             "factor_read_once_ms_at_hbm_peak": round(4 * far_values / (hbm_gbs * 1e6), 3),
             "persistent_ms": round(t_pers, 3),
+            "persistent_launch_in_cuda_graph": recorded,
             "products_per_s_persistent": round(nprod / (t_pers * 1e-3), 1),
             "persistent_shapes": {"pair_rows": shapes[0], "warp_rows": shapes[1]},
             "persistent_tune_s": round(t_ptune, 2),

@@ -332,6 +332,11 @@ int hodlr2d_batch_check(hodlr2d_batch_t b);
 /* The form the last hodlr2d_batch_matvec ran (HODLR2D_BATCH_GRAPH or
  * HODLR2D_BATCH_PERSISTENT), or -1 before the first. */
 int hodlr2d_batch_last_form(hodlr2d_batch_t b);
+/* 1 if the persistent form's launch is recorded in a CUDA graph (stream
+ * capture of the cooperative launch, replayed with one graph launch), 0 if
+ * the driver refused the capture and it is launched directly, -1 before the
+ * first persistent product. */
+int hodlr2d_batch_persistent_recorded(hodlr2d_batch_t b);
 /* Work shapes of the persistent form by box size: the levels whose boxes
  * hold at most pair_rows points (0 <= pair_rows <= 2048; binary64 uses at
  * most 1024) run as pairs, each stored pair read once (t1 = V^T x_Y,

@@ -364,6 +364,13 @@ class Batch:
         f = self._lib.hodlr2d_batch_last_form(self._h)
         return {1: "graph", 2: "persistent"}.get(f)
 
+    @property
+    def persistent_recorded(self):
+        """True if the persistent launch is replayed from a CUDA graph, False if
+        it is launched directly, None before the first persistent product."""
+        r = self._lib.hodlr2d_batch_persistent_recorded(self._h)
+        return None if r < 0 else bool(r)
+
     def _args(self, xs, ys):
         n = len(self.mats)
         xa = (C.c_void_p * n)(*[x.data_ptr() for x in xs])

@@ -91,6 +91,7 @@ SIGNATURES = {
     "hodlr2d_batch_set_wait_limit": (C.c_int, [_P, C.c_uint32]),
     "hodlr2d_batch_check": (C.c_int, [_P]),
     "hodlr2d_batch_last_form": (C.c_int, [_P]),
+    "hodlr2d_batch_persistent_recorded": (C.c_int, [_P]),
     "hodlr2d_batch_set_shapes": (C.c_int, [_P, C.c_int, C.c_int]),
     "hodlr2d_batch_get_shapes": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "hodlr2d_batch_autotune": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int,

@@ -137,6 +137,12 @@ int hodlr2d_batch_set_wait_limit(hodlr2d_batch_t b, uint32_t polls) {
 
 int hodlr2d_batch_last_form(hodlr2d_batch_t b) { return b ? b->last_form : -1; }
 
+int hodlr2d_batch_persistent_recorded(hodlr2d_batch_t b) {
+  if (!b) return HODLR2D_ERR_ARG;
+  if (!b->bp.d_sets) return -1;
+  return b->pexec ? 1 : 0;
+}
+
 int hodlr2d_batch_check(hodlr2d_batch_t b) {
   if (!b) return HODLR2D_ERR_ARG;
   H2D_CK(cudaStreamSynchronize(b->stream));

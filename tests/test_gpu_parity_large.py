@@ -179,6 +179,8 @@ def test_batch_against_oracle(h2d, batch_sets, form, shapes, blocks, place):
             b.matvec(xd, ys, mode=mode)
             b.check()
             assert b.last_form == form
+            if form == "persistent":  # one cooperative launch, replayed from a CUDA graph
+                assert b.persistent_recorded is True
             for y, w in zip(ys, want):
                 assert rel(y.cpu().numpy().T, w) <= BOUND[mode], mode
     b.close()
