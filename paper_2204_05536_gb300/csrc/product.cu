@@ -52,6 +52,7 @@ constexpr int kFuseRows = H2D_FUSE_ROWS;  // largest box handled by the single-r
 constexpr int kSmallPair = 256;   // boxes up to this size: 64-thread pair blocks
 constexpr int kChunk2 = 256;      // rows of one expansion task of the two-pass levels
 constexpr int kExpMaxEnt = 64;    // largest list of a box (15 pairs, two sides, margin)
+constexpr int kExpQ = 64;         // t columns staged at a time (several right-hand sides)
 constexpr int kChunkP = 512;      // rows of one projection task (16 per lane)
 // Two-pass levels whose boxes hold at most kDualRows points (with ranks of
 // at most kDualKmax and at least two pairs per SM) also get a pair plan; products with one
@@ -1368,6 +1369,80 @@ __global__ void __launch_bounds__(256, 4)
   }
 }
 
+// Two-pass projection with binary32 sums and few right-hand sides: one warp
+// per (task, group of <= 8 columns) of the work list pg, kProjNR right-hand
+// sides per pass.  For each quarter of the task's rows (4 per lane) the
+// lanes hold x of the pass's right-hand sides in registers and stream the
+// group's columns, so each factor value is loaded once for kProjNR
+// multiply-adds and x once for 8 columns; the 8 x kProjNR sums of a lane end
+// in one reduce-scatter (31 additions).  Lane j kProjNR + c writes column q0 + j,
+// right-hand side c0 + c, where k_proj2 puts it.
+constexpr int kProjNR = 4;
+template <class A>
+__global__ void __launch_bounds__(256, 3)
+    k_projn(ArgsV2 P, const ProjTask* __restrict__ tasks, const int2* __restrict__ pg,
+            int64_t ngroups, const typename A::val* __restrict__ xt,
+            typename A::val* __restrict__ part) {
+  using V = typename A::val;
+  using F = typename A::fac;
+  using Acc = typename A::acc;
+  constexpr int H = kChunkP / 128;  // rows per lane and quarter
+  constexpr int NC = kProj64Cols;
+  constexpr int NV = NC * kProjNR;
+  static_assert(NV == 32, "one sum per lane");
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (w >= ngroups) return;
+  const int2 g = pg[w];
+  const ProjTask T = tasks[g.x];
+  const int q0 = g.y, k = T.k;
+  const int c = min(NC, k - q0);
+  const F* mat = reinterpret_cast<const F*>(P.lev[T.level].fac) + T.mat + (int64_t)q0 * T.ld +
+                 T.r0;
+  const V* xb = xt + T.base + T.r0;
+  for (int c0 = 0; c0 < P.nrhs; c0 += kProjNR) {
+    const int nc = min(kProjNR, P.nrhs - c0);
+    Acc acc[NC][kProjNR];
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+#pragma unroll
+      for (int rr = 0; rr < kProjNR; ++rr) acc[j][rr] = A::zero();
+#pragma unroll 1
+    for (int hf = 0; hf < 4; ++hf) {
+      const int rb = 32 * H * hf;  // first row of the quarter, relative to r0
+      if (rb >= T.nr) break;       // uniform
+      V xr[H][kProjNR];
+#pragma unroll
+      for (int u = 0; u < H; ++u) {
+        const int r = rb + lane + 32 * u;
+#pragma unroll
+        for (int rr = 0; rr < kProjNR; ++rr)
+          xr[u][rr] = r < T.nr && rr < nc ? xb[(int64_t)(c0 + rr) * P.n + r] : A::vzero();
+      }
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        if (j >= c) continue;
+        const F* col = mat + (int64_t)j * T.ld + rb + lane;
+#pragma unroll
+        for (int u = 0; u < H; ++u) {
+          if (rb + 32 * u >= T.nr) continue;  // uniform
+          const V v = rb + lane + 32 * u < T.nr ? A::ld(col[32 * u]) : A::vzero();
+#pragma unroll
+          for (int rr = 0; rr < kProjNR; ++rr) A::fma(acc[j][rr], v, xr[u][rr]);
+        }
+      }
+    }
+    V sv[NV];
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+#pragma unroll
+      for (int rr = 0; rr < kProjNR; ++rr) sv[j * kProjNR + rr] = A::fin(acc[j][rr]);
+    const V tot = warp_reduce_scatter<A, NV>(sv, lane);
+    const int j = lane / kProjNR, rr = lane % kProjNR;
+    if (j < c && rr < nc) part[T.out * P.nrhs + (int64_t)(c0 + rr) * k + q0 + j] = tot;
+  }
+}
+
 // Chunk sums of the two-pass levels in binary64 for pair sides of at most
 // kTsumThread chunks: one thread per (pair side, column), the chunk partials
 // added in chunk order (no cross-lane sums); sides of more chunks are left
@@ -2237,39 +2312,56 @@ __device__ __forceinline__ void exp2_body(const ArgsV2& P, const ExpTask* __rest
   }
   __syncthreads();
   const int r = T.r0 + (int)threadIdx.x;
-  if (r >= T.r0 + T.nr) return;
+  const bool act = r < T.r0 + T.nr;
   const int32_t base = bstart(P.leaf_off, P.kappa, l, X);
   const int64_t ld = ldpad(bsize(P.leaf_off, P.kappa, l, X));
   const F* fac = reinterpret_cast<const F*>(L.fac);
   if (P.nrhs > 1) {  // EC right-hand sides per pass: each factor value loaded once per pass
+    // the pass's t values of an entry are staged in shared memory, kExpQ
+    // columns at a time, right-hand sides adjacent: one shared vector read
+    // serves all EC sums of a factor value (the whole block takes part)
     constexpr int EC = sizeof(typename A::acc) == 4 ? 8 : 4;
+    __shared__ __align__(16) V s_t[kExpQ][EC];
     for (int c0 = 0; c0 < P.nrhs; c0 += EC) {
+      const int nc = min(EC, P.nrhs - c0);
       Acc a[EC];
 #pragma unroll
       for (int c = 0; c < EC; ++c) a[c] = A::zero();
       for (int e = 0; e < ne; ++e) {
         const int k = s_k[e];
-        const F* M = fac + s_off[e] + r;
+        const F* M = fac + s_off[e] + (act ? r : T.r0);
         const V* tv = t + s_toff[e];
+        for (int q0 = 0; q0 < k; q0 += kExpQ) {
+          const int qn = min(kExpQ, k - q0);
+          __syncthreads();  // the previous columns are used up
+          for (int i = threadIdx.x; i < EC * qn; i += blockDim.x) {
+            const int c = i / qn, q = i - c * qn;
+            s_t[q][c] = c < nc ? tv[(int64_t)(c0 + c) * k + q0 + q] : A::vzero();
+          }
+          __syncthreads();
+          if (!act) continue;
 #pragma unroll 4
-        for (int q = 0; q < k; ++q) {
-          const V mv = A::ld(M[q * ld]);
+          for (int q = 0; q < qn; ++q) {
+            const V mv = A::ld(M[(int64_t)(q0 + q) * ld]);
 #pragma unroll
-          for (int c = 0; c < EC; ++c)
-            if (c0 + c < P.nrhs) A::fma(a[c], mv, tv[(int64_t)(c0 + c) * k + q]);
-          if ((q + 1) % kRenorm == 0)
+            for (int c = 0; c < EC; ++c)
+              if (c < nc) A::fma(a[c], mv, s_t[q][c]);
+            if ((q0 + q + 1) % kRenorm == 0)
 #pragma unroll
-            for (int c = 0; c < EC; ++c) A::renorm(a[c]);
+              for (int c = 0; c < EC; ++c) A::renorm(a[c]);
+          }
         }
 #pragma unroll
         for (int c = 0; c < EC; ++c) A::renorm(a[c]);
       }
+      if (act)
 #pragma unroll
-      for (int c = 0; c < EC; ++c)
-        if (c0 + c < P.nrhs) yl[((int64_t)l * P.nrhs + c0 + c) * P.n + base + r] = A::fin(a[c]);
+        for (int c = 0; c < EC; ++c)
+          if (c < nc) yl[((int64_t)l * P.nrhs + c0 + c) * P.n + base + r] = A::fin(a[c]);
     }
     return;
   }
+  if (!act) return;
   for (int c = 0; c < P.nrhs; ++c) {
     Acc a = A::zero();
     for (int e = 0; e < ne; ++e) {
@@ -2539,7 +2631,8 @@ static int build_two_pass(hodlr2d* h, int lmax) {
     if (!grp.empty())
       H2D_CK(cudaMemcpy(V.d_grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice));
   }
-  {  // binary64 projection work: (task, first column) per group of kProj64Cols columns
+  {  // grouped projection work (binary64; binary32 sums with few right-hand sides):
+     // (task, first column) per group of kProj64Cols columns
     std::vector<int2> pg;
     for (int64_t t = 0; t < (int64_t)proj.size(); ++t) {
       for (int q0 = 0; q0 < proj[t].k; q0 += kProj64Cols) pg.push_back(make_int2((int)t, q0));
@@ -3055,6 +3148,13 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
       else if (nrhs >= 24 && sizeof(Val) == 4)  // binary32 sums: tiled over many right-hand sides
         k_projm<A><<<(unsigned)nproj, 256, 0, s>>>(P, V.d_proj, xt,
                                                    reinterpret_cast<Val*>(V.d_part));
+      else if (nrhs > 1 && sizeof(typename A::acc) == 4) {  // few: column groups, x in registers
+        if constexpr (sizeof(typename A::acc) == 4) {
+          const int64_t ng = V.pre_pgrp[l2end];
+          k_projn<A><<<(unsigned)((ng * 32 + 255) / 256), 256, 0, s>>>(
+              P, V.d_proj, V.d_pgrp, ng, xt, reinterpret_cast<Val*>(V.d_part));
+        }
+      }
       else if (std::is_same<A, F64A>::value) {  // binary64: column groups, halving exchange
         const int64_t ng = V.pre_pgrp[l2end];
         k_proj64<<<(unsigned)((ng * 32 + 255) / 256), 256, 0, s>>>(
