@@ -1371,22 +1371,25 @@ __global__ void __launch_bounds__(256, 4)
 
 // Two-pass projection with binary32 sums and few right-hand sides: one warp
 // per (task, group of <= 8 columns) of the work list pg, kProjNR right-hand
-// sides per pass.  For each quarter of the task's rows (4 per lane) the
-// lanes hold x of the pass's right-hand sides in registers and stream the
-// group's columns, so each factor value is loaded once for kProjNR
-// multiply-adds and x once for 8 columns; the 8 x kProjNR sums of a lane end
-// in one reduce-scatter (31 additions).  Lane j kProjNR + c writes column q0 + j,
+// sides per pass.  For each half of the task's rows (8 per lane) the lanes
+// hold x of the pass's right-hand sides in registers and stream the group's
+// columns, so each factor value is loaded once for kProjNR multiply-adds and
+// x once for 8 columns; the 8 x kProjNR sums of a lane end in one
+// reduce-scatter (31 additions).  Both halves are unrolled (up to 128 factor
+// loads in flight per warp) at 128 registers: the quartered, 80-register
+// form was latency-bound (ncu at N = 2^17, 4 RHS: 29% warps active, long
+// scoreboard stalls, 9% of DRAM).  Lane j kProjNR + c writes column q0 + j,
 // right-hand side c0 + c, where k_proj2 puts it.
 constexpr int kProjNR = 4;
 template <class A>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 2)
     k_projn(ArgsV2 P, const ProjTask* __restrict__ tasks, const int2* __restrict__ pg,
             int64_t ngroups, const typename A::val* __restrict__ xt,
             typename A::val* __restrict__ part) {
   using V = typename A::val;
   using F = typename A::fac;
   using Acc = typename A::acc;
-  constexpr int H = kChunkP / 128;  // rows per lane and quarter
+  constexpr int H = kChunkP / 64;  // rows per lane and half
   constexpr int NC = kProj64Cols;
   constexpr int NV = NC * kProjNR;
   static_assert(NV == 32, "one sum per lane");
@@ -1407,9 +1410,9 @@ __global__ void __launch_bounds__(256, 3)
     for (int j = 0; j < NC; ++j)
 #pragma unroll
       for (int rr = 0; rr < kProjNR; ++rr) acc[j][rr] = A::zero();
-#pragma unroll 1
-    for (int hf = 0; hf < 4; ++hf) {
-      const int rb = 32 * H * hf;  // first row of the quarter, relative to r0
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      const int rb = 32 * H * hf;  // first row of the half, relative to r0
       if (rb >= T.nr) break;       // uniform
       V xr[H][kProjNR];
 #pragma unroll
@@ -2316,10 +2319,12 @@ __device__ __forceinline__ void exp2_body(const ArgsV2& P, const ExpTask* __rest
   const int32_t base = bstart(P.leaf_off, P.kappa, l, X);
   const int64_t ld = ldpad(bsize(P.leaf_off, P.kappa, l, X));
   const F* fac = reinterpret_cast<const F*>(L.fac);
-  if (P.nrhs > 1) {  // EC right-hand sides per pass: each factor value loaded once per pass
+  if (sizeof(F) == 2 && P.nrhs > 1) {  // bfloat16 factors, several right-hand sides:
     // the pass's t values of an entry are staged in shared memory, kExpQ
     // columns at a time, right-hand sides adjacent: one shared vector read
-    // serves all EC sums of a factor value (the whole block takes part)
+    // serves all EC sums of a factor value (the whole block takes part).
+    // Measured at N = 2^20, 4 RHS: bfloat16 3.07 -> 1.42 ms; binary32 1.63 ->
+    // 2.37 and float-float 3.81 -> 4.51 ms, so those keep the direct loads.
     constexpr int EC = sizeof(typename A::acc) == 4 ? 8 : 4;
     __shared__ __align__(16) V s_t[kExpQ][EC];
     for (int c0 = 0; c0 < P.nrhs; c0 += EC) {
@@ -2362,6 +2367,35 @@ __device__ __forceinline__ void exp2_body(const ArgsV2& P, const ExpTask* __rest
     return;
   }
   if (!act) return;
+  if (P.nrhs > 1) {  // EC right-hand sides per pass: each factor value loaded once per pass
+    constexpr int EC = sizeof(typename A::acc) == 4 ? 8 : 4;
+    for (int c0 = 0; c0 < P.nrhs; c0 += EC) {
+      Acc a[EC];
+#pragma unroll
+      for (int c = 0; c < EC; ++c) a[c] = A::zero();
+      for (int e = 0; e < ne; ++e) {
+        const int k = s_k[e];
+        const F* M = fac + s_off[e] + r;
+        const V* tv = t + s_toff[e];
+#pragma unroll 4
+        for (int q = 0; q < k; ++q) {
+          const V mv = A::ld(M[q * ld]);
+#pragma unroll
+          for (int c = 0; c < EC; ++c)
+            if (c0 + c < P.nrhs) A::fma(a[c], mv, tv[(int64_t)(c0 + c) * k + q]);
+          if ((q + 1) % kRenorm == 0)
+#pragma unroll
+            for (int c = 0; c < EC; ++c) A::renorm(a[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < EC; ++c) A::renorm(a[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < EC; ++c)
+        if (c0 + c < P.nrhs) yl[((int64_t)l * P.nrhs + c0 + c) * P.n + base + r] = A::fin(a[c]);
+    }
+    return;
+  }
   for (int c = 0; c < P.nrhs; ++c) {
     Acc a = A::zero();
     for (int e = 0; e < ne; ++e) {
