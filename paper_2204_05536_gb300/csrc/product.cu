@@ -1369,83 +1369,6 @@ __global__ void __launch_bounds__(256, 4)
   }
 }
 
-// Two-pass projection with binary32 sums and few right-hand sides: one warp
-// per (task, group of <= 8 columns) of the work list pg, kProjNR right-hand
-// sides per pass.  For each half of the task's rows (8 per lane) the lanes
-// hold x of the pass's right-hand sides in registers and stream the group's
-// columns, so each factor value is loaded once for kProjNR multiply-adds and
-// x once for 8 columns; the 8 x kProjNR sums of a lane end in one
-// reduce-scatter (31 additions).  Both halves are unrolled (up to 128 factor
-// loads in flight per warp) at 128 registers: the quartered, 80-register
-// form was latency-bound (ncu at N = 2^17, 4 RHS: 29% warps active, long
-// scoreboard stalls, 9% of DRAM).  Lane j kProjNR + c writes column q0 + j,
-// right-hand side c0 + c, where k_proj2 puts it.
-constexpr int kProjNR = 4;
-template <class A>
-__global__ void __launch_bounds__(256, 2)
-    k_projn(ArgsV2 P, const ProjTask* __restrict__ tasks, const int2* __restrict__ pg,
-            int64_t ngroups, const typename A::val* __restrict__ xt,
-            typename A::val* __restrict__ part) {
-  using V = typename A::val;
-  using F = typename A::fac;
-  using Acc = typename A::acc;
-  constexpr int H = kChunkP / 64;  // rows per lane and half
-  constexpr int NC = kProj64Cols;
-  constexpr int NV = NC * kProjNR;
-  static_assert(NV == 32, "one sum per lane");
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (w >= ngroups) return;
-  const int2 g = pg[w];
-  const ProjTask T = tasks[g.x];
-  const int q0 = g.y, k = T.k;
-  const int c = min(NC, k - q0);
-  const F* mat = reinterpret_cast<const F*>(P.lev[T.level].fac) + T.mat + (int64_t)q0 * T.ld +
-                 T.r0;
-  const V* xb = xt + T.base + T.r0;
-  for (int c0 = 0; c0 < P.nrhs; c0 += kProjNR) {
-    const int nc = min(kProjNR, P.nrhs - c0);
-    Acc acc[NC][kProjNR];
-#pragma unroll
-    for (int j = 0; j < NC; ++j)
-#pragma unroll
-      for (int rr = 0; rr < kProjNR; ++rr) acc[j][rr] = A::zero();
-#pragma unroll
-    for (int hf = 0; hf < 2; ++hf) {
-      const int rb = 32 * H * hf;  // first row of the half, relative to r0
-      if (rb >= T.nr) break;       // uniform
-      V xr[H][kProjNR];
-#pragma unroll
-      for (int u = 0; u < H; ++u) {
-        const int r = rb + lane + 32 * u;
-#pragma unroll
-        for (int rr = 0; rr < kProjNR; ++rr)
-          xr[u][rr] = r < T.nr && rr < nc ? xb[(int64_t)(c0 + rr) * P.n + r] : A::vzero();
-      }
-#pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        if (j >= c) continue;
-        const F* col = mat + (int64_t)j * T.ld + rb + lane;
-#pragma unroll
-        for (int u = 0; u < H; ++u) {
-          if (rb + 32 * u >= T.nr) continue;  // uniform
-          const V v = rb + lane + 32 * u < T.nr ? A::ld(col[32 * u]) : A::vzero();
-#pragma unroll
-          for (int rr = 0; rr < kProjNR; ++rr) A::fma(acc[j][rr], v, xr[u][rr]);
-        }
-      }
-    }
-    V sv[NV];
-#pragma unroll
-    for (int j = 0; j < NC; ++j)
-#pragma unroll
-      for (int rr = 0; rr < kProjNR; ++rr) sv[j * kProjNR + rr] = A::fin(acc[j][rr]);
-    const V tot = warp_reduce_scatter<A, NV>(sv, lane);
-    const int j = lane / kProjNR, rr = lane % kProjNR;
-    if (j < c && rr < nc) part[T.out * P.nrhs + (int64_t)(c0 + rr) * k + q0 + j] = tot;
-  }
-}
-
 // Chunk sums of the two-pass levels in binary64 for pair sides of at most
 // kTsumThread chunks: one thread per (pair side, column), the chunk partials
 // added in chunk order (no cross-lane sums); sides of more chunks are left
@@ -2665,8 +2588,7 @@ static int build_two_pass(hodlr2d* h, int lmax) {
     if (!grp.empty())
       H2D_CK(cudaMemcpy(V.d_grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice));
   }
-  {  // grouped projection work (binary64; binary32 sums with few right-hand sides):
-     // (task, first column) per group of kProj64Cols columns
+  {  // binary64 projection work: (task, first column) per group of kProj64Cols columns
     std::vector<int2> pg;
     for (int64_t t = 0; t < (int64_t)proj.size(); ++t) {
       for (int q0 = 0; q0 < proj[t].k; q0 += kProj64Cols) pg.push_back(make_int2((int)t, q0));
@@ -3182,13 +3104,6 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
       else if (nrhs >= 24 && sizeof(Val) == 4)  // binary32 sums: tiled over many right-hand sides
         k_projm<A><<<(unsigned)nproj, 256, 0, s>>>(P, V.d_proj, xt,
                                                    reinterpret_cast<Val*>(V.d_part));
-      else if (nrhs > 1 && sizeof(typename A::acc) == 4) {  // few: column groups, x in registers
-        if constexpr (sizeof(typename A::acc) == 4) {
-          const int64_t ng = V.pre_pgrp[l2end];
-          k_projn<A><<<(unsigned)((ng * 32 + 255) / 256), 256, 0, s>>>(
-              P, V.d_proj, V.d_pgrp, ng, xt, reinterpret_cast<Val*>(V.d_part));
-        }
-      }
       else if (std::is_same<A, F64A>::value) {  // binary64: column groups, halving exchange
         const int64_t ng = V.pre_pgrp[l2end];
         k_proj64<<<(unsigned)((ng * 32 + 255) / 256), 256, 0, s>>>(
