@@ -85,8 +85,9 @@ struct ProjTask {
 // Pair-mode work of one level: (level, pair) of every stored pair of rank > 0,
 // sorted into size classes by max(|X|, |Y|) (bounds kPairClassRows), so that
 // each class runs with a block shape fitted to its boxes.
-constexpr int kPairClasses = 9;
-constexpr int kPairClassRows[kPairClasses] = {48, 64, 128, 256, 384, 1280, 2560, 4608, 1 << 30};
+constexpr int kPairClasses = 11;
+constexpr int kPairClassRows[kPairClasses] = {16,  32,   48,   64,   128, 256,
+                                              384, 1280, 2560, 4608, 1 << 30};
 struct PairLevel {
   int2* d_work = nullptr;              // all classes, class by class
   int64_t nwork = 0;

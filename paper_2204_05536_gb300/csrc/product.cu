@@ -927,6 +927,134 @@ __global__ void __launch_bounds__(T)
   pairm_body<A, T, RM, NR>(P, work[blockIdx.x], xt, ppart, threadIdx.x);
 }
 
+// Sub-warp form of k_pairm for small boxes (binary32 sums): S lanes per pair
+// (S = 8 or 16), 32 / S pairs per warp, the items item0, item0 + 1, ... of
+// the work list; lane s of a segment takes rows s, s + S, ... (RM of them)
+// of X and of Y.  The column loop runs to the largest rank of the warp's
+// pairs (columns beyond a pair's own rank add zeros); the 2 NR sums of a
+// column reduce within the segment (reduce-scatter over S lanes) and come
+// back from the lanes that hold them.
+template <class A, int S, int RM, int NR>
+__device__ __forceinline__ void pairms_body(const ArgsV2& P, const int2* __restrict__ work,
+                                            int64_t nwork,
+                                            const typename A::val* __restrict__ xt,
+                                            typename A::val* __restrict__ ppart, int64_t item0) {
+  using V = typename A::val;
+  using F = typename A::fac;
+  using Acc = typename A::acc;
+  constexpr int NV = 2 * NR;
+  static_assert(NV <= S && S <= 32, "one sum per lane of a segment at least");
+  constexpr int SH = ilog2c(S) - ilog2c(NV);
+  const int lane = threadIdx.x & 31, g = lane / S, sl = lane % S, sbase = g * S;
+  const int64_t it = item0 + g;
+  int m = 0, n = 0, k = 0;
+  int64_t lm = 0, ln = 0, ppx = 0, ppy = 0;
+  int32_t xs = 0, ys = 0;
+  const F* Ug = nullptr;
+  const F* Vg = nullptr;
+  if (it < nwork) {
+    const int2 wk = work[it];
+    const LevelV2& L = P.lev[wk.x];
+    const PairMeta PM = L.meta[wk.y];
+    m = PM.m;
+    n = PM.n;
+    k = PM.k;
+    lm = ldpad(m);
+    ln = ldpad(n);
+    xs = PM.xs;
+    ys = PM.ys;
+    ppx = PM.ppx;
+    ppy = PM.ppy;
+    Ug = reinterpret_cast<const F*>(L.fac) + PM.foff;
+    Vg = Ug + lm * k;
+  }
+  int kmax = k;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  for (int c0 = 0; c0 < P.nrhs; c0 += NR) {
+    V xX[RM][NR], xY[RM][NR];
+    Acc yX[RM][NR], yY[RM][NR];
+#pragma unroll
+    for (int a = 0; a < RM; ++a) {
+      const int i = sl + a * S;
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        const bool ok = c0 + c < P.nrhs;
+        const V* xc = xt + (int64_t)(c0 + c) * P.n;
+        xX[a][c] = (ok && i < m) ? xc[xs + i] : A::vzero();
+        xY[a][c] = (ok && i < n) ? xc[ys + i] : A::vzero();
+        yX[a][c] = A::zero();
+        yY[a][c] = A::zero();
+      }
+    }
+    F u[RM], v[RM];  // column q + 1 is loaded while column q is reduced
+#pragma unroll
+    for (int a = 0; a < RM; ++a) {
+      const int i = sl + a * S;
+      u[a] = i < m && k > 0 ? Ug[i] : fac_zero<F>();
+      v[a] = i < n && k > 0 ? Vg[i] : fac_zero<F>();
+    }
+    for (int q = 0; q < kmax; ++q) {
+      F un[RM], vn[RM];
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        const int i = sl + a * S;
+        un[a] = i < m && q + 1 < k ? Ug[(int64_t)(q + 1) * lm + i] : fac_zero<F>();
+        vn[a] = i < n && q + 1 < k ? Vg[(int64_t)(q + 1) * ln + i] : fac_zero<F>();
+      }
+      V sv[NV];  // sv[c]: partial t1 of RHS c (V), sv[NR + c]: partial t2 (U)
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        Acc a1 = A::zero(), a2 = A::zero();
+#pragma unroll
+        for (int a = 0; a < RM; ++a) {
+          A::fma(a1, A::ld(v[a]), xY[a][c]);
+          A::fma(a2, A::ld(u[a]), xX[a][c]);
+        }
+        sv[c] = A::fin(a1);
+        sv[NR + c] = A::fin(a2);
+      }
+      const V mine = warp_reduce_scatter<A, NV, S>(sv, lane);
+      V t[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) t[c] = shfl_idx(mine, sbase + (c << SH));
+#pragma unroll
+      for (int c = 0; c < NR; ++c)
+#pragma unroll
+        for (int a = 0; a < RM; ++a) {
+          A::fma(yX[a][c], A::ld(u[a]), t[c]);       // U with t1
+          A::fma(yY[a][c], A::ld(v[a]), t[NR + c]);  // V with t2
+        }
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        u[a] = un[a];
+        v[a] = vn[a];
+      }
+    }
+    if (it >= nwork) continue;
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      if (c0 + c >= P.nrhs) break;
+      V* outx = ppart + (int64_t)(c0 + c) * P.pstride + ppx;
+      V* outy = ppart + (int64_t)(c0 + c) * P.pstride + ppy;
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        const int i = sl + a * S;
+        if (i < m) outx[i] = A::fin(yX[a][c]);
+        if (i < n) outy[i] = A::fin(yY[a][c]);
+      }
+    }
+  }
+}
+constexpr int kPairmsWarps = 4;
+template <class A, int S, int RM, int NR>
+__global__ void __launch_bounds__(32 * kPairmsWarps)
+    k_pairms(ArgsV2 P, const int2* __restrict__ work, int64_t nwork,
+             const typename A::val* __restrict__ xt, typename A::val* __restrict__ ppart) {
+  pairms_body<A, S, RM, NR>(P, work, nwork, xt, ppart,
+                            ((int64_t)blockIdx.x * kPairmsWarps + (threadIdx.x >> 5)) * (32 / S));
+}
+
 // Sub-warp form of k_pairg for the finest levels (boxes of <= kBoxRows
 // points): S lanes per pair, 32 / S pairs per warp, rows t, t + S, ... (at
 // most RM) of X and Y per lane.  The column loop runs to the largest rank of
@@ -2947,9 +3075,18 @@ template <class A>
 static int launch_pair_multi(const int2* work, int64_t nw, int rows, const ArgsV2& P,
                              const typename A::val* xt, typename A::val* ppart,
                              cudaStream_t st) {
-  constexpr int NR = sizeof(typename A::acc) == 4 ? 8 : 4;  // right-hand sides per pass
+  constexpr bool b32 = sizeof(typename A::acc) == 4;
+  constexpr int NR = b32 ? 8 : 4;  // right-hand sides per pass
   const unsigned nb = (unsigned)nw;
-  if (rows <= 64)
+  if (b32 && rows <= 16) {  // four pairs per warp
+    if constexpr (b32)
+      k_pairms<A, 8, 2, 4><<<(unsigned)((nw + 4 * kPairmsWarps - 1) / (4 * kPairmsWarps)),
+                             32 * kPairmsWarps, 0, st>>>(P, work, nw, xt, ppart);
+  } else if (b32 && rows <= 32) {  // two pairs per warp
+    if constexpr (b32)
+      k_pairms<A, 16, 2, 4><<<(unsigned)((nw + 2 * kPairmsWarps - 1) / (2 * kPairmsWarps)),
+                              32 * kPairmsWarps, 0, st>>>(P, work, nw, xt, ppart);
+  } else if (rows <= 64)
     k_pairm<A, 32, 2, NR><<<nb, 32, 0, st>>>(P, work, xt, ppart);
   else if (rows <= 128)
     k_pairm<A, 64, 2, NR><<<nb, 64, 0, st>>>(P, work, xt, ppart);
@@ -2965,10 +3102,60 @@ static int launch_pair_multi(const int2* work, int64_t nw, int rows, const ArgsV
   return HODLR2D_OK;
 }
 
-// Runs the pairs of level l, one launch per non-empty size class: k_pairg /
-// k_pairs (each factor value read once) for one right-hand side, block shape
-// by the class's largest box; k_pairm for several right-hand sides; k_pair for
-// binary64 sums (its shuffle-free second phase suits the slow binary64 pipe).
+// Which kernel form the launchers above pick for a size class of boxes of at
+// most `rows` points (their branch conditions, in order): consecutive
+// classes of the same form share one launch.
+template <class A>
+static int pair_form(int rows, int nrhs) {
+  if constexpr (std::is_same<A, F64A>::value) return rows <= kSmallPair ? 100 : 101;
+  constexpr bool b32 = sizeof(typename A::acc) == 4;
+  if (nrhs == 1) {
+    const int lim[8] = {48, 64, 128, 256, 384, 1280, 2560, kDualRows};
+    for (int i = 0; i < 8; ++i)
+      if (rows <= lim[i]) return i;
+    return rows <= kSmallPair ? 100 : 101;
+  }
+  if (b32 && rows <= 16) return 10;
+  if (b32 && rows <= 32) return 11;
+  if (rows <= 64) return 12;
+  if (rows <= 128) return 13;
+  if (rows <= kMultiRows) return 14;
+  if (rows <= 512 && nrhs <= kFewRhs) return 15;
+  if (rows <= kMultiRowsFew && nrhs <= kFewRhs) return 16;
+  return rows <= kSmallPair ? 100 : 101;
+}
+
+// Runs of consecutive size classes with one form (empty classes join any
+// run): calls f(first work item, items, largest box) once per run and
+// returns the number of runs.
+template <class A, class Fn>
+static int pair_runs(const PairLevel& G, int nrhs, Fn&& f) {
+  int runs = 0;
+  for (int c = 0; c < kPairClasses;) {
+    if (G.off[c + 1] == G.off[c]) {
+      ++c;
+      continue;
+    }
+    const int form = pair_form<A>(G.cls_rows[c], nrhs);
+    int rows = G.cls_rows[c], c2 = c + 1;
+    while (c2 < kPairClasses && (G.off[c2 + 1] == G.off[c2] ||
+                                 pair_form<A>(G.cls_rows[c2], nrhs) == form)) {
+      if (G.off[c2 + 1] > G.off[c2]) rows = std::max(rows, G.cls_rows[c2]);
+      ++c2;
+    }
+    const int rc = f(G.off[c], G.off[c2] - G.off[c], rows);
+    if (rc) return rc < 0 ? rc : -1;
+    ++runs;
+    c = c2;
+  }
+  return runs;
+}
+
+// Runs the pairs of level l, one launch per run of size classes of one form:
+// k_pairg / k_pairs (each factor value read once) for one right-hand side,
+// block shape by the run's largest box; k_pairm / k_pairms for several
+// right-hand sides; k_pair for binary64 sums (its shuffle-free second phase
+// suits the slow binary64 pipe).
 template <class A>
 static int launch_pairs(hodlr2d* h, int l, const ArgsV2& P, const typename A::val* xt,
                         typename A::val* ppart, cudaStream_t st) {
@@ -2983,20 +3170,16 @@ static int launch_pairs(hodlr2d* h, int l, const ArgsV2& P, const typename A::va
       return HODLR2D_OK;
     }
   }
-  for (int c = 0; c < kPairClasses; ++c) {
-    const int64_t nw = G.off[c + 1] - G.off[c];
-    if (nw == 0) continue;
-    const int2* work = G.d_work + G.off[c];
-    const int rows = G.cls_rows[c];
-    if constexpr (std::is_same<A, F64A>::value) {  // binary64: warp per column, two reads
-      H2D_TRY(launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st));
-    } else if (P.nrhs == 1) {
-      H2D_TRY(launch_pair_reg<A>(work, nw, rows, P, xt, ppart, st));
-    } else {
-      H2D_TRY(launch_pair_multi<A>(work, nw, rows, P, xt, ppart, st));
-    }
-  }
-  return HODLR2D_OK;
+  const int runs = pair_runs<A>(G, P.nrhs, [&](int64_t first, int64_t nw, int rows) {
+    const int2* work = G.d_work + first;
+    if constexpr (std::is_same<A, F64A>::value)  // binary64: warp per column, two reads
+      return launch_pair_plain<A>(work, nw, rows, P, xt, ppart, st);
+    else if (P.nrhs == 1)
+      return launch_pair_reg<A>(work, nw, rows, P, xt, ppart, st);
+    else
+      return launch_pair_multi<A>(work, nw, rows, P, xt, ppart, st);
+  });
+  return runs < 0 ? runs : HODLR2D_OK;
 }
 
 // The near field with one right-hand side per pass, or NM per pass for
@@ -3149,8 +3332,8 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
   for (int l = l2end; l <= h->kappa; ++l) {
     if (P.lmode[l] != LMODE_PAIR || V.plev[l].nwork == 0) continue;
     const int phase = V.lmode[l] == LMODE_BOX ? 7 : l < V.lpair_small ? 6 : 8;
-    int nlaunch = 0;  // one launch per non-empty size class (binary64: one per level)
-    for (int c = 0; c < kPairClasses; ++c) nlaunch += V.plev[l].off[c + 1] > V.plev[l].off[c];
+    // one launch per run of size classes of one form (binary64 small boxes: one per level)
+    int nlaunch = pair_runs<A>(V.plev[l], nrhs, [](int64_t, int64_t, int) { return 0; });
     if (std::is_same<A, F64A>::value && V.plev[l].max_rows <= kP64Rows &&
         h->lev[l].max_rank <= kP64Kmax)
       nlaunch = 1;
