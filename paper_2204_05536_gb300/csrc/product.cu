@@ -3390,11 +3390,14 @@ static int run_v2(hodlr2d* h, const double* x, double* y, int nrhs, int mode) {
 // largest box of a one-pair-per-unit item: 2048 points (8 rows a thread,
 // one right-hand side per pass) for 4-byte sums, 1024 for binary64
 constexpr int kBatchBlockRows = 2048;
+constexpr int kBatchWarp = 5, kBatchW16 = 6, kBatchW8 = 7;  // the warp-level pair kinds
 // pair items by the box size they take, largest first: one per unit with
 // 8, 4 or 2 rows a thread, two per unit (128 threads each), four per unit
 // (64 threads each), one per warp
-constexpr int kBatchPairKinds = 6;
-constexpr int kBatchKindRows[kBatchPairKinds - 1] = {2048, 1024, 512, 256, 128};
+constexpr int kBatchPairKinds = 8;
+// (the last three kinds take pairs of at most warp_rows points: a warp, or
+// 2 or 4 pairs per warp for boxes of at most 32 or 16 points)
+constexpr int kBatchKindRows[kBatchPairKinds - 3] = {2048, 1024, 512, 256, 128};
 
 struct BatchSet {
   ArgsV2 P;                   // LMODE_TWO below the first pair level, LMODE_PAIR from it on
@@ -3477,6 +3480,8 @@ enum BatchKind {
   BK_PROJ,        // eight projection warps
   BK_NEAR,        // eight near-field warps
   BK_WARP,        // eight pairs of at most warp_rows points (a warp each)
+  BK_W16,         // sixteen pairs of at most 32 points (16 lanes each)
+  BK_W8,          // thirty-two pairs of at most 16 points (8 lanes each)
   BK_TSUM,        // eight chunk-sum warps
   BK_EXP,         // one expansion task
   BK_COMBINE,     // 256 points
@@ -3549,11 +3554,27 @@ __device__ __forceinline__ void batch_unit(const BatchSet& S, int kind, int64_t 
       return;
     }
     case BK_WARP: {
-      const int64_t j = S.p0[5] + lv * 8 + warp;
-      if (j >= S.p0[6]) return;
+      const int64_t j = S.p0[kBatchWarp] + lv * 8 + warp;
+      if (j >= S.p0[kBatchWarp + 1]) return;
       const int2 wk = S.pwork[j];
       if (one) pairm_body<A, 32, 2, 1>(S.P, wk, xt, ppart, lane);
       else pairm_body<A, 32, 2, NRM>(S.P, wk, xt, ppart, lane);
+      return;
+    }
+    case BK_W16: {
+      const int2* w = S.pwork + S.p0[kBatchW16];
+      const int64_t nw = S.p0[kBatchW16 + 1] - S.p0[kBatchW16], i0 = (lv * 8 + warp) * 2;
+      if (i0 >= nw) return;  // uniform in the warp
+      if (one) pairms_body<A, 16, 2, 1>(S.P, w, nw, xt, ppart, i0);
+      else pairms_body<A, 16, 2, NRM>(S.P, w, nw, xt, ppart, i0);
+      return;
+    }
+    case BK_W8: {
+      const int2* w = S.pwork + S.p0[kBatchW8];
+      const int64_t nw = S.p0[kBatchW8 + 1] - S.p0[kBatchW8], i0 = (lv * 8 + warp) * 4;
+      if (i0 >= nw) return;
+      if (one) pairms_body<A, 8, 2, 1>(S.P, w, nw, xt, ppart, i0);
+      else pairms_body<A, 8, 2, NRM>(S.P, w, nw, xt, ppart, i0);
       return;
     }
     case BK_TSUM:
@@ -3697,9 +3718,11 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
         const PairLevel& G = V.plev[l];
         for (int c = 0; c < kPairClasses; ++c) {
           const int r = G.cls_rows[c];
-          int k = kBatchPairKinds - 1;  // the smallest kind whose boxes hold r points
-          if (r > warp_rows)
-            for (k = kBatchPairKinds - 2; k > 0 && r > kBatchKindRows[k]; --k) {
+          int k;  // the smallest kind whose boxes hold r points
+          if (r <= warp_rows)
+            k = r <= 16 ? kBatchW8 : r <= 32 ? kBatchW16 : kBatchWarp;
+          else
+            for (k = kBatchWarp - 1; k > 0 && r > kBatchKindRows[k]; --k) {
             }
           if (k != kind) continue;
           items.insert(items.end(), G.h_work.begin() + G.off[c], G.h_work.begin() + G.off[c + 1]);
@@ -3720,7 +3743,9 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
     u[BK_G64] = (S.p0[5] - S.p0[4] + 3) / 4;
     u[BK_PROJ] = S.u_proj;
     u[BK_NEAR] = S.u_near;
-    u[BK_WARP] = (S.p0[6] - S.p0[5] + 7) / 8;
+    u[BK_WARP] = (S.p0[kBatchWarp + 1] - S.p0[kBatchWarp] + 7) / 8;
+    u[BK_W16] = (S.p0[kBatchW16 + 1] - S.p0[kBatchW16] + 15) / 16;
+    u[BK_W8] = (S.p0[kBatchW8 + 1] - S.p0[kBatchW8] + 31) / 32;
     u[BK_TSUM] = (S.ntsum + 7) / 8;
     u[BK_EXP] = S.nexp;
   }
@@ -3732,8 +3757,10 @@ int batch_persist_setup(hodlr2d* const* hs, int count, const double* const* x, d
   kinds[0] = {BK_GATHER};
   kinds[1] = {BK_BLK8, BK_BLK4, BK_BLK, BK_G128, BK_G64, BK_PROJ};
   if (!(bp->place & 1)) kinds[1].push_back(BK_NEAR);
-  if (!(bp->place & 2)) kinds[1].push_back(BK_WARP);
-  if (bp->place & 2) kinds[2].push_back(BK_WARP);
+  for (int kd : {BK_WARP, BK_W16, BK_W8}) {
+    if (!(bp->place & 2)) kinds[1].push_back(kd);
+    else kinds[2].push_back(kd);
+  }
   kinds[2].push_back(BK_TSUM);
   kinds[3] = {BK_EXP};
   if (bp->place & 1) kinds[3].push_back(BK_NEAR);
