@@ -927,7 +927,7 @@ __global__ void __launch_bounds__(T)
   pairm_body<A, T, RM, NR>(P, work[blockIdx.x], xt, ppart, threadIdx.x);
 }
 
-// Sub-warp form of k_pairm for small boxes (binary32 sums): S lanes per pair
+// Sub-warp form of k_pairm for small boxes: S lanes per pair
 // (S = 8 or 16), 32 / S pairs per warp, the items item0, item0 + 1, ... of
 // the work list; lane s of a segment takes rows s, s + S, ... (RM of them)
 // of X and of Y.  The column loop runs to the largest rank of the warp's
@@ -1025,6 +1025,14 @@ __device__ __forceinline__ void pairms_body(const ArgsV2& P, const int2* __restr
           A::fma(yX[a][c], A::ld(u[a]), t[c]);       // U with t1
           A::fma(yY[a][c], A::ld(v[a]), t[NR + c]);  // V with t2
         }
+      if ((q + 1) % kRenorm == 0)
+#pragma unroll
+        for (int c = 0; c < NR; ++c)
+#pragma unroll
+          for (int a = 0; a < RM; ++a) {
+            A::renorm(yX[a][c]);
+            A::renorm(yY[a][c]);
+          }
 #pragma unroll
       for (int a = 0; a < RM; ++a) {
         u[a] = un[a];
@@ -3078,14 +3086,12 @@ static int launch_pair_multi(const int2* work, int64_t nw, int rows, const ArgsV
   constexpr bool b32 = sizeof(typename A::acc) == 4;
   constexpr int NR = b32 ? 8 : 4;  // right-hand sides per pass
   const unsigned nb = (unsigned)nw;
-  if (b32 && rows <= 16) {  // four pairs per warp
-    if constexpr (b32)
-      k_pairms<A, 8, 2, 4><<<(unsigned)((nw + 4 * kPairmsWarps - 1) / (4 * kPairmsWarps)),
-                             32 * kPairmsWarps, 0, st>>>(P, work, nw, xt, ppart);
-  } else if (b32 && rows <= 32) {  // two pairs per warp
-    if constexpr (b32)
-      k_pairms<A, 16, 2, 4><<<(unsigned)((nw + 2 * kPairmsWarps - 1) / (2 * kPairmsWarps)),
-                              32 * kPairmsWarps, 0, st>>>(P, work, nw, xt, ppart);
+  if (rows <= 16) {  // four pairs per warp
+    k_pairms<A, 8, 2, 4><<<(unsigned)((nw + 4 * kPairmsWarps - 1) / (4 * kPairmsWarps)),
+                           32 * kPairmsWarps, 0, st>>>(P, work, nw, xt, ppart);
+  } else if (rows <= 32) {  // two pairs per warp
+    k_pairms<A, 16, 2, 4><<<(unsigned)((nw + 2 * kPairmsWarps - 1) / (2 * kPairmsWarps)),
+                            32 * kPairmsWarps, 0, st>>>(P, work, nw, xt, ppart);
   } else if (rows <= 64)
     k_pairm<A, 32, 2, NR><<<nb, 32, 0, st>>>(P, work, xt, ppart);
   else if (rows <= 128)
@@ -3115,8 +3121,8 @@ static int pair_form(int rows, int nrhs) {
       if (rows <= lim[i]) return i;
     return rows <= kSmallPair ? 100 : 101;
   }
-  if (b32 && rows <= 16) return 10;
-  if (b32 && rows <= 32) return 11;
+  if (rows <= 16) return 10;
+  if (rows <= 32) return 11;
   if (rows <= 64) return 12;
   if (rows <= 128) return 13;
   if (rows <= kMultiRows) return 14;
