@@ -238,3 +238,40 @@ def test_df32_rank_near_200_blocks(h2d, oracle):
     for mode, bound in (("f64", 1e-12), ("df32", 1e-11)):
         y = gpu_product(g, x, mode)
         assert rel(y, y_o) <= bound, mode
+
+
+@pytest.mark.parametrize("form", ["graph", "persistent"])
+def test_batch_degenerate_sets(h2d, oracle, form):
+    """Batches that mix degenerate sets with ordinary ones, each against its
+    own oracle product on the same factors: a single point, a set no larger
+    than one leaf (kappa = 0: the whole matrix is the dense self block, no
+    stored pairs), a set of exactly one leaf plus one point (kappa = 1), a
+    set whose points all sit in one corner (deep, lopsided tree with empty
+    boxes), and an ordinary set; one and five right-hand sides."""
+    rng = np.random.default_rng(11)
+    corner = 0.9 + 0.1 * rng.uniform(0.0, 1.0, (700, 2))
+    corner = np.concatenate([corner, rng.uniform(-1.0, 1.0, (60, 2))])
+    sets = [rng.uniform(-1.0, 1.0, (1, 2)), inputs.uniform(32, seed=12),
+            inputs.uniform(33, seed=13), corner, inputs.uniform(3000, seed=14)]
+    mats, orcs, xs = [], [], []
+    for i, p in enumerate(sets):
+        a = 0.05
+        o = oracle.Oracle(p, oracle.kernel("imq", a), 32, 1e-10)
+        g = h2d.HODLR2D(p, h2d.kernel("imq", a), 32, 1e-10, compress=False)
+        g.import_factors(*o.export_factors())
+        g.prepare("f32")
+        xs.append(rng.standard_normal(((1, 5)[i % 2], len(p))))
+        mats.append(g)
+        orcs.append(o)
+    assert [o.kappa for o in orcs[:3]] == [0, 0, 1]
+    want = [o.matvec(np.ascontiguousarray(x.T)) for o, x in zip(orcs, xs)]
+    b = h2d.Batch(mats, stream=torch.cuda.current_stream(), form=form)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    for mode in ("f64", "f32"):
+        ys = [torch.empty_like(x) for x in xd]
+        b.matvec(xd, ys, mode=mode)
+        b.check()
+        assert b.last_form == form
+        for y, w in zip(ys, want):
+            assert rel(y.cpu().numpy().T, w) <= BOUND[mode], mode
+    b.close()
