@@ -1665,38 +1665,6 @@ __device__ __forceinline__ void proj2_body(const ArgsV2& P, const ProjTask* __re
   const int k = T.k;
   using F = typename A::fac;
   const F* col = reinterpret_cast<const F*>(L.fac) + T.mat + (int64_t)q * T.ld;
-  if constexpr (std::is_same<F, __nv_bfloat16>::value) {
-    // bfloat16: two rows per 4-byte load (columns, matrix offsets and chunk
-    // starts are even, so the pairs are 4-byte aligned)
-    constexpr int R2 = kChunkP / 64;
-    const int end = T.r0 + T.nr;
-    float va[R2], vb[R2];
-#pragma unroll
-    for (int u = 0; u < R2; ++u) {
-      const int r = T.r0 + 2 * lane + 64 * u;
-      if (r + 1 < end) {
-        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(col + r));
-        va[u] = f.x;
-        vb[u] = f.y;
-      } else {
-        va[u] = r < end ? __bfloat162float(col[r]) : 0.f;
-        vb[u] = 0.f;
-      }
-    }
-    for (int c = 0; c < P.nrhs; ++c) {
-      const V* xv = xt + c * P.n + base;
-      Acc a = A::zero();
-#pragma unroll
-      for (int u = 0; u < R2; ++u) {
-        const int r = T.r0 + 2 * lane + 64 * u;
-        if (r < end) A::fma(a, va[u], xv[r]);
-        if (r + 1 < end) A::fma(a, vb[u], xv[r + 1]);
-      }
-      const V sum = A::warp_sum(a);
-      if (lane == 0) part[T.out * P.nrhs + (int64_t)c * k + q] = sum;
-    }
-    return;
-  }
   V v[R];
 #pragma unroll
   for (int u = 0; u < R; ++u) {
