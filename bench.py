@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     p.add_argument("--extras", default="all",
                    help="comma-separated secondary measurements to run (default: all)")
+    p.add_argument("--batch-sets", type=int, default=256,
+                   help="point sets of the batch measurement (smaller for profiling)")
     p.add_argument("--n-learned", type=int, default=1 << 22,
                    help="points of the learned-rank build (log r kernel)")
     args = p.parse_args()
@@ -633,7 +635,7 @@ def extra_paper_replay(pkg, inputs, stream):
     return out
 
 
-def extras(pkg, inputs, n, n_learned, names="all"):
+def extras(pkg, inputs, n, n_learned, names="all", batch_sets=256):
     """Secondary measurements on one GPU (each section timed on its own);
     names: "all" or a comma-separated subset of the section names."""
     import torch
@@ -643,7 +645,7 @@ def extras(pkg, inputs, n, n_learned, names="all"):
     for name, fn in (("rbf_system", lambda: extra_gmres_nrhs(pkg, inputs, n, stream)),
                      ("paper_replay", lambda: extra_paper_replay(pkg, inputs, stream)),
                      ("panel_system_log", lambda: extra_panel_system(pkg, inputs, stream)),
-                     ("batch_point_sets", lambda: extra_batch(pkg, inputs, stream)),
+                     ("batch_point_sets", lambda: extra_batch(pkg, inputs, stream, batch_sets)),
                      ("learned_rank_log", lambda: extra_learned(pkg, inputs, stream, n_learned))):
         if pick is not None and name not in pick:
             continue
@@ -842,7 +844,7 @@ def run_ours(args, ws, rank, local):
         del v["y"]
     g.close()
     if ws == 1 and not args.no_extras:
-        out["extras"] = extras(pkg, inputs, n, args.n_learned, args.extras)
+        out["extras"] = extras(pkg, inputs, n, args.n_learned, args.extras, args.batch_sets)
     return out
 
 
