@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(T)
   }
   int par = 0, stb = 0;
   for (int q0 = 0; q0 < k; q0 += G) {
-    F u[RM][G], v[RM][G];
+    V u[RM][G], v[RM][G];  // the step's columns, converted to the arithmetic type once
     if constexpr (kAsync) {
       // group q0 + (S - 1) G into the slot freed by the previous step
       issue(q0 + (kPairgStages - 1) * G, (stb + kPairgStages - 1) % kPairgStages);
@@ -702,8 +702,8 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
         for (int a = 0; a < RM; ++a) {
           const int i = tid + a * T;
-          u[a][g] = (qok && i < m) ? *slot(stb, 0, a, g) : fac_zero<F>();
-          v[a][g] = (qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>();
+          u[a][g] = A::ld((qok && i < m) ? *slot(stb, 0, a, g) : fac_zero<F>());
+          v[a][g] = A::ld((qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>());
         }
       }
       stb = (stb + 1) % kPairgStages;
@@ -716,8 +716,8 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
         for (int a = 0; a < RM; ++a) {
           const int i = tid + a * T;
-          u[a][g] = (qok && i < m) ? uc[i] : fac_zero<F>();
-          v[a][g] = (qok && i < n) ? vc[i] : fac_zero<F>();
+          u[a][g] = A::ld((qok && i < m) ? uc[i] : fac_zero<F>());
+          v[a][g] = A::ld((qok && i < n) ? vc[i] : fac_zero<F>());
         }
       }
     }
@@ -729,8 +729,8 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
       for (int a = 0; a < RM; ++a)  // row groups past the box are skipped (block-uniform)
         if (a * T < mn) {
-          A::fma(a1, A::ld(v[a][g]), xY[a]);
-          A::fma(a2, A::ld(u[a][g]), xX[a]);
+          A::fma(a1, v[a][g], xY[a]);
+          A::fma(a2, u[a][g], xX[a]);
         }
       s[g] = A::fin(a1);
       s[G + g] = A::fin(a2);
@@ -759,8 +759,8 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
       for (int a = 0; a < RM; ++a)
         if (a * T < mn) {
-          A::fma(yX[a], A::ld(u[a][g]), t[g]);      // U with t1
-          A::fma(yY[a], A::ld(v[a][g]), t[G + g]);  // V with t2
+          A::fma(yX[a], u[a][g], t[g]);      // U with t1
+          A::fma(yY[a], v[a][g], t[G + g]);  // V with t2
         }
     if ((q0 / G + 1) % (kRenorm / G) == 0)
 #pragma unroll
@@ -852,6 +852,12 @@ __device__ __forceinline__ void pairm_body(const ArgsV2& P, const int2 wk,
         un[a] = i < m && q + 1 < k ? Ug[(int64_t)(q + 1) * lm + i] : fac_zero<F>();
         vn[a] = i < n && q + 1 < k ? Vg[(int64_t)(q + 1) * ln + i] : fac_zero<F>();
       }
+      V uf[RM], vf[RM];  // the column in the arithmetic type, converted once
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        uf[a] = A::ld(u[a]);
+        vf[a] = A::ld(v[a]);
+      }
       V s[NV];  // s[c] = partial t1 of RHS c (V), s[NR + c] = partial t2 (U)
 #pragma unroll
       for (int c = 0; c < NR; ++c) {
@@ -859,8 +865,8 @@ __device__ __forceinline__ void pairm_body(const ArgsV2& P, const int2 wk,
 #pragma unroll
         for (int a = 0; a < RM; ++a)
           if (a * T < mn) {
-            A::fma(a1, A::ld(v[a]), xY[a][c]);
-            A::fma(a2, A::ld(u[a]), xX[a][c]);
+            A::fma(a1, vf[a], xY[a][c]);
+            A::fma(a2, uf[a], xX[a][c]);
           }
         s[c] = A::fin(a1);
         s[NR + c] = A::fin(a2);
@@ -889,8 +895,8 @@ __device__ __forceinline__ void pairm_body(const ArgsV2& P, const int2 wk,
 #pragma unroll
         for (int a = 0; a < RM; ++a)
           if (a * T < mn) {
-            A::fma(yX[a][c], A::ld(u[a]), t[c]);       // U with t1
-            A::fma(yY[a][c], A::ld(v[a]), t[NR + c]);  // V with t2
+            A::fma(yX[a][c], uf[a], t[c]);       // U with t1
+            A::fma(yY[a][c], vf[a], t[NR + c]);  // V with t2
           }
       if ((q + 1) % kRenorm == 0)
 #pragma unroll
@@ -1002,14 +1008,20 @@ __device__ __forceinline__ void pairms_body(const ArgsV2& P, const int2* __restr
         un[a] = i < m && q + 1 < k ? Ug[(int64_t)(q + 1) * lm + i] : fac_zero<F>();
         vn[a] = i < n && q + 1 < k ? Vg[(int64_t)(q + 1) * ln + i] : fac_zero<F>();
       }
+      V uf[RM], vf[RM];  // the column in the arithmetic type, converted once
+#pragma unroll
+      for (int a = 0; a < RM; ++a) {
+        uf[a] = A::ld(u[a]);
+        vf[a] = A::ld(v[a]);
+      }
       V sv[NV];  // sv[c]: partial t1 of RHS c (V), sv[NR + c]: partial t2 (U)
 #pragma unroll
       for (int c = 0; c < NR; ++c) {
         Acc a1 = A::zero(), a2 = A::zero();
 #pragma unroll
         for (int a = 0; a < RM; ++a) {
-          A::fma(a1, A::ld(v[a]), xY[a][c]);
-          A::fma(a2, A::ld(u[a]), xX[a][c]);
+          A::fma(a1, vf[a], xY[a][c]);
+          A::fma(a2, uf[a], xX[a][c]);
         }
         sv[c] = A::fin(a1);
         sv[NR + c] = A::fin(a2);
@@ -1022,8 +1034,8 @@ __device__ __forceinline__ void pairms_body(const ArgsV2& P, const int2* __restr
       for (int c = 0; c < NR; ++c)
 #pragma unroll
         for (int a = 0; a < RM; ++a) {
-          A::fma(yX[a][c], A::ld(u[a]), t[c]);       // U with t1
-          A::fma(yY[a][c], A::ld(v[a]), t[NR + c]);  // V with t2
+          A::fma(yX[a][c], uf[a], t[c]);       // U with t1
+          A::fma(yY[a][c], vf[a], t[NR + c]);  // V with t2
         }
       if ((q + 1) % kRenorm == 0)
 #pragma unroll
@@ -1146,7 +1158,7 @@ __global__ void __launch_bounds__(128)
   if constexpr (kAsync) issue(0, 0);
   int stb = 0;
   for (int q0 = 0; q0 < kw; q0 += G) {
-    F u[RM][G], v[RM][G];
+    V u[RM][G], v[RM][G];  // the step's columns, converted to the arithmetic type once
     if constexpr (kAsync) {
       issue(q0 + G, stb ^ 1);
       cp_async_wait<1>();
@@ -1156,8 +1168,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int a = 0; a < RM; ++a) {
           const int i = sl + a * S;
-          u[a][g] = (qok && i < m) ? *slot(stb, 0, a, g) : fac_zero<F>();
-          v[a][g] = (qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>();
+          u[a][g] = A::ld((qok && i < m) ? *slot(stb, 0, a, g) : fac_zero<F>());
+          v[a][g] = A::ld((qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>());
         }
       }
       stb ^= 1;
@@ -1170,8 +1182,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int a = 0; a < RM; ++a) {
           const int i = sl + a * S;
-          u[a][g] = (qok && i < m) ? uc[i] : fac_zero<F>();
-          v[a][g] = (qok && i < n) ? vc[i] : fac_zero<F>();
+          u[a][g] = A::ld((qok && i < m) ? uc[i] : fac_zero<F>());
+          v[a][g] = A::ld((qok && i < n) ? vc[i] : fac_zero<F>());
         }
       }
     }
@@ -1182,8 +1194,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int a = 0; a < RM; ++a)  // row groups past the warp's boxes are skipped
         if (a * S < mnw) {
-          A::fma(a1, A::ld(v[a][g]), xY[a]);
-          A::fma(a2, A::ld(u[a][g]), xX[a]);
+          A::fma(a1, v[a][g], xY[a]);
+          A::fma(a2, u[a][g], xX[a]);
         }
       s[g] = A::fin(a1);
       s[G + g] = A::fin(a2);
@@ -1197,8 +1209,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int a = 0; a < RM; ++a)
         if (a * S < mnw) {
-          A::fma(yX[a], A::ld(u[a][g]), t[g]);      // U with t1
-          A::fma(yY[a], A::ld(v[a][g]), t[G + g]);  // V with t2
+          A::fma(yX[a], u[a][g], t[g]);      // U with t1
+          A::fma(yY[a], v[a][g], t[G + g]);  // V with t2
         }
     if ((q0 / G + 1) % (kRenorm / G) == 0)
 #pragma unroll
