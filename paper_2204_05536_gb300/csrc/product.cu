@@ -614,6 +614,21 @@ __device__ __forceinline__ typename A::val warp_reduce_scatter(typename A::val (
   return r;
 }
 
+// A step's factor column values held as loaded (CVT false: converted at each
+// use) or converted to the arithmetic type at load (CVT true).
+template <class A, bool CVT>
+struct ColType {
+  using type = typename std::conditional<CVT, typename A::val, typename A::fac>::type;
+  static __device__ __forceinline__ type load(typename A::fac f) {
+    if constexpr (CVT) return A::ld(f);
+    else return f;
+  }
+  static __device__ __forceinline__ typename A::val use(type x) {
+    if constexpr (CVT) return x;
+    else return A::ld(x);
+  }
+};
+
 // k_pairg stages its factor loads through shared memory for float-float
 // factors in blocks of at most 128 threads (measured: these gain, the larger
 // blocks and the binary32 forms lose occupancy for nothing); bytes of dynamic
@@ -690,8 +705,14 @@ __global__ void __launch_bounds__(T)
     for (int sidx = 0; sidx < kPairgStages - 1; ++sidx) issue(sidx * G, sidx);
   }
   int par = 0, stb = 0;
+  // blocks of 256 and 512 threads convert the step's columns to the
+  // arithmetic type once, at load (bfloat16, N = 2^20: their levels 0.95 ->
+  // 0.81 ms); the smaller ones, like k_pairs, keep the factor type and
+  // convert where used (with both converting at load, the levels of boxes of
+  // <= 256 points went 0.25 -> 0.37 ms)
+  using CT = ColType<A, (T >= 256)>;
   for (int q0 = 0; q0 < k; q0 += G) {
-    V u[RM][G], v[RM][G];  // the step's columns, converted to the arithmetic type once
+    typename CT::type u[RM][G], v[RM][G];
     if constexpr (kAsync) {
       // group q0 + (S - 1) G into the slot freed by the previous step
       issue(q0 + (kPairgStages - 1) * G, (stb + kPairgStages - 1) % kPairgStages);
@@ -702,8 +723,8 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
         for (int a = 0; a < RM; ++a) {
           const int i = tid + a * T;
-          u[a][g] = A::ld((qok && i < m) ? *slot(stb, 0, a, g) : fac_zero<F>());
-          v[a][g] = A::ld((qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>());
+          u[a][g] = CT::load((qok && i < m) ? *slot(stb, 0, a, g) : fac_zero<F>());
+          v[a][g] = CT::load((qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>());
         }
       }
       stb = (stb + 1) % kPairgStages;
@@ -716,8 +737,8 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
         for (int a = 0; a < RM; ++a) {
           const int i = tid + a * T;
-          u[a][g] = A::ld((qok && i < m) ? uc[i] : fac_zero<F>());
-          v[a][g] = A::ld((qok && i < n) ? vc[i] : fac_zero<F>());
+          u[a][g] = CT::load((qok && i < m) ? uc[i] : fac_zero<F>());
+          v[a][g] = CT::load((qok && i < n) ? vc[i] : fac_zero<F>());
         }
       }
     }
@@ -729,8 +750,8 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
       for (int a = 0; a < RM; ++a)  // row groups past the box are skipped (block-uniform)
         if (a * T < mn) {
-          A::fma(a1, v[a][g], xY[a]);
-          A::fma(a2, u[a][g], xX[a]);
+          A::fma(a1, CT::use(v[a][g]), xY[a]);
+          A::fma(a2, CT::use(u[a][g]), xX[a]);
         }
       s[g] = A::fin(a1);
       s[G + g] = A::fin(a2);
@@ -759,8 +780,8 @@ __global__ void __launch_bounds__(T)
 #pragma unroll
       for (int a = 0; a < RM; ++a)
         if (a * T < mn) {
-          A::fma(yX[a], u[a][g], t[g]);      // U with t1
-          A::fma(yY[a], v[a][g], t[G + g]);  // V with t2
+          A::fma(yX[a], CT::use(u[a][g]), t[g]);      // U with t1
+          A::fma(yY[a], CT::use(v[a][g]), t[G + g]);  // V with t2
         }
     if ((q0 / G + 1) % (kRenorm / G) == 0)
 #pragma unroll
@@ -1158,7 +1179,7 @@ __global__ void __launch_bounds__(128)
   if constexpr (kAsync) issue(0, 0);
   int stb = 0;
   for (int q0 = 0; q0 < kw; q0 += G) {
-    V u[RM][G], v[RM][G];  // the step's columns, converted to the arithmetic type once
+    F u[RM][G], v[RM][G];  // the step's columns in the factor type (converted where used)
     if constexpr (kAsync) {
       issue(q0 + G, stb ^ 1);
       cp_async_wait<1>();
@@ -1168,8 +1189,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int a = 0; a < RM; ++a) {
           const int i = sl + a * S;
-          u[a][g] = A::ld((qok && i < m) ? *slot(stb, 0, a, g) : fac_zero<F>());
-          v[a][g] = A::ld((qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>());
+          u[a][g] = (qok && i < m) ? *slot(stb, 0, a, g) : fac_zero<F>();
+          v[a][g] = (qok && i < n) ? *slot(stb, 1, a, g) : fac_zero<F>();
         }
       }
       stb ^= 1;
@@ -1182,8 +1203,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int a = 0; a < RM; ++a) {
           const int i = sl + a * S;
-          u[a][g] = A::ld((qok && i < m) ? uc[i] : fac_zero<F>());
-          v[a][g] = A::ld((qok && i < n) ? vc[i] : fac_zero<F>());
+          u[a][g] = (qok && i < m) ? uc[i] : fac_zero<F>();
+          v[a][g] = (qok && i < n) ? vc[i] : fac_zero<F>();
         }
       }
     }
@@ -1194,8 +1215,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int a = 0; a < RM; ++a)  // row groups past the warp's boxes are skipped
         if (a * S < mnw) {
-          A::fma(a1, v[a][g], xY[a]);
-          A::fma(a2, u[a][g], xX[a]);
+          A::fma(a1, A::ld(v[a][g]), xY[a]);
+          A::fma(a2, A::ld(u[a][g]), xX[a]);
         }
       s[g] = A::fin(a1);
       s[G + g] = A::fin(a2);
@@ -1209,8 +1230,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int a = 0; a < RM; ++a)
         if (a * S < mnw) {
-          A::fma(yX[a], u[a][g], t[g]);      // U with t1
-          A::fma(yY[a], v[a][g], t[G + g]);  // V with t2
+          A::fma(yX[a], A::ld(u[a][g]), t[g]);      // U with t1
+          A::fma(yY[a], A::ld(v[a][g]), t[G + g]);  // V with t2
         }
     if ((q0 / G + 1) % (kRenorm / G) == 0)
 #pragma unroll
