@@ -2377,6 +2377,45 @@ __global__ void __launch_bounds__(256)
 // then one thread per row sums U t1 / V t2 over the list in ascending partner
 // order, eight independent loads at a time.
 
+// The several-RHS expansion of one row (exp2_body), EC right-hand sides per
+// pass over the box's list: each factor value is loaded once per pass.
+template <class A, int EC>
+__device__ __forceinline__ void exp2_multi(const ArgsV2& P, int ne, const int* s_k,
+                                           const int64_t* s_off, const int64_t* s_toff,
+                                           const typename A::fac* __restrict__ fac,
+                                           const typename A::val* __restrict__ t,
+                                           typename A::val* __restrict__ yl, int l, int64_t ld,
+                                           int32_t base, int r) {
+  using V = typename A::val;
+  using Acc = typename A::acc;
+  using F = typename A::fac;
+  for (int c0 = 0; c0 < P.nrhs; c0 += EC) {
+    Acc a[EC];
+#pragma unroll
+    for (int c = 0; c < EC; ++c) a[c] = A::zero();
+    for (int e = 0; e < ne; ++e) {
+      const int k = s_k[e];
+      const F* M = fac + s_off[e] + r;
+      const V* tv = t + s_toff[e];
+#pragma unroll 4
+      for (int q = 0; q < k; ++q) {
+        const V mv = A::ld(M[q * ld]);
+#pragma unroll
+        for (int c = 0; c < EC; ++c)
+          if (c0 + c < P.nrhs) A::fma(a[c], mv, tv[(int64_t)(c0 + c) * k + q]);
+        if ((q + 1) % kRenorm == 0)
+#pragma unroll
+          for (int c = 0; c < EC; ++c) A::renorm(a[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < EC; ++c) A::renorm(a[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < EC; ++c)
+      if (c0 + c < P.nrhs) yl[((int64_t)l * P.nrhs + c0 + c) * P.n + base + r] = A::fin(a[c]);
+  }
+}
+
 // (blocks of 256 threads; every thread of the block calls it with the same
 // task: it synchronises the block once)
 template <class A>
@@ -2460,32 +2499,13 @@ __device__ __forceinline__ void exp2_body(const ArgsV2& P, const ExpTask* __rest
   }
   if (!act) return;
   if (P.nrhs > 1) {  // EC right-hand sides per pass: each factor value loaded once per pass
+    // (twice as many per pass above 8 right-hand sides: half the passes over
+    // the factors)
     constexpr int EC = sizeof(typename A::acc) == 4 ? 8 : 4;
-    for (int c0 = 0; c0 < P.nrhs; c0 += EC) {
-      Acc a[EC];
-#pragma unroll
-      for (int c = 0; c < EC; ++c) a[c] = A::zero();
-      for (int e = 0; e < ne; ++e) {
-        const int k = s_k[e];
-        const F* M = fac + s_off[e] + r;
-        const V* tv = t + s_toff[e];
-#pragma unroll 4
-        for (int q = 0; q < k; ++q) {
-          const V mv = A::ld(M[q * ld]);
-#pragma unroll
-          for (int c = 0; c < EC; ++c)
-            if (c0 + c < P.nrhs) A::fma(a[c], mv, tv[(int64_t)(c0 + c) * k + q]);
-          if ((q + 1) % kRenorm == 0)
-#pragma unroll
-            for (int c = 0; c < EC; ++c) A::renorm(a[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < EC; ++c) A::renorm(a[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < EC; ++c)
-        if (c0 + c < P.nrhs) yl[((int64_t)l * P.nrhs + c0 + c) * P.n + base + r] = A::fin(a[c]);
-    }
+    if (P.nrhs > 8)
+      exp2_multi<A, 2 * EC>(P, ne, s_k, s_off, s_toff, fac, t, yl, l, ld, base, r);
+    else
+      exp2_multi<A, EC>(P, ne, s_k, s_off, s_toff, fac, t, yl, l, ld, base, r);
     return;
   }
   for (int c = 0; c < P.nrhs; ++c) {
