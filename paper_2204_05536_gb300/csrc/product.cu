@@ -2499,10 +2499,11 @@ __device__ __forceinline__ void exp2_body(const ArgsV2& P, const ExpTask* __rest
   }
   if (!act) return;
   if (P.nrhs > 1) {  // EC right-hand sides per pass: each factor value loaded once per pass
-    // (twice as many per pass above 8 right-hand sides: half the passes over
-    // the factors)
+    // (float-float: 8 per pass above 8 right-hand sides, half the passes
+    // over the factors; 32 RHS at N = 2^20: 126 -> 115 ms for the product,
+    // where binary32 with 16 per pass lost: expansions 9.06 -> 9.58 ms)
     constexpr int EC = sizeof(typename A::acc) == 4 ? 8 : 4;
-    if (P.nrhs > 8)
+    if (std::is_same<A, DF32A>::value && P.nrhs > 8)
       exp2_multi<A, 2 * EC>(P, ne, s_k, s_off, s_toff, fac, t, yl, l, ld, base, r);
     else
       exp2_multi<A, EC>(P, ne, s_k, s_off, s_toff, fac, t, yl, l, ld, base, r);
