@@ -2450,12 +2450,14 @@ __device__ __forceinline__ void exp2_body(const ArgsV2& P, const ExpTask* __rest
   const int32_t base = bstart(P.leaf_off, P.kappa, l, X);
   const int64_t ld = ldpad(bsize(P.leaf_off, P.kappa, l, X));
   const F* fac = reinterpret_cast<const F*>(L.fac);
-  if (sizeof(F) == 2 && P.nrhs > 1) {  // bfloat16 factors, several right-hand sides:
+  if ((sizeof(F) == 2 || (std::is_same<A, F32A>::value && P.nrhs > 8)) && P.nrhs > 1) {
+    // bfloat16 factors with several right-hand sides, binary32 with many:
     // the pass's t values of an entry are staged in shared memory, kExpQ
     // columns at a time, right-hand sides adjacent: one shared vector read
     // serves all EC sums of a factor value (the whole block takes part).
     // Measured at N = 2^20, 4 RHS: bfloat16 3.07 -> 1.42 ms; binary32 1.63 ->
-    // 2.37 and float-float 3.81 -> 4.51 ms, so those keep the direct loads.
+    // 2.37 and float-float 3.81 -> 4.51 ms, so those keep the direct loads;
+    // binary32 at 32 RHS gains (9.06 -> 8.41 ms) and stages above 8.
     constexpr int EC = sizeof(typename A::acc) == 4 ? 8 : 4;
     __shared__ __align__(16) V s_t[kExpQ][EC];
     for (int c0 = 0; c0 < P.nrhs; c0 += EC) {
