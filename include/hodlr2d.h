@@ -306,7 +306,9 @@ int hodlr2d_pair_features(hodlr2d_t h, int64_t* npairs, float* feats, float* log
  *     benchmark's 256 sets, until hodlr2d_batch_autotune has timed both
  *     forms on the caller's inputs; then the faster of the two.
  * Either form is set up again when a handle's plans, working memory or
- * factor copies have changed since the recording.  The handles must outlive
+ * factor copies have changed since the recording.  A handle may appear once
+ * in a batch (repeats: ARG; its working memory serves one product at a
+ * time).  The handles must outlive
  * the batch and must not be used concurrently with it.  x[i], y[i]: device
  * pointers, n_i x nrhs[i] column-major.  Profiling (hodlr2d_profile) must be
  * off on every handle.  Errors: ARG, STATE, CUDA. */

@@ -95,6 +95,14 @@ int hodlr2d_batch_create(const hodlr2d_t* handles, int count, hodlr2d_batch_t* o
     }
     b->sets.push_back(handles[i]);
   }
+  {  // a handle's working memory serves one product at a time: no repeats
+    std::vector<hodlr2d*> sorted(b->sets);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+      delete b;
+      return HODLR2D_ERR_ARG;
+    }
+  }
   int rc = HODLR2D_OK;
   for (int j = 0; j < hodlr2d_batch::kLanes && !rc; ++j) {
     if (cudaStreamCreateWithFlags(&b->lanes[j], cudaStreamNonBlocking) != cudaSuccess ||

@@ -93,3 +93,14 @@ def test_autotune_leaf(pkg):
     best, times = pkg.autotune_leaf(p, pkg.kernel("imq", 0.01), 1e-8, candidates=(16, 32, 64))
     assert best in (16, 32, 64) and set(times) == {16, 32, 64}
     assert all(t > 0 for t in times.values())
+
+
+def test_batch_rejects_a_repeated_handle(pkg):
+    from paper_2204_05536_gb300 import _lib
+    p = inputs.uniform(2000, seed=7)
+    g = pkg.HODLR2D(p, pkg.kernel("imq", 0.02), 32, 1e-8)
+    h = pkg.HODLR2D(p, pkg.kernel("imq", 0.02), 32, 1e-8)
+    with pytest.raises(_lib.HodlrError) as ei:
+        pkg.Batch([g, h, g])
+    assert ei.value.code == _lib.ERR_ARG
+    pkg.Batch([g, h]).close()
