@@ -65,3 +65,28 @@ def test_argument_checks_without_gpu():
     assert lib.hodlr2d_gmres(None, p, p, 1e-8) == _lib.ERR_ARG
     assert lib.hodlr2d_get_stats(None, None) == _lib.ERR_ARG
     lib.hodlr2d_free(None)  # no-op
+
+
+def test_batch_argument_checks_without_gpu():
+    """The batch entry points reject null handles and out-of-range settings
+    before any device work."""
+    from paper_2204_05536_gb300 import _lib
+    lib = _lib.load()
+    out = C.c_void_p()
+    assert lib.hodlr2d_batch_create(None, 1, C.byref(out)) == _lib.ERR_ARG
+    arr = (C.c_void_p * 1)(None)
+    assert lib.hodlr2d_batch_create(arr, 0, C.byref(out)) == _lib.ERR_ARG
+    assert lib.hodlr2d_batch_create(arr, 1, C.byref(out)) == _lib.ERR_ARG  # a null handle
+    for call in (lambda: lib.hodlr2d_batch_set_form(None, 0),
+                 lambda: lib.hodlr2d_batch_set_wait_limit(None, 1),
+                 lambda: lib.hodlr2d_batch_set_shapes(None, 384, 64),
+                 lambda: lib.hodlr2d_batch_set_blocks_per_sm(None, 3),
+                 lambda: lib.hodlr2d_batch_set_placement(None, 0),
+                 lambda: lib.hodlr2d_batch_check(None),
+                 lambda: lib.hodlr2d_batch_persistent_recorded(None),
+                 lambda: lib.hodlr2d_batch_matvec(None, None, None, None, 0),
+                 lambda: lib.hodlr2d_batch_autotune(None, None, None, None, 0, 1, None),
+                 lambda: lib.hodlr2d_batch_phase_ms(None, None)):
+        assert call() == _lib.ERR_ARG
+    assert lib.hodlr2d_batch_last_form(None) == -1
+    lib.hodlr2d_batch_free(None)  # no-op
